@@ -1,0 +1,515 @@
+/*
+ * pmrc_oracle.c -- plain CPU statement of product-matrix MSR regenerating
+ * codes (Le Scouarnec, "Fast Product-Matrix Regenerating Codes").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA path is
+ * checked against.  Only the test suite, the smoke check and the bench's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper
+ * with the library under paper_1412_3022_gb300/, and the library never calls
+ * it.
+ *
+ * Everything here is deliberately slow and literal:
+ *   - GF(2^8) arithmetic through log/antilog tables (modulus x^8+x^4+x^3+x^2+1,
+ *     i.e. 0x11D, generator g = 2);
+ *   - every matrix is built entry by entry from its definition in the paper;
+ *   - inverses are plain Gauss-Jordan elimination;
+ *   - region work is the definition Y[r][t] = sum_c G[r][c] * X[c][t],
+ *     one byte at a time.
+ *
+ * Notation (0-based throughout; the paper is 1-based in Sec. 3.3 and 0-based
+ * in the Y_{alpha i + j} indexing of Sec. 3.1):
+ *   k data nodes, d = 2k-2 helpers, alpha = d-k+1 = k-1 blocks per node,
+ *   n nodes in total, k*alpha data blocks X, n*alpha coded blocks Y.
+ *
+ * Error codes: 0 ok, -1 bad argument, -2 singular matrix.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#include <stdlib.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ESINGULAR (-2)
+
+#define OR_VANILLA 0
+#define OR_SPARSE 1
+
+/* ------------------------------------------------------------------------ */
+/* GF(2^8), log/antilog tables (Sec. 4: the paper works in GF(2^8) through   */
+/* GF-Complete; modulus 0x11D, generator g = 2).                            */
+/* ------------------------------------------------------------------------ */
+
+static uint8_t or_exp[255]; /* or_exp[i] = g^i                         */
+static int or_log[256];     /* or_log[g^i] = i; or_log[0] unused (-1)   */
+static int or_ready = 0;
+
+static void or_init(void)
+{
+    if (or_ready)
+        return;
+    int x = 1;
+    for (int i = 0; i < 256; i++)
+        or_log[i] = -1;
+    for (int i = 0; i < 255; i++) {
+        or_exp[i] = (uint8_t)x;
+        or_log[x] = i;
+        x <<= 1;              /* multiply by g = 2 ...              */
+        if (x & 0x100)
+            x ^= 0x11D;       /* ... and reduce modulo the polynomial */
+    }
+    or_ready = 1;
+}
+
+uint8_t or_gf_mul(uint8_t a, uint8_t b)
+{
+    or_init();
+    if (a == 0 || b == 0)
+        return 0;
+    return or_exp[(or_log[a] + or_log[b]) % 255];
+}
+
+/* a^-1 for a != 0; returns 0 for a == 0 (callers never ask for it). */
+uint8_t or_gf_inv(uint8_t a)
+{
+    or_init();
+    if (a == 0)
+        return 0;
+    return or_exp[(255 - or_log[a]) % 255];
+}
+
+/* g^e for any integer e >= 0. */
+uint8_t or_gf_pow_g(int e)
+{
+    or_init();
+    return or_exp[e % 255];
+}
+
+int or_gf_log(uint8_t a)
+{
+    or_init();
+    return or_log[a];
+}
+
+/* Addition and subtraction in GF(2^8) are both XOR. */
+static uint8_t or_add(uint8_t a, uint8_t b) { return (uint8_t)(a ^ b); }
+
+/* ------------------------------------------------------------------------ */
+/* Small dense matrices over GF(2^8), row-major.                             */
+/* ------------------------------------------------------------------------ */
+
+/* C (m x p) = A (m x q) * B (q x p) */
+void or_mat_mul(int m, int q, int p, const uint8_t *A, const uint8_t *B, uint8_t *C)
+{
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < p; j++) {
+            uint8_t s = 0;
+            for (int l = 0; l < q; l++)
+                s = or_add(s, or_gf_mul(A[i * q + l], B[l * p + j]));
+            C[i * p + j] = s;
+        }
+}
+
+/* Gauss-Jordan inverse of the m x m matrix A.  Returns OR_ESINGULAR if A has
+ * no inverse (Sec. 2: decoding is X = G~^-1 Y~). */
+int or_invert(int m, const uint8_t *A, uint8_t *Ainv)
+{
+    if (m <= 0)
+        return OR_EINVAL;
+    uint8_t *W = (uint8_t *)malloc((size_t)m * 2 * m);
+    if (!W)
+        return OR_EINVAL;
+    int w = 2 * m;
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < w; j++)
+            W[i * w + j] = j < m ? A[i * m + j] : (uint8_t)(j - m == i);
+    for (int col = 0; col < m; col++) {
+        int piv = -1;
+        for (int i = col; i < m; i++)
+            if (W[i * w + col] != 0) {
+                piv = i;
+                break;
+            }
+        if (piv < 0) {
+            free(W);
+            return OR_ESINGULAR;
+        }
+        if (piv != col)
+            for (int j = 0; j < w; j++) {
+                uint8_t t = W[col * w + j];
+                W[col * w + j] = W[piv * w + j];
+                W[piv * w + j] = t;
+            }
+        uint8_t s = or_gf_inv(W[col * w + col]);
+        for (int j = 0; j < w; j++)
+            W[col * w + j] = or_gf_mul(s, W[col * w + j]);
+        for (int i = 0; i < m; i++) {
+            if (i == col || W[i * w + col] == 0)
+                continue;
+            uint8_t f = W[i * w + col];
+            for (int j = 0; j < w; j++)
+                W[i * w + j] = or_add(W[i * w + j], or_gf_mul(f, W[col * w + j]));
+        }
+    }
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++)
+            Ainv[i * m + j] = W[i * w + m + j];
+    free(W);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Code parameters and the encoding matrix Psi = [Phi  Lambda*Phi]           */
+/* (Sec. 3.3).                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* MSR point with d = 2k-2: alpha = Delta = d-k+1 = k-1 (Sec. 2). */
+int or_params(int n, int k, int *d, int *alpha)
+{
+    if (k < 2 || n < 2 * k - 1 || n > 254)
+        return OR_EINVAL;
+    *d = 2 * k - 2;
+    *alpha = k - 1;
+    return OR_OK;
+}
+
+/* Phi (n x alpha) and the diagonal of Lambda (n).
+ *
+ * Vanilla (Sec. 3.3, the Vandermonde construction): Phi_{i,j} = g^{ij}
+ * (0-based) and, from the printed n=5 example whose Lambda is
+ * diag(1, g^2, g^4, g^6, g^8) at alpha = 2, lambda_i = g^{i*alpha}; then
+ * Psi_{i,l} = g^{il} is the Vandermonde matrix printed beside it.
+ *
+ * Sparse (Sec. 3.3, the paper's construction), in the paper's 1-based
+ * indices i = 1..n, j = 1..alpha:
+ *   Phi_{i,j} = delta_{ij}                        for i <= alpha,
+ *   Phi_{i,j} = (g^{i+alpha} - g^{j-1})^-1          for i > alpha,
+ *   lambda_i  = (g^{i+alpha} - g^0) / (g^{i+alpha} - g^alpha).
+ */
+int or_phi_lambda(int n, int k, int construction, uint8_t *phi, uint8_t *lambda)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    if (construction == OR_VANILLA) {
+        for (int i = 0; i < n; i++) {
+            for (int j = 0; j < a; j++)
+                phi[i * a + j] = or_gf_pow_g(i * j);
+            lambda[i] = or_gf_pow_g(i * a);
+        }
+        return OR_OK;
+    }
+    if (construction == OR_SPARSE) {
+        for (int i1 = 1; i1 <= n; i1++) {
+            int i = i1 - 1;
+            for (int j1 = 1; j1 <= a; j1++) {
+                int j = j1 - 1;
+                if (i1 <= a)
+                    phi[i * a + j] = (uint8_t)(i1 == j1);
+                else
+                    phi[i * a + j] =
+                        or_gf_inv(or_add(or_gf_pow_g(i1 + a), or_gf_pow_g(j1 - 1)));
+            }
+            uint8_t num = or_add(or_gf_pow_g(i1 + a), or_gf_pow_g(0));
+            uint8_t den = or_add(or_gf_pow_g(i1 + a), or_gf_pow_g(a));
+            lambda[i] = or_gf_mul(num, or_gf_inv(den));
+        }
+        return OR_OK;
+    }
+    return OR_EINVAL;
+}
+
+/* Psi (n x d) = [Phi  Lambda*Phi] (Sec. 3.3, first constraint). */
+int or_psi(int n, int k, int construction, uint8_t *psi)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    uint8_t *phi = (uint8_t *)malloc((size_t)n * a);
+    uint8_t *lam = (uint8_t *)malloc((size_t)n);
+    int rc = or_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < a; j++) {
+                psi[i * d + j] = phi[i * a + j];
+                psi[i * d + a + j] = or_gf_mul(lam[i], phi[i * a + j]);
+            }
+    free(phi);
+    free(lam);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Message matrix and its index matrix L (Sec. 3.1).                         */
+/* ------------------------------------------------------------------------ */
+
+/* L (d x alpha): M_{l,j} = X_{L[l][j]}.  M = [S1; S2] with S1 and S2
+ * symmetric alpha x alpha.  The upper triangle of S1 is numbered row by row
+ * (0 .. alpha(alpha+1)/2 - 1), S2 continues the numbering; the lower triangle
+ * mirrors the upper one.  For k = 3 this is the paper's printed example
+ * L^t = [[1,2,4,5],[2,3,5,6]] (1-based). */
+int or_index_matrix(int k, int *L)
+{
+    int a = k - 1, d = 2 * k - 2;
+    if (k < 2)
+        return OR_EINVAL;
+    int half = a * (a + 1) / 2;
+    for (int s = 0; s < 2; s++) {
+        int base = s * half;
+        for (int r = 0; r < a; r++)
+            for (int c = 0; c < a; c++) {
+                int i = r < c ? r : c, j = r < c ? c : r; /* upper-triangle cell */
+                int num = 0;                              /* row-major rank of (i, j) */
+                for (int rr = 0; rr < i; rr++)
+                    num += a - rr;
+                num += j - i;
+                L[(s * a + r) * a + c] = base + num;
+            }
+    }
+    (void)d;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linearized generator (Sec. 3.1) and systematic form (Sec. 3.2).           */
+/* ------------------------------------------------------------------------ */
+
+/* G (n*alpha x k*alpha): G[alpha i + j][L[l][j]] = Psi[i][l] for l < d, and
+ * zero elsewhere.  (The paper's sum runs "l = 1..n"; M has d rows, so it runs
+ * over l < d.) */
+int or_generator(int n, int k, int construction, uint8_t *G)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a;
+    uint8_t *psi = (uint8_t *)malloc((size_t)n * d);
+    int *L = (int *)malloc(sizeof(int) * d * a);
+    int rc = or_psi(n, k, construction, psi);
+    if (rc == OR_OK) {
+        or_index_matrix(k, L);
+        memset(G, 0, (size_t)n * a * K);
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < a; j++)
+                for (int l = 0; l < d; l++)
+                    G[(size_t)(a * i + j) * K + L[l * a + j]] = psi[i * d + l];
+    }
+    free(psi);
+    free(L);
+    return rc;
+}
+
+/* G' = G * G~^-1 with G~ the first k*alpha rows of G (Sec. 3.2).  The first
+ * k*alpha rows of G' are the identity; the rest is G''. */
+int or_systematic_generator(int n, int k, int construction, uint8_t *Gp)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a, N = n * a;
+    uint8_t *G = (uint8_t *)malloc((size_t)N * K);
+    uint8_t *Ginv = (uint8_t *)malloc((size_t)K * K);
+    int rc = or_generator(n, k, construction, G);
+    if (rc == OR_OK)
+        rc = or_invert(K, G, Ginv); /* G~ = first K rows of G */
+    if (rc == OR_OK)
+        or_mat_mul(N, K, K, G, Ginv, Gp);
+    free(G);
+    free(Ginv);
+    return rc;
+}
+
+/* The code's generator: G (non-systematic) or G' (systematic). */
+int or_code_generator(int n, int k, int construction, int systematic, uint8_t *Gout)
+{
+    return systematic ? or_systematic_generator(n, k, construction, Gout)
+                      : or_generator(n, k, construction, Gout);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Region work: Y = M X over byte blocks (Sec. 2: Y = GX, blockwise).        */
+/* ------------------------------------------------------------------------ */
+
+/* out[r][t] = sum_c M[r][c] * in[c][t] for t < nbytes.  Block c of the input
+ * starts at in + c*in_stride, block r of the output at out + r*out_stride. */
+void or_region_apply(int rows, int cols, const uint8_t *M, const uint8_t *in,
+                     size_t in_stride, uint8_t *out, size_t out_stride, size_t nbytes)
+{
+    for (int r = 0; r < rows; r++) {
+        uint8_t *y = out + (size_t)r * out_stride;
+        memset(y, 0, nbytes);
+        for (int c = 0; c < cols; c++) {
+            uint8_t m = M[(size_t)r * cols + c];
+            if (m == 0)
+                continue; /* a zero coefficient adds nothing (Sec. 3.3) */
+            const uint8_t *x = in + (size_t)c * in_stride;
+            for (size_t t = 0; t < nbytes; t++)
+                y[t] = or_add(y[t], or_gf_mul(m, x[t]));
+        }
+    }
+}
+
+/* Encode (Sec. 3.1/3.2): out receives all n*alpha coded blocks, node-major
+ * (block alpha*i + j is slot j of node i).  For the systematic code the first
+ * k*alpha blocks equal the data. */
+int or_encode(int n, int k, int construction, int systematic, const uint8_t *data,
+              uint8_t *out, size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a, N = n * a;
+    uint8_t *G = (uint8_t *)malloc((size_t)N * K);
+    int rc = or_code_generator(n, k, construction, systematic, G);
+    if (rc == OR_OK)
+        or_region_apply(N, K, G, data, nbytes, out, nbytes, nbytes);
+    free(G);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Repair of node f from d helpers (product-matrix MSR repair; Sec. 3.3      */
+/* describes which helper blocks are read).                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Helper coefficients: the helper sends p_h = sum_j phi_f[j] * Y[alpha h + j],
+ * i.e. its stored row C_h = psi_h^t M projected on phi_f. */
+int or_helper_coefficients(int n, int k, int construction, int f, uint8_t *coef)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a) || f < 0 || f >= n)
+        return OR_EINVAL;
+    uint8_t *phi = (uint8_t *)malloc((size_t)n * a);
+    uint8_t *lam = (uint8_t *)malloc((size_t)n);
+    int rc = or_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK)
+        memcpy(coef, phi + (size_t)f * a, (size_t)a);
+    free(phi);
+    free(lam);
+    return rc;
+}
+
+int or_repair_helper(int n, int k, int construction, int f, const uint8_t *blocks,
+                     uint8_t *out, size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    uint8_t *coef = (uint8_t *)malloc((size_t)a);
+    int rc = or_helper_coefficients(n, k, construction, f, coef);
+    if (rc == OR_OK)
+        or_region_apply(1, a, coef, blocks, nbytes, out, nbytes, nbytes);
+    free(coef);
+    return rc;
+}
+
+/* Newcomer matrix D (alpha x d).  With Psi_H the rows of Psi for the helpers
+ * (in list order), the received vector is p = Psi_H M phi_f, so
+ * M phi_f = Psi_H^-1 p = [S1 phi_f; S2 phi_f].  By symmetry of S1 and S2 the
+ * lost row is C_f = phi_f^t S1 + lambda_f phi_f^t S2, hence
+ *   D[j][c] = Psi_H^-1[j][c] + lambda_f * Psi_H^-1[alpha + j][c]. */
+int or_newcomer_matrix(int n, int k, int construction, int f, const int *helpers,
+                       uint8_t *D)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a) || f < 0 || f >= n)
+        return OR_EINVAL;
+    for (int i = 0; i < d; i++) {
+        if (helpers[i] < 0 || helpers[i] >= n || helpers[i] == f)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (helpers[j] == helpers[i])
+                return OR_EINVAL;
+    }
+    uint8_t *psi = (uint8_t *)malloc((size_t)n * d);
+    uint8_t *PH = (uint8_t *)malloc((size_t)d * d);
+    uint8_t *PHinv = (uint8_t *)malloc((size_t)d * d);
+    uint8_t *phi = (uint8_t *)malloc((size_t)n * a);
+    uint8_t *lam = (uint8_t *)malloc((size_t)n);
+    int rc = or_psi(n, k, construction, psi);
+    if (rc == OR_OK)
+        rc = or_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK) {
+        for (int i = 0; i < d; i++)
+            memcpy(PH + (size_t)i * d, psi + (size_t)helpers[i] * d, (size_t)d);
+        rc = or_invert(d, PH, PHinv);
+    }
+    if (rc == OR_OK)
+        for (int j = 0; j < a; j++)
+            for (int c = 0; c < d; c++)
+                D[j * d + c] = or_add(PHinv[j * d + c],
+                                      or_gf_mul(lam[f], PHinv[(a + j) * d + c]));
+    free(psi);
+    free(PH);
+    free(PHinv);
+    free(phi);
+    free(lam);
+    return rc;
+}
+
+/* recv: d blocks, in the order of helpers; out: the alpha blocks of node f. */
+int or_repair_newcomer(int n, int k, int construction, int f, const int *helpers,
+                       const uint8_t *recv, uint8_t *out, size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    uint8_t *D = (uint8_t *)malloc((size_t)a * d);
+    int rc = or_newcomer_matrix(n, k, construction, f, helpers, D);
+    if (rc == OR_OK)
+        or_region_apply(a, d, D, recv, nbytes, out, nbytes, nbytes);
+    free(D);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction from any k nodes (Sec. 2: X = G~^-1 Y~).                   */
+/* ------------------------------------------------------------------------ */
+
+/* Inverse of the k*alpha rows of the code generator that belong to nodes[]
+ * (node-major, slots in order). */
+int or_decode_matrix(int n, int k, int construction, int systematic, const int *nodes,
+                     uint8_t *Rinv)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    for (int i = 0; i < k; i++) {
+        if (nodes[i] < 0 || nodes[i] >= n)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (nodes[j] == nodes[i])
+                return OR_EINVAL;
+    }
+    int K = k * a, N = n * a;
+    uint8_t *G = (uint8_t *)malloc((size_t)N * K);
+    uint8_t *GR = (uint8_t *)malloc((size_t)K * K);
+    int rc = or_code_generator(n, k, construction, systematic, G);
+    if (rc == OR_OK) {
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < a; j++)
+                memcpy(GR + (size_t)(a * i + j) * K,
+                       G + (size_t)(a * nodes[i] + j) * K, (size_t)K);
+        rc = or_invert(K, GR, Rinv);
+    }
+    free(G);
+    free(GR);
+    return rc;
+}
+
+/* node_blocks: the k*alpha blocks of nodes[] (node-major); data: k*alpha
+ * data blocks X. */
+int or_decode(int n, int k, int construction, int systematic, const int *nodes,
+              const uint8_t *node_blocks, uint8_t *data, size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a;
+    uint8_t *Rinv = (uint8_t *)malloc((size_t)K * K);
+    int rc = or_decode_matrix(n, k, construction, systematic, nodes, Rinv);
+    if (rc == OR_OK)
+        or_region_apply(K, K, Rinv, node_blocks, nbytes, data, nbytes, nbytes);
+    free(Rinv);
+    return rc;
+}
