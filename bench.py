@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark of the PM-MSR hot path on GB300.
+
+Workload: the n=16, k=8, d=14, alpha=7 product-matrix MSR code over GF(2^8)
+(modulus 0x11D), one stripe of 56 data blocks of 1 MiB (56 MiB) of seeded
+uniform random bytes.  One step runs every operation of the hot path once:
+
+  gen_encode  vanilla (Vandermonde) generator form, 56 -> 112 blocks
+  sys_encode  sparse systematic form, 56 data -> 56 parity blocks
+  repair      a seeded failed node: d=14 helper projections (one batched
+              launch) and the newcomer's apply, 14 -> 7 blocks
+  decode      reconstruction from a seeded 8-node subset (systematic, lazy:
+              data blocks of surviving data nodes stay in place)
+
+Throughput is user data / time (the paper's Sec. 4 definition: k*alpha
+blocks for encode and decode, alpha blocks for repair), GB = 1e9 B.  L2 is
+flushed (512 MiB write) before every operation, outside the timed events.
+Each operation is timed with CUDA events on the launch stream.
+
+--impl reference times the CPU oracle (plain C, one core) on a bounded
+column sample of the same stripe instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PM-MSR k=8 encode/repair GB/s & %HBM roofline; batched vs plain; p99 ms"
+N_, K_, A_ = 16, 8, 7
+D_ = 2 * K_ - 2
+WORKLOAD = ("PM-MSR n=16 k=8 d=14 alpha=7 GF(2^8)/0x11D, 56 data blocks x 1 MiB "
+            "(56 MiB stripe): vanilla generator encode + sparse systematic encode + "
+            "repair of a seeded node (14 helper projections + newcomer) + "
+            "reconstruction from a seeded 8-node subset")
+FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--block-bytes", type=int, default=1 << 20)
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ ours
+class Workload:
+    def __init__(self, torch, P, inputs, B, seed, device):
+        self.t = torch
+        self.B = B
+        a, K = A_, K_ * A_
+        self.sysc = P.Code(N_, K_, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+        self.genc = P.Code(N_, K_, P.PMRC_VANILLA, P.PMRC_NONSYSTEMATIC)
+        self.X = inputs.device_blocks(K, B, seed, device=device)
+        self.gen_out = torch.empty((N_ * a, B), dtype=torch.uint8, device=device)
+        # the stored codeword (data + parity) that repair and decode read
+        self.Y = torch.empty((N_ * a, B), dtype=torch.uint8, device=device)
+        self.Y[:K].copy_(self.X)
+        self.f = inputs.failed_node(N_, seed)
+        self.H = self.sysc.default_helpers(self.f)
+        self.recv = torch.empty((D_, B), dtype=torch.uint8, device=device)
+        self.node = torch.empty((a, B), dtype=torch.uint8, device=device)
+        self.S = inputs.node_subset(N_, K_, seed)
+        self.data_out = torch.empty((K, B), dtype=torch.uint8, device=device)
+        self.x_ptrs = [self.X[i] for i in range(K)]
+        self.gen_ptrs = [self.gen_out[i] for i in range(N_ * a)]
+        self.par_ptrs = [self.Y[K + i] for i in range(K)]
+        self.helper_in = [self.Y[a * h + j] for h in self.H for j in range(a)]
+        self.recv_ptrs = [self.recv[i] for i in range(D_)]
+        self.node_ptrs = [self.node[j] for j in range(a)]
+        self.dec_in = [self.Y[a * i + j] for i in self.S for j in range(a)]
+        self.dec_out = [self.data_out[r] for r in range(K)]
+        for pos, i in enumerate(self.S):   # lazy decode: present data stays in place
+            if i < K_:
+                for j in range(a):
+                    self.dec_out[a * i + j] = self.dec_in[a * pos + j]
+        self.sysc.encode(self.x_ptrs, self.par_ptrs, B)  # codeword for repair/decode
+        self._bytes()
+
+    def _bytes(self):
+        """Algorithmic HBM bytes and user bytes per operation."""
+        import numpy as np
+        B, a, K = self.B, A_, K_ * A_
+        coef = self.sysc.helper_coefficients(self.f)
+        reads_per_helper = int((coef != 0).sum())
+        R = self.sysc.decode_matrix(self.S)
+        present = {a * i + j for i in self.S if i < K_ for j in range(a)}
+        missing = [r for r in range(K) if r not in present]
+        dec_inputs = int((R[missing] != 0).any(axis=0).sum()) if missing else 0
+        self.alg = {
+            "gen_encode": (K + N_ * a) * B,
+            "sys_encode": (K + K) * B,
+            "repair_helpers": (D_ * reads_per_helper + D_) * B,
+            "repair_newcomer": (D_ + a) * B,
+            "decode": (dec_inputs + len(missing)) * B,
+        }
+        self.user = {"gen_encode": K * B, "sys_encode": K * B, "repair": a * B, "decode": K * B}
+        self.decode_missing = len(missing)
+        self.helper_reads = reads_per_helper
+        del np
+
+    def ops(self):
+        s, B = self, self.B
+        return [
+            ("gen_encode", lambda: s.genc.encode(s.x_ptrs, s.gen_ptrs, B)),
+            ("sys_encode", lambda: s.sysc.encode(s.x_ptrs, s.par_ptrs, B)),
+            ("repair_helpers", lambda: s.sysc.repair_helpers(s.f, s.H, s.helper_in, s.recv_ptrs, B)),
+            ("repair_newcomer", lambda: s.sysc.repair_newcomer(s.f, s.H, s.recv_ptrs, s.node_ptrs, B)),
+            ("decode", lambda: s.sysc.decode(s.S, s.dec_in, s.dec_out, B)),
+        ]
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1412_3022_gb300 as P
+    from paper_1412_3022_gb300 import inputs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B = args.block_bytes
+    W = Workload(torch, P, inputs, B, args.seed + 1000 * rank, dev)
+    ops = W.ops()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    names = [n for n, _ in ops]
+    ev = {n: [] for n in names}
+
+    def step(record):
+        for name, fn in ops:
+            flush.fill_(7)
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            fn()
+            if record:
+                e1.record(stream)
+                ev[name].append((e0, e1))
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    op_ms = {n: sum(a.elapsed_time(b) for a, b in ev[n]) / args.steps for n in names}
+    step_ms = sum(op_ms.values())
+    if dist:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    user_step = sum(W.user.values())
+    value = user_step * world / (step_ms * 1e-3) / 1e9
+    hbm, peak_src = measured_peaks()
+
+    per_op = {}
+    for n in names:
+        gbs = W.alg[n] / (op_ms[n] * 1e-3) / 1e9
+        per_op[n] = {"ms": round(op_ms[n], 4), "alg_bytes": W.alg[n],
+                     "hbm_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4)}
+    for n in ("gen_encode", "sys_encode", "decode"):
+        per_op[n]["user_GBps"] = round(W.user[n] / (op_ms[n] * 1e-3) / 1e9, 2)
+    rep_ms = op_ms["repair_helpers"] + op_ms["repair_newcomer"]
+    per_op["repair"] = {"ms": round(rep_ms, 4),
+                        "user_GBps": round(W.user["repair"] / (rep_ms * 1e-3) / 1e9, 2),
+                        "frac_hbm": round((W.alg["repair_helpers"] + W.alg["repair_newcomer"])
+                                          / (rep_ms * 1e-3) / 1e9 / hbm, 4),
+                        "failed_node": W.f, "helper_reads": W.helper_reads}
+    per_op["decode"]["nodes"] = W.S
+    per_op["decode"]["missing_rows"] = W.decode_missing
+    dom = max(names, key=lambda n: op_ms[n])
+    ach = W.alg[dom] / (op_ms[dom] * 1e-3) / 1e9
+    roofline = {"kernel": "region_kernel (" + dom + ")", "bound": "hbm",
+                "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "peak_source": peak_src + " hbm_gbs (burst copy)",
+                "traffic": None}
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                roofline["traffic"] = json.load(f).get(dom)
+        except (OSError, ValueError):
+            pass
+
+    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream)
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "wall_ms_per_step": round(wall * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded uniform random bytes, generated on device)",
+        "config": {"workload": WORKLOAD, "block_bytes": B, "stripe_bytes": K_ * A_ * B,
+                   "user_bytes_per_step": user_step, "l2": "flushed before every op "
+                   "(512 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world} (independent stripes, no collective)"},
+        "roofline": roofline,
+        "per_op": per_op,
+        "gpu_launches": 5 * args.steps,
+        "clocks": ck,
+        "paper_context_MBps": {"sys_encode_sparse_k8_16KB_1core": 790,
+                               "sys_encode_vanilla_k8_1core": 210, "repair_sparse_1core": 480},
+    }
+    if e2e:
+        result["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args, W, torch)
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+def run_e2e(torch, W, args, dev, stream):
+    """Same step through the public API with host buffers: pinned H2D of the
+    stripe, every operation, D2H of every block the step produced."""
+    B, K, a = W.B, K_ * A_, A_
+    hx = torch.empty((K, B), dtype=torch.uint8).pin_memory()
+    hx.copy_(W.X.cpu())
+    out_rows = W.gen_out.shape[0] + K + a + W.decode_missing
+    hout = torch.empty((out_rows, B), dtype=torch.uint8).pin_memory()
+    present = {a * i + j for i in W.S if i < K_ for j in range(a)}
+    missing = [r for r in range(K) if r not in present]
+    ops = W.ops()
+
+    def step():
+        W.X.copy_(hx, non_blocking=True)
+        for _, fn in ops:
+            fn()
+        o = 0
+        hout[o:o + N_ * a].copy_(W.gen_out, non_blocking=True)
+        o += N_ * a
+        hout[o:o + K].copy_(W.Y[K:], non_blocking=True)
+        o += K
+        hout[o:o + a].copy_(W.node, non_blocking=True)
+        o += a
+        for r in missing:
+            hout[o].copy_(W.data_out[r], non_blocking=True)
+            o += 1
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    user = sum(W.user.values())
+    return {"value": round(user / (ms * 1e-3) / 1e9, 2), "unit": "GB/s", "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": K * B, "d2h_bytes_per_step": out_rows * B}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_step(O, X, Y, f, H, S):
+    """One pass of the four operations through the CPU oracle on column-sliced
+    blocks X (data) and Y (stored codeword)."""
+    a = A_
+    O.encode(N_, K_, O.VANILLA, False, X)
+    O.encode(N_, K_, O.SPARSE, True, X)
+    sent = __import__("numpy").stack(
+        [O.repair_helper(N_, K_, O.SPARSE, f, Y[a * h:a * h + a]) for h in H])
+    O.repair_newcomer(N_, K_, O.SPARSE, f, H, sent)
+    rows = [a * i + j for i in S for j in range(a)]
+    O.decode(N_, K_, O.SPARSE, True, S, Y[rows])
+
+
+def oracle_sample(cols, seed):
+    import numpy as np
+
+    import oracle as O
+    from paper_1412_3022_gb300 import inputs
+    X = inputs.blocks(K_ * A_, cols, seed)
+    Y = O.encode(N_, K_, O.SPARSE, True, X)
+    f = inputs.failed_node(N_, seed)
+    S = inputs.node_subset(N_, K_, seed)
+    # default helpers: the d lowest-index survivors if invertible, else the next set
+    import itertools
+    surv = [i for i in range(N_) if i != f]
+    for H in itertools.combinations(surv, D_):
+        try:
+            O.newcomer_matrix(N_, K_, O.SPARSE, f, list(H))
+            break
+        except O.OracleError:
+            continue
+    del np
+    return O, X, Y, f, list(H), S
+
+
+def calibrate_cols(seconds, seed):
+    cols = 4096
+    O, X, Y, f, H, S = oracle_sample(cols, seed)
+    t0 = time.perf_counter()
+    oracle_step(O, X, Y, f, H, S)
+    dt = time.perf_counter() - t0
+    want = int(cols * seconds / max(dt, 1e-3))
+    return max(4096, min(want // 4096 * 4096, 1 << 20))
+
+
+def cpu_baseline(args, W, torch):
+    seed = args.seed
+    cols = calibrate_cols(args.cpu_seconds, seed)
+    O, X, Y, f, H, S = oracle_sample(cols, seed)
+    t0 = time.perf_counter()
+    oracle_step(O, X, Y, f, H, S)
+    dt = time.perf_counter() - t0
+    user = (2 * K_ * A_ + A_ + K_ * A_) * cols
+    return {"value": round(user / dt / 1e9, 5), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "seconds": round(dt, 2),
+            "sample": f"one step (all four operations) on {cols}-byte column slices of the "
+                      f"n=16 k=8 stripe (56 blocks x {cols} B), plain C oracle, one thread"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    # size each step so that warmup+steps stay within a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    cols = calibrate_cols(min(budget, 6.0), args.seed)
+    O, X, Y, f, H, S = oracle_sample(cols, args.seed)
+    for _ in range(args.warmup):
+        oracle_step(O, X, Y, f, H, S)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(O, X, Y, f, H, S)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    user = (2 * K_ * A_ + A_ + K_ * A_) * cols
+    value = round(user / dt / 1e9, 5)
+    sample = (f"each step: all four operations on {cols}-byte column slices of the n=16 k=8 "
+              f"stripe, plain C oracle, one thread")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f" (oracle on {cols}-byte column slices)",
+                       "block_bytes": cols},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * pmrc.h -- C ABI of libpmrc: product-matrix minimum-storage regenerating
+ * (PM-MSR) codes over GF(2^8) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Follows N. Le Scouarnec, "Fast Product-Matrix Regenerating Codes":
+ *   Sec. 2    the code as a linear map: k*alpha data blocks X, n*alpha coded
+ *             blocks Y = G X; decoding X = G~^-1 Y~ from the rows that remain;
+ *             MSR point alpha = Delta = d-k+1; repair downloads one block from
+ *             each of d helpers.
+ *   Sec. 3.1  linearization: G[alpha i + j][L[l][j]] = Psi[i][l].
+ *   Sec. 3.2  systematic form G' = G G~^-1 = [I; G''].
+ *   Sec. 3.3  Psi = [Phi  Lambda*Phi]: the vanilla (Vandermonde) and the
+ *             sparse (identity + Cauchy) constructions; helpers of a failed
+ *             node among the alpha first read one block, alpha otherwise.
+ *
+ * Parameters: d = 2k-2, alpha = k-1, 2k-1 <= n <= 254, field GF(2^8) with
+ * modulus x^8+x^4+x^3+x^2+1 (0x11D) and generator g = 2.  Node i stores the
+ * alpha blocks Y[alpha*i .. alpha*i + alpha-1] ("node-major").  The message
+ * matrix M = [S1; S2] numbers the upper triangle of S1 row by row, then that
+ * of S2 (only non-systematic codewords depend on this order).
+ *
+ * Conventions shared by every call:
+ *   - Region pointers (data, out, blocks, ...) are DEVICE pointers owned by
+ *     the caller, all blocks of one call have the same size block_bytes
+ *     (any value >= 0; 0 does nothing).  16-byte aligned pointers take the
+ *     vector path, any other alignment a slower byte path; results are the
+ *     same.  Arrays of pointers (const uint8_t *const *) are HOST arrays.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream) on the current CUDA device, return a status, never
+ *     throw and never exit.  Input blocks must not overlap output blocks.
+ *   - A call may build and upload a small coefficient plan on first use of
+ *     an (operation, failure pattern, device) combination (a synchronous
+ *     cudaMalloc + cudaMemcpy); make that first call outside CUDA stream
+ *     capture.  Later calls with the same pattern allocate nothing.
+ *   - One code handle may be used from several threads at once.
+ *   - On failure the call returns a negative PMRC_E* status, writes nothing
+ *     and pmrc_last_error() describes the problem (thread-local).
+ */
+#ifndef PMRC_H
+#define PMRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmrc_code pmrc_code;
+typedef struct CUstream_st *pmrc_stream_t; /* same type as cudaStream_t */
+
+enum {
+  PMRC_OK = 0,
+  PMRC_EINVAL = -1,      /* bad argument (range, NULL, repeated node id)      */
+  PMRC_ESINGULAR = -2,   /* helper set / node set does not determine the data */
+  PMRC_EUNSUPPORTED = -3,/* parameters outside what the construction supports */
+  PMRC_ENOMEM = -4,      /* host or device allocation failed                  */
+  PMRC_ECUDA = -5,       /* a CUDA call failed (message in pmrc_last_error)   */
+  PMRC_ETIMEOUT = -6,    /* a bounded device wait gave up                     */
+  PMRC_EBUSY = -7        /* resource in use (batch/server state)              */
+};
+
+enum { PMRC_VANILLA = 0, PMRC_SPARSE = 1 };            /* Sec. 3.3            */
+enum { PMRC_NONSYSTEMATIC = 0, PMRC_SYSTEMATIC = 1 };  /* Sec. 3.1 / Sec. 3.2 */
+
+/* Builds the code (Phi, Lambda, Psi, L, G and, for the systematic form,
+ * G' = G G~^-1) on the host and its encode plan.  Host only: works without a
+ * GPU.  d must equal 2k-2 (PMRC_EINVAL otherwise).  Returns
+ * PMRC_EUNSUPPORTED when the construction is not an MSR code in GF(2^8) at
+ * this size (e.g. vanilla with repeated lambda, k=16 n=32).  *out receives
+ * a handle owned by the caller (free with pmrc_destroy). */
+int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out);
+
+/* Frees the handle and its device plans.  The caller makes sure no call on
+ * it is still running on the GPU.  NULL is ignored. */
+void pmrc_destroy(pmrc_code *code);
+
+/* Encode (Sec. 3.1 / 3.2).  data: k*alpha device pointers (X).  out:
+ * non-systematic -> n*alpha pointers, all coded blocks Y = G X;
+ * systematic     -> (n-k)*alpha pointers, the parity blocks G'' X (the first
+ * k*alpha blocks of Y are the data itself).  NULL entries of out are
+ * skipped. */
+int pmrc_encode(const pmrc_code *code, const uint8_t *const *data, uint8_t *const *out,
+                size_t block_bytes, pmrc_stream_t stream);
+
+/* Helper side of repairing node `failed` (Sec. 3.3): node `helper` sends
+ * p = sum_j phi_failed[j] * Y[alpha*helper + j].  helper_blocks: the alpha
+ * blocks the helper stores; entries whose coefficient is zero are never
+ * read and may be NULL (sparse code: a failed node among the alpha first
+ * needs one block).  out: one block. */
+int pmrc_repair_helper(const pmrc_code *code, int failed, int helper,
+                       const uint8_t *const *helper_blocks, uint8_t *out, size_t block_bytes,
+                       pmrc_stream_t stream);
+
+/* The same projection for nhelpers helpers in one launch.  helper_blocks:
+ * nhelpers*alpha pointers (helper h's blocks at [h*alpha, h*alpha+alpha)),
+ * out: nhelpers pointers.  helpers[] only serves the range checks. */
+int pmrc_repair_helpers(const pmrc_code *code, int failed, int nhelpers, const int *helpers,
+                        const uint8_t *const *helper_blocks, uint8_t *const *out,
+                        size_t block_bytes, pmrc_stream_t stream);
+
+/* Newcomer side of the repair: from the d projected blocks received from
+ * `helpers` (d distinct node ids != failed, host array, same order as
+ * received), rebuild the alpha blocks of node `failed` with
+ * D = [I | lambda_f I] Psi_H^-1.  PMRC_ESINGULAR when the helpers' rows of
+ * Psi are singular (possible at n >= 2k for the sparse code). */
+int pmrc_repair_newcomer(const pmrc_code *code, int failed, const int *helpers,
+                         const uint8_t *const *received, uint8_t *const *out,
+                         size_t block_bytes, pmrc_stream_t stream);
+
+/* Reconstruction from any k nodes (Sec. 2: X = G~^-1 Y~).  nodes: k
+ * distinct node ids (host array).  node_blocks: their k*alpha blocks,
+ * node-major in the order of nodes.  data_out: k*alpha pointers for X; a
+ * NULL entry is not produced, and an entry equal to the node block that
+ * already holds that data block (systematic code) is left in place, so only
+ * the missing blocks are computed (lazy decode, Sec. 3.1). */
+int pmrc_decode(const pmrc_code *code, const int *nodes, const uint8_t *const *node_blocks,
+                uint8_t *const *data_out, size_t block_bytes, pmrc_stream_t stream);
+
+/* Default helpers for node `failed`: the first d-subset of the survivors,
+ * in lexicographic order, whose Psi rows are invertible (the d lowest ids
+ * when they qualify).  helpers_out: d ints. */
+int pmrc_default_helpers(const pmrc_code *code, int failed, int *helpers_out);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *pmrc_last_error(void);
+
+/* ---- host-side introspection (no GPU needed) ---------------------------- */
+
+/* params_out[6] = {n, k, d, alpha, construction, form}. */
+int pmrc_code_params(const pmrc_code *code, int *params_out);
+
+/* The code's generator, n*alpha x k*alpha, row-major: G (non-systematic) or
+ * G' (systematic). */
+int pmrc_code_generator(const pmrc_code *code, uint8_t *g_out);
+
+/* phi_failed (alpha bytes): the helper coefficients of pmrc_repair_helper. */
+int pmrc_helper_coefficients(const pmrc_code *code, int failed, uint8_t *coef_out);
+
+/* D (alpha x d, row-major) applied by pmrc_repair_newcomer. */
+int pmrc_newcomer_matrix(const pmrc_code *code, int failed, const int *helpers, uint8_t *d_out);
+
+/* (k*alpha x k*alpha, row-major) inverse applied by pmrc_decode. */
+int pmrc_decode_matrix(const pmrc_code *code, const int *nodes, uint8_t *r_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMRC_H */

@@ -1,0 +1,281 @@
+"""Python binding of libpmrc: product-matrix MSR regenerating codes on GB300.
+
+Argument marshalling only.  Every function of ``include/pmrc.h`` is exposed
+under the same name; region pointers are device addresses (ints) or CUDA
+tensors (their ``data_ptr()``), pointer arrays are Python sequences, and the
+stream is a ``torch.cuda.Stream``, a raw handle or ``None`` (torch's current
+stream).  A negative status raises :class:`PMRCError` with the library's
+message.  All region work runs in the library's CUDA kernels; there is no
+CPU path.  If ``libpmrc.so`` is missing it is built with nvcc on first use,
+and the import fails loudly if that is impossible.
+
+:class:`Code` wraps a handle for convenience (the same calls as methods).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmrc.so")
+
+PMRC_OK = 0
+PMRC_EINVAL = -1
+PMRC_ESINGULAR = -2
+PMRC_EUNSUPPORTED = -3
+PMRC_ENOMEM = -4
+PMRC_ECUDA = -5
+PMRC_ETIMEOUT = -6
+PMRC_EBUSY = -7
+
+PMRC_VANILLA = 0
+PMRC_SPARSE = 1
+PMRC_NONSYSTEMATIC = 0
+PMRC_SYSTEMATIC = 1
+
+_STATUS = {v: k for k, v in dict(globals()).items() if k.startswith("PMRC_E")}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PMRCError(RuntimeError):
+    def __init__(self, rc: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(rc, rc)} ({msg})")
+        self.rc = rc
+
+
+_i = ctypes.c_int
+_sz = ctypes.c_size_t
+_vp = ctypes.c_void_p
+_pp = ctypes.POINTER(ctypes.c_void_p)
+_ip = ctypes.POINTER(ctypes.c_int)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+_SIGNATURES = {
+    "pmrc_create": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "pmrc_destroy": (None, [_vp]),
+    "pmrc_encode": (_i, [_vp, _pp, _pp, _sz, _vp]),
+    "pmrc_repair_helper": (_i, [_vp, _i, _i, _pp, _vp, _sz, _vp]),
+    "pmrc_repair_helpers": (_i, [_vp, _i, _i, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_repair_newcomer": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_decode": (_i, [_vp, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_default_helpers": (_i, [_vp, _i, _ip]),
+    "pmrc_last_error": (ctypes.c_char_p, []),
+    "pmrc_code_params": (_i, [_vp, _ip]),
+    "pmrc_code_generator": (_i, [_vp, _u8p]),
+    "pmrc_helper_coefficients": (_i, [_vp, _i, _u8p]),
+    "pmrc_newcomer_matrix": (_i, [_vp, _i, _ip, _u8p]),
+    "pmrc_decode_matrix": (_i, [_vp, _ip, _u8p]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libpmrc.so (built in-tree with nvcc if missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(rc: int, where: str):
+    if rc < 0:
+        raise PMRCError(rc, where, lib().pmrc_last_error().decode())
+    return rc
+
+
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _ptrs(seq):
+    arr = (ctypes.c_void_p * len(seq))()
+    for i, x in enumerate(seq):
+        arr[i] = _addr(x) or None
+    return arr
+
+
+def _ints(seq):
+    arr = (ctypes.c_int * len(seq))()
+    for i, x in enumerate(seq):
+        arr[i] = int(x)
+    return arr
+
+
+def _stream(s) -> int:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_initialized():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- C ABI
+def pmrc_create(n: int, k: int, d: int, construction: int, form: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pmrc_create(n, k, d, construction, form, ctypes.byref(h)), "pmrc_create")
+    return int(h.value)
+
+
+def pmrc_destroy(code: int) -> None:
+    if code:
+        lib().pmrc_destroy(code)
+
+
+def pmrc_encode(code, data, out, block_bytes, stream=None) -> None:
+    _check(lib().pmrc_encode(code, _ptrs(data), _ptrs(out), block_bytes, _stream(stream)),
+           "pmrc_encode")
+
+
+def pmrc_repair_helper(code, failed, helper, helper_blocks, out, block_bytes, stream=None):
+    _check(lib().pmrc_repair_helper(code, failed, helper, _ptrs(helper_blocks), _addr(out),
+                                    block_bytes, _stream(stream)), "pmrc_repair_helper")
+
+
+def pmrc_repair_helpers(code, failed, helpers, helper_blocks, out, block_bytes, stream=None):
+    _check(lib().pmrc_repair_helpers(code, failed, len(out), _ints(helpers),
+                                     _ptrs(helper_blocks), _ptrs(out), block_bytes,
+                                     _stream(stream)), "pmrc_repair_helpers")
+
+
+def pmrc_repair_newcomer(code, failed, helpers, received, out, block_bytes, stream=None):
+    _check(lib().pmrc_repair_newcomer(code, failed, _ints(helpers), _ptrs(received), _ptrs(out),
+                                      block_bytes, _stream(stream)), "pmrc_repair_newcomer")
+
+
+def pmrc_decode(code, nodes, node_blocks, data_out, block_bytes, stream=None):
+    _check(lib().pmrc_decode(code, _ints(nodes), _ptrs(node_blocks), _ptrs(data_out),
+                             block_bytes, _stream(stream)), "pmrc_decode")
+
+
+def pmrc_default_helpers(code, failed) -> list:
+    p = pmrc_code_params(code)
+    out = (ctypes.c_int * p["d"])()
+    _check(lib().pmrc_default_helpers(code, failed, out), "pmrc_default_helpers")
+    return list(out)
+
+
+def pmrc_last_error() -> str:
+    return lib().pmrc_last_error().decode()
+
+
+def pmrc_code_params(code) -> dict:
+    out = (ctypes.c_int * 6)()
+    _check(lib().pmrc_code_params(code, out), "pmrc_code_params")
+    return dict(zip(("n", "k", "d", "alpha", "construction", "form"), list(out)))
+
+
+def _u8buf(size):
+    return (ctypes.c_uint8 * size)()
+
+
+def _mat(buf, rows, cols):
+    import numpy as np
+    return np.frombuffer(bytes(buf), dtype=np.uint8).reshape(rows, cols).copy()
+
+
+def pmrc_code_generator(code):
+    p = pmrc_code_params(code)
+    N, K = p["n"] * p["alpha"], p["k"] * p["alpha"]
+    buf = _u8buf(N * K)
+    _check(lib().pmrc_code_generator(code, buf), "pmrc_code_generator")
+    return _mat(buf, N, K)
+
+
+def pmrc_helper_coefficients(code, failed):
+    p = pmrc_code_params(code)
+    buf = _u8buf(p["alpha"])
+    _check(lib().pmrc_helper_coefficients(code, failed, buf), "pmrc_helper_coefficients")
+    return _mat(buf, 1, p["alpha"])[0]
+
+
+def pmrc_newcomer_matrix(code, failed, helpers):
+    p = pmrc_code_params(code)
+    buf = _u8buf(p["alpha"] * p["d"])
+    _check(lib().pmrc_newcomer_matrix(code, failed, _ints(helpers), buf), "pmrc_newcomer_matrix")
+    return _mat(buf, p["alpha"], p["d"])
+
+
+def pmrc_decode_matrix(code, nodes):
+    p = pmrc_code_params(code)
+    K = p["k"] * p["alpha"]
+    buf = _u8buf(K * K)
+    _check(lib().pmrc_decode_matrix(code, _ints(nodes), buf), "pmrc_decode_matrix")
+    return _mat(buf, K, K)
+
+
+# ---------------------------------------------------------------- handle
+class Code:
+    """Owns a pmrc_code handle; methods are the C calls on it."""
+
+    def __init__(self, n: int, k: int, construction: int = PMRC_SPARSE,
+                 form: int = PMRC_SYSTEMATIC):
+        self.handle = pmrc_create(n, k, 2 * k - 2, construction, form)
+        p = pmrc_code_params(self.handle)
+        self.n, self.k, self.d, self.alpha = p["n"], p["k"], p["d"], p["alpha"]
+        self.construction, self.form = construction, form
+
+    def close(self):
+        if self.handle:
+            pmrc_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_outputs(self) -> int:
+        a = self.alpha
+        return (self.n - self.k) * a if self.form == PMRC_SYSTEMATIC else self.n * a
+
+    def encode(self, data, out, block_bytes, stream=None):
+        pmrc_encode(self.handle, data, out, block_bytes, stream)
+
+    def repair_helper(self, failed, helper, blocks, out, block_bytes, stream=None):
+        pmrc_repair_helper(self.handle, failed, helper, blocks, out, block_bytes, stream)
+
+    def repair_helpers(self, failed, helpers, blocks, out, block_bytes, stream=None):
+        pmrc_repair_helpers(self.handle, failed, helpers, blocks, out, block_bytes, stream)
+
+    def repair_newcomer(self, failed, helpers, received, out, block_bytes, stream=None):
+        pmrc_repair_newcomer(self.handle, failed, helpers, received, out, block_bytes, stream)
+
+    def decode(self, nodes, node_blocks, data_out, block_bytes, stream=None):
+        pmrc_decode(self.handle, nodes, node_blocks, data_out, block_bytes, stream)
+
+    def default_helpers(self, failed):
+        return pmrc_default_helpers(self.handle, failed)
+
+    def generator(self):
+        return pmrc_code_generator(self.handle)
+
+    def helper_coefficients(self, failed):
+        return pmrc_helper_coefficients(self.handle, failed)
+
+    def newcomer_matrix(self, failed, helpers):
+        return pmrc_newcomer_matrix(self.handle, failed, helpers)
+
+    def decode_matrix(self, nodes):
+        return pmrc_decode_matrix(self.handle, nodes)

@@ -1,0 +1,288 @@
+// C ABI of libpmrc (include/pmrc.h): argument checks, plan cache, launches.
+#include "../../include/pmrc.h"
+
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+#include "code.h"
+#include "plan.h"
+#include "region.h"
+
+using namespace pmrc;
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int rc, const std::string &msg) {
+  g_last_error = msg;
+  return rc;
+}
+}  // namespace
+
+namespace pmrc {
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+std::shared_ptr<Plan> cached_plan(const pmrc_code *c, const std::string &key,
+                                  const std::function<std::shared_ptr<Plan>()> &make) {
+  std::lock_guard<std::mutex> g(c->mu);
+  auto it = c->cache.find(key);
+  if (it != c->cache.end()) return it->second;
+  auto p = make();
+  if (!p) return p;
+  if (c->cache.size() >= kPlanCacheCap) c->cache.erase(c->cache.begin());
+  c->cache[key] = p;
+  return p;
+}
+
+int helper_plan(const pmrc_code *c, int f, int nh, std::shared_ptr<Plan> &out,
+                std::string &err) {
+  if (f < 0 || f >= c->m.n) {
+    err = "failed node out of range";
+    return kEInval;
+  }
+  const std::string key = "h:" + std::to_string(f) + ":" + std::to_string(nh);
+  out = cached_plan(c, key, [&]() {
+    std::vector<uint8_t> coef;
+    helper_coefficients(c->m, f, coef);
+    const int a = c->m.alpha;
+    Mat M(nh, nh * a);  // block diagonal: helper h reads its own alpha blocks
+    std::vector<int> slot(nh);
+    for (int h = 0; h < nh; h++) {
+      for (int j = 0; j < a; j++) M.at(h, h * a + j) = coef[j];
+      slot[h] = h;
+    }
+    return make_plan(M, slot, nh);
+  });
+  return kOk;
+}
+
+int newcomer_plan(const pmrc_code *c, int f, const int *helpers, std::shared_ptr<Plan> &out,
+                  std::string &err) {
+  std::string key = "n:" + std::to_string(f);
+  for (int i = 0; i < c->m.d; i++) key += "," + std::to_string(helpers[i]);
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) {
+      out = it->second;
+      return kOk;
+    }
+  }
+  Mat D;
+  int rc = newcomer_matrix(c->m, f, helpers, D, err);
+  if (rc) return rc;
+  out = cached_plan(c, key, [&]() {
+    std::vector<int> slot(c->m.alpha);
+    for (int j = 0; j < c->m.alpha; j++) slot[j] = j;
+    return make_plan(D, slot, c->m.alpha);
+  });
+  return kOk;
+}
+
+int decode_plan(const pmrc_code *c, const int *nodes, const std::vector<char> &want,
+                std::shared_ptr<Plan> &out, std::string &err) {
+  const int K = c->m.k * c->m.alpha;
+  std::string key = "d:";
+  for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
+  key += ":";
+  for (int r = 0; r < K; r++) key += want[r] ? '1' : '0';
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->cache.find(key);
+    if (it != c->cache.end()) {
+      out = it->second;
+      return kOk;
+    }
+  }
+  Mat Rinv;
+  int rc = decode_matrix(c->m, nodes, Rinv, err);
+  if (rc) return rc;
+  out = cached_plan(c, key, [&]() {
+    std::vector<int> slot(K);
+    for (int r = 0; r < K; r++) slot[r] = want[r] ? r : -1;
+    return make_plan(Rinv, slot, K);
+  });
+  return kOk;
+}
+
+// Which data rows a decode call must produce: non-NULL outputs, except a
+// systematic data block whose output pointer is the node block holding it.
+int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                  uint8_t *const *data_out, std::vector<char> &want) {
+  const int a = c->m.alpha, K = c->m.k * a;
+  want.assign(K, 0);
+  for (int r = 0; r < K; r++) want[r] = data_out[r] != nullptr;
+  if (c->m.systematic)
+    for (int i = 0; i < c->m.k; i++)
+      if (nodes[i] < c->m.k)
+        for (int j = 0; j < a; j++) {
+          const int r = a * nodes[i] + j;  // data row held by this node block
+          if (data_out[r] == node_blocks[a * i + j]) want[r] = 0;
+        }
+  return kOk;
+}
+
+}  // namespace pmrc
+
+extern "C" {
+
+const char *pmrc_last_error(void) { return g_last_error.c_str(); }
+
+int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out) {
+  if (!out) return fail(PMRC_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<pmrc_code> c(new (std::nothrow) pmrc_code());
+  if (!c) return fail(PMRC_ENOMEM, "out of host memory");
+  std::string err;
+  int rc = build_code(n, k, d, construction, form, c->m, err);
+  if (rc) return fail(rc, err);
+  const int a = c->m.alpha, K = k * a, N = n * a;
+  if (K + (form ? N - K : N) > kMaxSlots)
+    return fail(PMRC_EUNSUPPORTED, "code too large: more than 1024 block pointers per encode");
+  // encode plan: all rows (non-systematic) or the parity rows (systematic)
+  const int first = form ? K : 0;
+  Mat M(N - first, K);
+  std::copy(c->m.Gcode.v.begin() + (size_t)first * K, c->m.Gcode.v.end(), M.v.begin());
+  std::vector<int> slot(N - first);
+  for (int r = 0; r < N - first; r++) slot[r] = r;
+  c->encode = make_plan(M, slot, N - first);
+  *out = c.release();
+  g_last_error.clear();
+  return PMRC_OK;
+}
+
+void pmrc_destroy(pmrc_code *code) { delete code; }
+
+int pmrc_code_params(const pmrc_code *c, int *p) {
+  if (!c || !p) return fail(PMRC_EINVAL, "NULL argument");
+  p[0] = c->m.n;
+  p[1] = c->m.k;
+  p[2] = c->m.d;
+  p[3] = c->m.alpha;
+  p[4] = c->m.construction;
+  p[5] = c->m.systematic;
+  return PMRC_OK;
+}
+
+int pmrc_code_generator(const pmrc_code *c, uint8_t *g) {
+  if (!c || !g) return fail(PMRC_EINVAL, "NULL argument");
+  memcpy(g, c->m.Gcode.v.data(), c->m.Gcode.v.size());
+  return PMRC_OK;
+}
+
+int pmrc_helper_coefficients(const pmrc_code *c, int f, uint8_t *coef) {
+  if (!c || !coef) return fail(PMRC_EINVAL, "NULL argument");
+  if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
+  std::vector<uint8_t> v;
+  helper_coefficients(c->m, f, v);
+  memcpy(coef, v.data(), v.size());
+  return PMRC_OK;
+}
+
+int pmrc_newcomer_matrix(const pmrc_code *c, int f, const int *helpers, uint8_t *d_out) {
+  if (!c || !helpers || !d_out) return fail(PMRC_EINVAL, "NULL argument");
+  Mat D;
+  std::string err;
+  int rc = newcomer_matrix(c->m, f, helpers, D, err);
+  if (rc) return fail(rc, err);
+  memcpy(d_out, D.v.data(), D.v.size());
+  return PMRC_OK;
+}
+
+int pmrc_decode_matrix(const pmrc_code *c, const int *nodes, uint8_t *r_out) {
+  if (!c || !nodes || !r_out) return fail(PMRC_EINVAL, "NULL argument");
+  Mat R;
+  std::string err;
+  int rc = decode_matrix(c->m, nodes, R, err);
+  if (rc) return fail(rc, err);
+  memcpy(r_out, R.v.data(), R.v.size());
+  return PMRC_OK;
+}
+
+int pmrc_default_helpers(const pmrc_code *c, int f, int *helpers_out) {
+  if (!c || !helpers_out) return fail(PMRC_EINVAL, "NULL argument");
+  std::string err;
+  int rc = default_helpers(c->m, f, helpers_out, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int pmrc_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                size_t nbytes, pmrc_stream_t stream) {
+  if (!c || !data || !out) return fail(PMRC_EINVAL, "NULL argument");
+  std::string err;
+  int rc = launch_region(*c->encode, data, out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int pmrc_repair_helpers(const pmrc_code *c, int f, int nh, const int *helpers,
+                        const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
+                        pmrc_stream_t stream) {
+  if (!c || !blocks || !out || nh <= 0 || (nh > 1 && !helpers))
+    return fail(PMRC_EINVAL, "NULL argument or nhelpers <= 0");
+  if (nh * (c->m.alpha + 1) > kMaxSlots) return fail(PMRC_EUNSUPPORTED, "too many helpers");
+  if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
+  if (helpers)
+    for (int h = 0; h < nh; h++)
+      if (helpers[h] < 0 || helpers[h] >= c->m.n || helpers[h] == f)
+        return fail(PMRC_EINVAL, "helper id out of range or equal to the failed node");
+  for (int h = 0; h < nh; h++)
+    if (!out[h]) return fail(PMRC_EINVAL, "output block is NULL");
+  std::shared_ptr<Plan> p;
+  std::string err;
+  int rc = helper_plan(c, f, nh, p, err);
+  if (rc) return fail(rc, err);
+  rc = launch_region(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int pmrc_repair_helper(const pmrc_code *c, int f, int helper, const uint8_t *const *blocks,
+                       uint8_t *out, size_t nbytes, pmrc_stream_t stream) {
+  if (!out) return fail(PMRC_EINVAL, "output block is NULL");
+  return pmrc_repair_helpers(c, f, 1, &helper, blocks, &out, nbytes, stream);
+}
+
+int pmrc_repair_newcomer(const pmrc_code *c, int f, const int *helpers,
+                         const uint8_t *const *received, uint8_t *const *out, size_t nbytes,
+                         pmrc_stream_t stream) {
+  if (!c || !helpers || !received || !out) return fail(PMRC_EINVAL, "NULL argument");
+  for (int j = 0; j < c->m.alpha; j++)
+    if (!out[j]) return fail(PMRC_EINVAL, "output block is NULL");
+  std::shared_ptr<Plan> p;
+  std::string err;
+  int rc = newcomer_plan(c, f, helpers, p, err);
+  if (rc) return fail(rc, err);
+  rc = launch_region(*p, received, out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream) {
+  if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
+  {
+    std::vector<char> seen(c->m.n, 0);
+    for (int i = 0; i < c->m.k; i++) {
+      if (nodes[i] < 0 || nodes[i] >= c->m.n || seen[nodes[i]])
+        return fail(PMRC_EINVAL, "nodes: out of range or repeated node id");
+      seen[nodes[i]] = 1;
+    }
+  }
+  std::vector<char> want;
+  decode_wanted(c, nodes, node_blocks, data_out, want);
+  std::shared_ptr<Plan> p;
+  std::string err;
+  int rc = decode_plan(c, nodes, want, p, err);
+  if (rc) return fail(rc, err);
+  rc = launch_region(*p, node_blocks, data_out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+}  // extern "C"

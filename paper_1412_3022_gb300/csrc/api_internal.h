@@ -1,0 +1,37 @@
+// Internal view of the code handle, shared by the C ABI and the batching
+// and serving layers.
+#pragma once
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "code.h"
+#include "plan.h"
+
+struct pmrc_code {
+  pmrc::CodeMatrices m;
+  std::shared_ptr<pmrc::Plan> encode;  // built at create
+  mutable std::mutex mu;               // guards cache
+  mutable std::map<std::string, std::shared_ptr<pmrc::Plan>> cache;
+};
+
+namespace pmrc {
+
+constexpr size_t kPlanCacheCap = 4096;
+
+void set_last_error(const std::string &msg);
+
+std::shared_ptr<Plan> cached_plan(const pmrc_code *c, const std::string &key,
+                                  const std::function<std::shared_ptr<Plan>()> &make);
+int helper_plan(const pmrc_code *c, int f, int nh, std::shared_ptr<Plan> &out, std::string &err);
+int newcomer_plan(const pmrc_code *c, int f, const int *helpers, std::shared_ptr<Plan> &out,
+                  std::string &err);
+int decode_plan(const pmrc_code *c, const int *nodes, const std::vector<char> &want,
+                std::shared_ptr<Plan> &out, std::string &err);
+int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                  uint8_t *const *data_out, std::vector<char> &want);
+
+}  // namespace pmrc

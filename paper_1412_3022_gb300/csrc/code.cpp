@@ -1,0 +1,245 @@
+// Host construction of PM-MSR codes (see code.h for the paper sections).
+#include "code.h"
+
+#include <algorithm>
+
+#include "gf256.h"
+
+namespace pmrc {
+
+Mat mat_mul(const Mat &A, const Mat &B) {
+  Mat C(A.rows, B.cols);
+  const auto &T = mul_table().t;
+  for (int i = 0; i < A.rows; i++)
+    for (int l = 0; l < A.cols; l++) {
+      uint8_t a = A.at(i, l);
+      if (!a) continue;
+      const uint8_t *row = T[a];
+      for (int j = 0; j < B.cols; j++) C.at(i, j) ^= row[B.at(l, j)];
+    }
+  return C;
+}
+
+bool mat_inverse(const Mat &A, Mat &out) {
+  const int m = A.rows;
+  if (m != A.cols || m <= 0) return false;
+  const auto &T = mul_table().t;
+  Mat W(m, 2 * m);
+  for (int i = 0; i < m; i++) {
+    for (int j = 0; j < m; j++) W.at(i, j) = A.at(i, j);
+    W.at(i, m + i) = 1;
+  }
+  for (int c = 0; c < m; c++) {
+    int p = c;
+    while (p < m && W.at(p, c) == 0) p++;
+    if (p == m) return false;
+    if (p != c)
+      for (int j = 0; j < 2 * m; j++) std::swap(W.at(p, j), W.at(c, j));
+    const uint8_t *s = T[gf_inv(W.at(c, c))];
+    for (int j = 0; j < 2 * m; j++) W.at(c, j) = s[W.at(c, j)];
+    for (int r = 0; r < m; r++) {
+      uint8_t f = W.at(r, c);
+      if (r == c || !f) continue;
+      const uint8_t *fr = T[f];
+      for (int j = 0; j < 2 * m; j++) W.at(r, j) ^= fr[W.at(c, j)];
+    }
+  }
+  out = Mat(m, m);
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < m; j++) out.at(i, j) = W.at(i, m + j);
+  return true;
+}
+
+static uint8_t gpow(unsigned e) { return gf_pow(2, e % 255); }
+
+int build_code(int n, int k, int d, int construction, int systematic, CodeMatrices &c,
+               std::string &err) {
+  if (k < 2 || d != 2 * k - 2) {
+    err = "PM-MSR needs k >= 2 and d = 2k-2";
+    return kEInval;
+  }
+  if (n < d + 1 || n > 254) {
+    err = "n must satisfy 2k-1 <= n <= 254";
+    return kEInval;
+  }
+  if (construction != 0 && construction != 1) {
+    err = "construction must be PMRC_VANILLA or PMRC_SPARSE";
+    return kEInval;
+  }
+  if (systematic != 0 && systematic != 1) {
+    err = "form must be PMRC_NONSYSTEMATIC or PMRC_SYSTEMATIC";
+    return kEInval;
+  }
+  const int a = k - 1;
+  c.n = n;
+  c.k = k;
+  c.d = d;
+  c.alpha = a;
+  c.construction = construction;
+  c.systematic = systematic;
+  c.phi = Mat(n, a);
+  c.lambda.assign(n, 0);
+  if (construction == 0) {
+    // Vandermonde: Phi_ij = g^(i j), lambda_i = g^(i alpha) (0-based), so
+    // that Psi_il = g^(i l) (Sec. 3.3, printed n=5 example).
+    for (int i = 0; i < n; i++) {
+      for (int j = 0; j < a; j++) c.phi.at(i, j) = gpow((unsigned)(i * j));
+      c.lambda[i] = gpow((unsigned)(i * a));
+    }
+  } else {
+    // Sparse: identity on the first alpha rows, Cauchy below; 1-based
+    // i, j as in Sec. 3.3:  Phi_ij = (g^(i+alpha) + g^(j-1))^-1 for i > alpha,
+    // lambda_i = (g^(i+alpha) + 1) / (g^(i+alpha) + g^alpha).
+    for (int i = 1; i <= n; i++) {
+      const uint8_t z = gpow((unsigned)(i + a));
+      for (int j = 1; j <= a; j++)
+        c.phi.at(i - 1, j - 1) = (i <= a) ? (uint8_t)(i == j) : gf_inv(z ^ gpow((unsigned)(j - 1)));
+      c.lambda[i - 1] = gmul(z ^ 1, gf_inv(z ^ gpow((unsigned)a)));
+    }
+  }
+  {
+    std::vector<uint8_t> s = c.lambda;
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end()) {
+      err = "construction has repeated lambda values at this (n, k): not an MSR code in GF(2^8)";
+      return kEUnsupported;
+    }
+  }
+  c.psi = Mat(n, d);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < a; j++) {
+      c.psi.at(i, j) = c.phi.at(i, j);
+      c.psi.at(i, a + j) = gmul(c.lambda[i], c.phi.at(i, j));
+    }
+  // Index matrix (Sec. 3.1): upper triangles of S1 then S2 numbered row by
+  // row; M = [S1; S2] is d x alpha with symmetric blocks.
+  c.L.assign((size_t)d * a, 0);
+  {
+    std::vector<int> tri((size_t)a * a, 0);
+    int next = 0;
+    for (int r = 0; r < a; r++)
+      for (int q = r; q < a; q++) tri[(size_t)r * a + q] = tri[(size_t)q * a + r] = next++;
+    const int half = next;
+    for (int r = 0; r < a; r++)
+      for (int q = 0; q < a; q++) {
+        c.L[(size_t)r * a + q] = tri[(size_t)r * a + q];
+        c.L[(size_t)(a + r) * a + q] = half + tri[(size_t)r * a + q];
+      }
+  }
+  const int K = k * a, N = n * a;
+  c.G = Mat(N, K);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < a; j++)
+      for (int l = 0; l < d; l++) c.G.at(a * i + j, c.L[(size_t)l * a + j]) = c.psi.at(i, l);
+  if (!systematic) {
+    c.Gcode = c.G;
+  } else {
+    Mat top(K, K), topinv;
+    std::copy(c.G.v.begin(), c.G.v.begin() + (size_t)K * K, top.v.begin());
+    if (!mat_inverse(top, topinv)) {
+      err = "the first k nodes do not determine the data: no systematic form";
+      return kEUnsupported;
+    }
+    c.Gcode = mat_mul(c.G, topinv);
+  }
+  return kOk;
+}
+
+void helper_coefficients(const CodeMatrices &c, int f, std::vector<uint8_t> &coef) {
+  coef.assign(c.phi.v.begin() + (size_t)f * c.alpha, c.phi.v.begin() + (size_t)(f + 1) * c.alpha);
+}
+
+static int check_distinct(const int *ids, int cnt, int n, int exclude, std::string &err,
+                          const char *what) {
+  std::vector<char> seen(n, 0);
+  for (int i = 0; i < cnt; i++) {
+    if (ids[i] < 0 || ids[i] >= n) {
+      err = std::string(what) + ": node id out of range";
+      return kEInval;
+    }
+    if (ids[i] == exclude) {
+      err = std::string(what) + ": the failed node cannot help";
+      return kEInval;
+    }
+    if (seen[ids[i]]) {
+      err = std::string(what) + ": repeated node id";
+      return kEInval;
+    }
+    seen[ids[i]] = 1;
+  }
+  return kOk;
+}
+
+int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, std::string &err) {
+  if (f < 0 || f >= c.n) {
+    err = "failed node out of range";
+    return kEInval;
+  }
+  int rc = check_distinct(helpers, c.d, c.n, f, err, "helpers");
+  if (rc) return rc;
+  Mat PH(c.d, c.d), inv;
+  for (int i = 0; i < c.d; i++)
+    for (int l = 0; l < c.d; l++) PH.at(i, l) = c.psi.at(helpers[i], l);
+  if (!mat_inverse(PH, inv)) {
+    err = "the helpers' rows of Psi are singular for this failed node";
+    return kESingular;
+  }
+  // Psi_H M phi_f = p  =>  M phi_f = Psi_H^-1 p = [S1 phi_f; S2 phi_f];
+  // node f stores phi_f^t S1 + lambda_f phi_f^t S2 (S1, S2 symmetric).
+  const int a = c.alpha;
+  D = Mat(a, c.d);
+  const uint8_t lf = c.lambda[f];
+  for (int j = 0; j < a; j++)
+    for (int q = 0; q < c.d; q++) D.at(j, q) = inv.at(j, q) ^ gmul(lf, inv.at(a + j, q));
+  return kOk;
+}
+
+int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err) {
+  int rc = check_distinct(nodes, c.k, c.n, -1, err, "nodes");
+  if (rc) return rc;
+  const int a = c.alpha, K = c.k * a;
+  Mat GR(K, K);
+  for (int i = 0; i < c.k; i++)
+    for (int j = 0; j < a; j++)
+      std::copy(c.Gcode.v.begin() + (size_t)(a * nodes[i] + j) * K,
+                c.Gcode.v.begin() + (size_t)(a * nodes[i] + j + 1) * K,
+                GR.v.begin() + (size_t)(a * i + j) * K);
+  if (!mat_inverse(GR, Rinv)) {
+    err = "these k nodes do not determine the data";
+    return kESingular;
+  }
+  return kOk;
+}
+
+int default_helpers(const CodeMatrices &c, int f, int *out, std::string &err) {
+  if (f < 0 || f >= c.n) {
+    err = "failed node out of range";
+    return kEInval;
+  }
+  std::vector<int> surv;
+  for (int i = 0; i < c.n; i++)
+    if (i != f) surv.push_back(i);
+  const int m = (int)surv.size(), d = c.d;
+  // Combinations of d survivors in lexicographic order: the first is the d
+  // lowest-index survivors.
+  std::vector<int> idx(d);
+  for (int i = 0; i < d; i++) idx[i] = i;
+  for (int tries = 0; tries < 100000; tries++) {
+    Mat PH(d, d), inv;
+    for (int i = 0; i < d; i++)
+      for (int l = 0; l < d; l++) PH.at(i, l) = c.psi.at(surv[idx[i]], l);
+    if (mat_inverse(PH, inv)) {
+      for (int i = 0; i < d; i++) out[i] = surv[idx[i]];
+      return kOk;
+    }
+    int p = d - 1;
+    while (p >= 0 && idx[p] == m - d + p) p--;
+    if (p < 0) break;
+    idx[p]++;
+    for (int q = p + 1; q < d; q++) idx[q] = idx[q - 1] + 1;
+  }
+  err = "no invertible helper set found for this failed node";
+  return kESingular;
+}
+
+}  // namespace pmrc

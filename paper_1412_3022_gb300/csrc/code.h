@@ -1,0 +1,73 @@
+// Host-side construction of product-matrix MSR codes and of the small
+// matrices each region operation applies.
+//
+//   Sec. 2    erasure code as a linear map, MSR point alpha = d-k+1
+//   Sec. 3.1  linearization: generator G from Psi and the index matrix L
+//   Sec. 3.2  systematic form G' = G * G~^-1 = [I; G'']
+//   Sec. 3.3  Psi = [Phi  Lambda*Phi], vanilla (Vandermonde) and sparse
+//             (identity + Cauchy) constructions; helper read reduction
+//
+// All matrices are row-major uint8 over GF(2^8) (modulus 0x11D).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pmrc {
+
+enum Status {
+  kOk = 0,
+  kEInval = -1,
+  kESingular = -2,
+  kEUnsupported = -3,
+  kENoMem = -4,
+  kECuda = -5,
+  kETimeout = -6,
+  kEBusy = -7,
+};
+
+struct Mat {
+  int rows = 0, cols = 0;
+  std::vector<uint8_t> v;
+  Mat() = default;
+  Mat(int r, int c) : rows(r), cols(c), v((size_t)r * c, 0) {}
+  uint8_t &at(int r, int c) { return v[(size_t)r * cols + c]; }
+  uint8_t at(int r, int c) const { return v[(size_t)r * cols + c]; }
+};
+
+Mat mat_mul(const Mat &A, const Mat &B);
+// Gauss-Jordan inverse; returns false if A is singular.
+bool mat_inverse(const Mat &A, Mat &out);
+
+struct CodeMatrices {
+  int n = 0, k = 0, d = 0, alpha = 0;
+  int construction = 0;  // 0 vanilla, 1 sparse
+  int systematic = 0;
+  Mat phi;      // n x alpha
+  std::vector<uint8_t> lambda;  // n
+  Mat psi;      // n x d
+  std::vector<int> L;           // d x alpha index matrix
+  Mat G;        // n*alpha x k*alpha, linearized generator (Sec. 3.1)
+  Mat Gcode;    // the code's generator: G, or G' = G G~^-1 when systematic
+};
+
+// Builds every matrix of the code.  Returns kEInval for bad parameters,
+// kEUnsupported when the construction is not an MSR code in GF(2^8) at this
+// size (repeated lambda, or G~ singular for the systematic form).
+int build_code(int n, int k, int d, int construction, int systematic, CodeMatrices &out,
+               std::string &err);
+
+// Repair (Sec. 3.3 read pattern; product-matrix repair): the helper
+// coefficients are phi_f; the newcomer applies D = [I | lambda_f I] Psi_H^-1.
+void helper_coefficients(const CodeMatrices &c, int f, std::vector<uint8_t> &coef);
+int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, std::string &err);
+
+// Reconstruction from k nodes (Sec. 2): rows of (Gcode restricted to the
+// nodes' rows)^-1.  `wanted[r]` selects the data rows to produce.
+int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err);
+
+// Default helper set for node f: the d lowest-index survivors, or the first
+// set (in that order of preference) whose Psi rows are invertible.
+int default_helpers(const CodeMatrices &c, int f, int *helpers_out, std::string &err);
+
+}  // namespace pmrc

@@ -1,0 +1,60 @@
+// Region plans: a GF(2^8) matrix M (rows x cols) cut into dense blocks for
+// the region kernel, out[r] = sum_c M[r][c] * in[c] over byte blocks
+// (Sec. 2: every operation of the code is Y = M X for some small M).
+//
+// Rows of a product-matrix generator that belong to the same slot j use the
+// same inputs (the symbols of column j of the message matrix, Sec. 3.1), so
+// grouping rows by their non-zero columns gives dense row x input blocks.
+// Each input of a block is loaded and split once and then multiplied into
+// every row of the block held in registers.
+#pragma once
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "code.h"
+
+namespace pmrc {
+
+constexpr int kMaxBlockRows = 16;   // rows held in registers per block
+constexpr int kMaxSlots = 1024;     // input + output pointers per launch
+
+// Device image of one block (the arrays live in the same allocation).
+struct BlockDesc {
+  uint32_t in_off;    // index into the uint16 array: input slots
+  uint32_t out_off;   // index into the uint16 array: output slots
+  uint32_t coef_off;  // byte offset into the coefficient array (ninputs x R)
+  uint16_t nrows;
+  uint16_t ninputs;
+};
+
+struct PlanBlock {
+  std::vector<uint16_t> rows;    // output slots
+  std::vector<uint16_t> inputs;  // input slots
+  std::vector<uint8_t> coef;     // inputs.size() x R, input-major
+};
+
+struct Plan {
+  int nin = 0, nout = 0;  // slots the caller supplies
+  int R = 1;              // rows per block in the kernel (1, 2, 4, 8 or 16)
+  int max_inputs = 0;     // largest block input count (shared-memory staging)
+  int64_t nnz = 0;        // non-zero coefficients (work per byte)
+  std::vector<PlanBlock> blocks;
+  std::vector<uint8_t> image;  // BlockDesc[] | uint16 slots | coefficients
+  size_t coef_base = 0, idx_base = 0;
+  // per-device copies of `image`
+  std::mutex mu;
+  std::map<int, void *> dev;
+  ~Plan();
+  // Returns the device copy for the current device (uploads on first use).
+  int device_image(const void **out, std::string &err);
+};
+
+// out_slot[r] is the output slot of row r (or -1 to skip the row).  Input
+// slots are the columns of M; in the device image output slots are stored
+// after them (slot index = M.cols + out_slot).
+std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, int nout);
+
+}  // namespace pmrc

@@ -1,0 +1,110 @@
+"""CPU-only checks of libpmrc: it builds and loads, exports every symbol its
+header declares, and its host-side matrices (generator, systematic form,
+helper coefficients, newcomer and decode matrices) equal the oracle's byte
+for byte.  No GPU work is launched here."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1412_3022_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pmrc_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.lib()
+    names = header_functions()
+    assert "pmrc_create" in names and "pmrc_decode" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+CODES = [(5, 3), (6, 3), (8, 4), (16, 8), (24, 12), (32, 16), (9, 5)]
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("cons", [0, 1])
+@pytest.mark.parametrize("n,k", CODES)
+def test_generator_matches_oracle(n, k, cons, form):
+    if cons == 0 and (n, k) == (32, 16):
+        with pytest.raises(P.PMRCError) as e:
+            P.Code(n, k, cons, form)
+        assert e.value.rc == P.PMRC_EUNSUPPORTED
+        return
+    c = P.Code(n, k, cons, form)
+    assert np.array_equal(c.generator(), O.generator(n, k, cons, systematic=bool(form)))
+
+
+@pytest.mark.parametrize("cons", [0, 1])
+@pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (16, 8)])
+def test_repair_and_decode_matrices_match_oracle(n, k, cons):
+    c = P.Code(n, k, cons, 1)
+    d = 2 * k - 2
+    rng = np.random.default_rng(n * 100 + k)
+    for f in range(n):
+        assert np.array_equal(c.helper_coefficients(f), O.helper_coefficients(n, k, cons, f))
+        H = c.default_helpers(f)
+        assert len(H) == d and f not in H and len(set(H)) == d
+        assert np.array_equal(c.newcomer_matrix(f, H), O.newcomer_matrix(n, k, cons, f, H))
+        Hs = list(rng.permutation(H))
+        assert np.array_equal(c.newcomer_matrix(f, Hs), O.newcomer_matrix(n, k, cons, f, Hs))
+    subsets = list(itertools.combinations(range(n), k))
+    for i in rng.choice(len(subsets), min(30, len(subsets)), replace=False):
+        S = list(subsets[i])
+        assert np.array_equal(c.decode_matrix(S), O.decode_matrix(n, k, cons, True, S))
+
+
+@pytest.mark.parametrize("k", [3, 4, 8, 12, 16])
+def test_default_helpers_valid_for_every_node(k):
+    n = 2 * k
+    c = P.Code(n, k, 1, 1)
+    for f in range(n):
+        H = c.default_helpers(f)
+        O.newcomer_matrix(n, k, 1, f, H)  # the oracle agrees it is invertible
+
+
+def test_error_statuses():
+    with pytest.raises(P.PMRCError) as e:
+        P.pmrc_create(16, 8, 13, 1, 1)          # d != 2k-2
+    assert e.value.rc == P.PMRC_EINVAL
+    with pytest.raises(P.PMRCError) as e:
+        P.pmrc_create(14, 8, 14, 1, 1)          # n < 2k-1
+    assert e.value.rc == P.PMRC_EINVAL
+    with pytest.raises(P.PMRCError) as e:
+        P.pmrc_create(16, 8, 14, 2, 1)          # construction
+    assert e.value.rc == P.PMRC_EINVAL
+    c = P.Code(8, 4, 1, 1)
+    with pytest.raises(P.PMRCError) as e:
+        c.newcomer_matrix(0, [1, 1, 2, 3, 4, 5])  # repeated helper
+    assert e.value.rc == P.PMRC_EINVAL
+    with pytest.raises(P.PMRCError) as e:
+        c.newcomer_matrix(0, [0, 1, 2, 3, 4, 5])  # failed node helps
+    assert e.value.rc == P.PMRC_EINVAL
+    with pytest.raises(P.PMRCError) as e:
+        c.newcomer_matrix(0, [2, 3, 4, 5, 6, 7])  # leaves out 0 and 1 (both < alpha)
+    assert e.value.rc == P.PMRC_ESINGULAR
+    with pytest.raises(P.PMRCError) as e:
+        c.decode_matrix([0, 1, 2, 2])
+    assert e.value.rc == P.PMRC_EINVAL
+    assert "repeated" in P.pmrc_last_error()
+    # calls that validate before touching the GPU
+    with pytest.raises(P.PMRCError) as e:
+        c.repair_newcomer(0, [2, 3, 4, 5, 6, 7], [0] * 6, [0] * 3, 16)
+    assert e.value.rc == P.PMRC_EINVAL  # NULL outputs are rejected first
+    with pytest.raises(P.PMRCError) as e:
+        c.decode([0, 1, 2, 9], [0] * 12, [0] * 12, 16)
+    assert e.value.rc == P.PMRC_EINVAL
