@@ -143,6 +143,13 @@ int pmrc_newcomer_matrix(const pmrc_code *code, int failed, const int *helpers, 
 /* (k*alpha x k*alpha, row-major) inverse applied by pmrc_decode. */
 int pmrc_decode_matrix(const pmrc_code *code, const int *nodes, uint8_t *r_out);
 
+/* How the region kernel would cut the rows x cols matrix m (row-major, host)
+ * into dense blocks: stats_out[5] = {blocks, rows per block held in
+ * registers (R), products per byte column (entries, zeros included), input
+ * splits per byte column (sum of block input counts), non-zero
+ * coefficients}. */
+int pmrc_plan_stats(int rows, int cols, const uint8_t *m, int64_t *stats_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "pmrc_helper_coefficients": (_i, [_vp, _i, _u8p]),
     "pmrc_newcomer_matrix": (_i, [_vp, _i, _ip, _u8p]),
     "pmrc_decode_matrix": (_i, [_vp, _ip, _u8p]),
+    "pmrc_plan_stats": (_i, [_i, _i, _u8p, ctypes.POINTER(ctypes.c_int64)]),
 }
 
 
@@ -221,6 +222,15 @@ def pmrc_decode_matrix(code, nodes):
     buf = _u8buf(K * K)
     _check(lib().pmrc_decode_matrix(code, _ints(nodes), buf), "pmrc_decode_matrix")
     return _mat(buf, K, K)
+
+
+def pmrc_plan_stats(m) -> dict:
+    import numpy as np
+    m = np.ascontiguousarray(m, dtype=np.uint8)
+    out = (ctypes.c_int64 * 5)()
+    _check(lib().pmrc_plan_stats(m.shape[0], m.shape[1],
+                                 m.ctypes.data_as(_u8p), out), "pmrc_plan_stats")
+    return dict(zip(("blocks", "R", "entries", "input_splits", "nnz"), list(out)))
 
 
 # ---------------------------------------------------------------- handle

@@ -208,6 +208,26 @@ int pmrc_decode_matrix(const pmrc_code *c, const int *nodes, uint8_t *r_out) {
   return PMRC_OK;
 }
 
+int pmrc_plan_stats(int rows, int cols, const uint8_t *m, int64_t *st) {
+  if (rows <= 0 || cols <= 0 || !m || !st) return fail(PMRC_EINVAL, "bad matrix");
+  Mat M(rows, cols);
+  memcpy(M.v.data(), m, (size_t)rows * cols);
+  std::vector<int> slot(rows);
+  for (int r = 0; r < rows; r++) slot[r] = r;
+  auto p = make_plan(M, slot, rows);
+  int64_t ent = 0, ins = 0;
+  for (auto &b : p->blocks) {
+    ent += (int64_t)b.inputs.size() * b.rows.size();
+    ins += (int64_t)b.inputs.size();
+  }
+  st[0] = (int64_t)p->blocks.size();
+  st[1] = p->R;
+  st[2] = ent;
+  st[3] = ins;
+  st[4] = p->nnz;
+  return PMRC_OK;
+}
+
 int pmrc_default_helpers(const pmrc_code *c, int f, int *helpers_out) {
   if (!c || !helpers_out) return fail(PMRC_EINVAL, "NULL argument");
   std::string err;

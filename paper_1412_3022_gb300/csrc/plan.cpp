@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include "gf256.h"
+
 namespace pmrc {
 
 Plan::~Plan() {
@@ -75,47 +77,57 @@ std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, 
       it->second.push_back(r);
     }
   }
-  // 2. cut groups into blocks of at most kMaxBlockRows rows.  Groups of a
-  // single row or two (sparse, unstructured matrices) are merged with their
-  // neighbours: a shared input is then split once for several rows, and a
-  // zero coefficient costs only a skipped branch in the kernel.
+  // 2. merge groups into blocks of at most kMaxBlockRows rows.  A block
+  // costs kSplitCost per input (load + bit-field split, shared by its rows)
+  // plus one product per (row, input) -- zero coefficients included, since
+  // the kernel does not branch on them.  Pairs of blocks are merged greedily
+  // while that lowers the total cost, so rows with the same or largely
+  // overlapping inputs share the input splits, and rows with disjoint
+  // inputs (block-diagonal matrices) stay apart.
   struct Proto {
     std::vector<int> rows;
-    std::vector<uint16_t> inputs;
+    std::vector<char> used;  // input columns
+    int ninputs = 0;
   };
+  constexpr double kSplitCost = 1.5;
+  auto cost = [&](int rows, int inputs) { return inputs * kSplitCost + (double)rows * inputs; };
   std::vector<Proto> protos;
-  size_t total_rows = 0;
-  for (auto &s : order) total_rows += groups[s].size();
-  const bool merge = !order.empty() && total_rows < 3 * order.size();
-  if (!merge) {
-    for (auto &s : order) {
-      auto &rows = groups[s];
-      const int nblk = (int)((rows.size() + kMaxBlockRows - 1) / kMaxBlockRows);
-      // balance rows over the blocks of a group
-      for (int b = 0; b < nblk; b++) {
-        Proto p;
-        size_t lo = rows.size() * b / nblk, hi = rows.size() * (b + 1) / nblk;
-        p.rows.assign(rows.begin() + lo, rows.begin() + hi);
-        p.inputs = s;
-        protos.push_back(std::move(p));
-      }
-    }
-  } else {
-    std::vector<int> rows;
-    for (auto &s : order)
-      for (int r : groups[s]) rows.push_back(r);
-    for (size_t lo = 0; lo < rows.size(); lo += kMaxBlockRows) {
+  for (auto &sup : order) {
+    auto &rows = groups[sup];
+    const int nblk = (int)((rows.size() + kMaxBlockRows - 1) / kMaxBlockRows);
+    for (int b = 0; b < nblk; b++) {  // balance rows over the blocks of a group
       Proto p;
-      size_t hi = std::min(rows.size(), lo + kMaxBlockRows);
+      size_t lo = rows.size() * b / nblk, hi = rows.size() * (b + 1) / nblk;
       p.rows.assign(rows.begin() + lo, rows.begin() + hi);
-      std::vector<char> used(M.cols, 0);
-      for (int r : p.rows)
-        for (int c = 0; c < M.cols; c++)
-          if (M.at(r, c)) used[c] = 1;
-      for (int c = 0; c < M.cols; c++)
-        if (used[c]) p.inputs.push_back((uint16_t)c);
+      p.used.assign(M.cols, 0);
+      for (uint16_t c : sup) p.used[c] = 1;
+      p.ninputs = (int)sup.size();
       protos.push_back(std::move(p));
     }
+  }
+  for (;;) {
+    double best = 0;
+    int bi = -1, bj = -1;
+    for (size_t i = 0; i < protos.size(); i++)
+      for (size_t j = i + 1; j < protos.size(); j++) {
+        const int r = (int)(protos[i].rows.size() + protos[j].rows.size());
+        if (r > kMaxBlockRows) continue;
+        int u = 0;
+        for (int c = 0; c < M.cols; c++) u += protos[i].used[c] | protos[j].used[c];
+        const double gain = cost((int)protos[i].rows.size(), protos[i].ninputs) +
+                            cost((int)protos[j].rows.size(), protos[j].ninputs) - cost(r, u);
+        if (gain > best) {
+          best = gain;
+          bi = (int)i;
+          bj = (int)j;
+        }
+      }
+    if (bi < 0) break;
+    Proto &A = protos[bi], &Bp = protos[bj];
+    A.rows.insert(A.rows.end(), Bp.rows.begin(), Bp.rows.end());
+    A.ninputs = 0;
+    for (int c = 0; c < M.cols; c++) A.ninputs += (A.used[c] |= Bp.used[c]);
+    protos.erase(protos.begin() + bj);
   }
   int maxr = 1;
   for (auto &p : protos) maxr = std::max(maxr, (int)p.rows.size());
@@ -124,25 +136,29 @@ std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, 
   for (auto &p : protos) {
     PlanBlock b;
     for (int r : p.rows) b.rows.push_back((uint16_t)(M.cols + out_slot[r]));
-    plan->max_inputs = std::max(plan->max_inputs, (int)p.inputs.size());
-    b.inputs = p.inputs;
-    b.coef.assign(p.inputs.size() * R, 0);
-    for (size_t i = 0; i < p.inputs.size(); i++)
-      for (size_t q = 0; q < p.rows.size(); q++) b.coef[i * R + q] = M.at(p.rows[q], p.inputs[i]);
+    for (int c = 0; c < M.cols; c++)
+      if (p.used[c]) b.inputs.push_back((uint16_t)c);
+    plan->max_inputs = std::max(plan->max_inputs, (int)b.inputs.size());
+    b.coef.assign(b.inputs.size() * R, 0);
+    for (size_t i = 0; i < b.inputs.size(); i++)
+      for (size_t q = 0; q < p.rows.size(); q++) b.coef[i * R + q] = M.at(p.rows[q], b.inputs[i]);
     plan->blocks.push_back(std::move(b));
   }
-  // 3. device image: descriptors, uint16 slots, coefficients
+  // 3. device image: descriptors, uint16 slots, per-entry split tables
+  static const SplitTables split = make_split_tables();
   const size_t nb = plan->blocks.size();
-  size_t nidx = 0, ncoef = 0;
+  size_t nidx = 0, nent = 0;
   for (auto &b : plan->blocks) {
     nidx += b.inputs.size() + b.rows.size();
-    ncoef += b.coef.size();
+    nent += b.coef.size();
+    plan->max_entries = std::max(plan->max_entries, (int)b.coef.size());
   }
   plan->idx_base = nb * sizeof(BlockDesc);
-  plan->coef_base = (plan->idx_base + nidx * 2 + 15) & ~(size_t)15;
-  plan->image.assign(plan->coef_base + ncoef + 16, 0);
+  plan->tab4_base = (plan->idx_base + nidx * 2 + 15) & ~(size_t)15;
+  plan->tab1_base = plan->tab4_base + nent * sizeof(TabEntry);
+  plan->image.assign(plan->tab1_base + nent * 4 + 16, 0);
   uint8_t *img = plan->image.data();
-  uint32_t io = 0, co = 0;
+  uint32_t io = 0, eo = 0;
   for (size_t i = 0; i < nb; i++) {
     auto &b = plan->blocks[i];
     BlockDesc d{};
@@ -152,9 +168,14 @@ std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, 
     d.out_off = io;
     memcpy(img + plan->idx_base + (size_t)io * 2, b.rows.data(), b.rows.size() * 2);
     io += (uint32_t)b.rows.size();
-    d.coef_off = co;
-    memcpy(img + plan->coef_base + co, b.coef.data(), b.coef.size());
-    co += (uint32_t)b.coef.size();
+    d.tab_off = eo;
+    for (size_t e = 0; e < b.coef.size(); e++) {
+      const uint32_t *w = split.w[b.coef[e]];
+      TabEntry t{w[0], w[1], w[2], w[3]};
+      memcpy(img + plan->tab4_base + (size_t)(eo + e) * sizeof(TabEntry), &t, sizeof t);
+      memcpy(img + plan->tab1_base + (size_t)(eo + e) * 4, &w[4], 4);
+    }
+    eo += (uint32_t)b.coef.size();
     d.nrows = (uint16_t)b.rows.size();
     d.ninputs = (uint16_t)b.inputs.size();
     memcpy(img + i * sizeof(BlockDesc), &d, sizeof d);

@@ -25,9 +25,15 @@ constexpr int kMaxSlots = 1024;     // input + output pointers per launch
 struct BlockDesc {
   uint32_t in_off;    // index into the uint16 array: input slots
   uint32_t out_off;   // index into the uint16 array: output slots
-  uint32_t coef_off;  // byte offset into the coefficient array (ninputs x R)
+  uint32_t tab_off;   // entry index into the split-table arrays (ninputs x R)
   uint16_t nrows;
   uint16_t ninputs;
+};
+
+// Split tables of one coefficient (see gf256.h): T0 and T1 as a 16-byte
+// vector, T2 as one word.
+struct TabEntry {
+  uint32_t t0a, t0b, t1a, t1b;
 };
 
 struct PlanBlock {
@@ -42,8 +48,10 @@ struct Plan {
   int max_inputs = 0;     // largest block input count (shared-memory staging)
   int64_t nnz = 0;        // non-zero coefficients (work per byte)
   std::vector<PlanBlock> blocks;
-  std::vector<uint8_t> image;  // BlockDesc[] | uint16 slots | coefficients
-  size_t coef_base = 0, idx_base = 0;
+  // BlockDesc[] | uint16 slots | TabEntry[] | uint32 T2[]
+  std::vector<uint8_t> image;
+  size_t idx_base = 0, tab4_base = 0, tab1_base = 0;
+  int max_entries = 0;    // largest ninputs x R of a block
   // per-device copies of `image`
   std::mutex mu;
   std::map<int, void *> dev;

@@ -16,30 +16,37 @@
 //     tables the paper's CPU code uses, Sec. 4);
 //   * the accumulators hold bytes in an interleaved lane order that makes
 //     the selector construction cheap; two PRMTs per word restore byte order
-//     before the 16-byte store.
-//
-// Zero coefficients are skipped and a coefficient of 1 is a plain XOR, both
-// on warp-uniform branches.
+//     before the 16-byte store;
+//   * the split tables of every (input, row) coefficient of the block are
+//     precomputed in the plan and staged in shared memory; a zero
+//     coefficient has all-zero tables, so no coefficient needs a branch.
 #include "gf256.h"
 #include "region.h"
 
 namespace pmrc {
-
-__constant__ SplitTables c_split = make_split_tables();
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kVec = 16;  // bytes per thread per tile
 
+// Multipliers passed at run time so that the selector construction below is
+// issued as integer multiply-adds (FMA pipe) rather than shifts (ALU pipe),
+// which the table lookups keep busy.
+struct MulConsts {
+  uint32_t x2, x16, hi16, hi26, hi29, hi30;  // 2, 16, 2^16, 2^26, 2^29, 2^30
+};
+
 template <int MAXP>
 struct RegionArgs {
   const uint8_t *image;  // plan device image
   uint64_t nbytes;       // block size
   uint32_t idx_base;     // byte offset of the uint16 slot array in image
-  uint32_t coef_base;    // byte offset of the coefficient array in image
+  uint32_t tab4_base;    // byte offset of the TabEntry array
+  uint32_t tab1_base;    // byte offset of the T2 word array
   uint32_t ntiles;       // ceil(nbytes / (kThreads * kVec))
   int aligned;           // every pointer is 16-byte aligned
+  MulConsts k;
   uint8_t *ptr[MAXP];    // input slots, then output slots
 };
 
@@ -49,48 +56,29 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
   return d;
 }
 
-// Selectors for 8 bytes (w0 = bytes 0-3, w1 = bytes 4-7).  Nibble 2m of the
+// Selectors for 8 bytes (w0 = bytes 0-3, w1 = bytes 4-7).  Nibble 2m of a
 // field word holds the field of byte m of w0, nibble 2m+1 that of byte m of
-// w1; s[2q] feeds lanes (w0.b0, w1.b0, w0.b1, w1.b1), s[2q+1] lanes
-// (w0.b2, w1.b2, w0.b3, w1.b3).
-__device__ __forceinline__ void split_fields(uint32_t w0, uint32_t w1, uint32_t *s) {
-  const uint32_t f0 = (w0 & 0x07070707u) | ((w1 & 0x07070707u) << 4);
-  const uint32_t f1 = ((w0 >> 3) & 0x07070707u) | ((w1 << 1) & 0x70707070u);
-  const uint32_t f2 = ((w0 >> 6) & 0x03030303u) | ((w1 >> 2) & 0x30303030u);
+// w1 (fields: x&7, (x>>3)&7, x>>6).  s[2q] feeds lanes (w0.b0, w1.b0, w0.b1,
+// w1.b1) of field q, s[2q+1] lanes (w0.b2, w1.b2, w0.b3, w1.b3).  The
+// fields of w0 and w1 never overlap, so they are combined by addition.
+__device__ __forceinline__ void split_fields(uint32_t w0, uint32_t w1, const MulConsts &k,
+                                             uint32_t *s) {
+  const uint32_t f0 = (w1 & 0x07070707u) * k.x16 + (w0 & 0x07070707u);
+  const uint32_t f1 = (w1 & 0x38383838u) * k.x2 + __umulhi(w0 & 0x38383838u, k.hi29);
+  const uint32_t f2 = __umulhi(w1 & 0xC0C0C0C0u, k.hi30) + __umulhi(w0 & 0xC0C0C0C0u, k.hi26);
   s[0] = f0;
-  s[1] = f0 >> 16;
+  s[1] = __umulhi(f0, k.hi16);
   s[2] = f1;
-  s[3] = f1 >> 16;
+  s[3] = __umulhi(f1, k.hi16);
   s[4] = f2;
-  s[5] = f2 >> 16;
+  s[5] = __umulhi(f2, k.hi16);
 }
 
-template <int R>
-__device__ __forceinline__ void mac_input(uint32_t (&acc)[R][4], const uint4 x,
-                                          const uint8_t *coefs, int nrows) {
-  uint32_t s[12];
-  split_fields(x.x, x.y, s);
-  split_fields(x.z, x.w, s + 6);
-#pragma unroll
-  for (int r = 0; r < R; r++) {
-    if (r < nrows) {
-      const uint32_t c = coefs[r];
-      if (c > 1) {
-        const uint32_t *T = c_split.w[c];
-        const uint32_t t0 = T[0], t1 = T[1], t2 = T[2], t3 = T[3], t4 = T[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const uint32_t *sq = s + 6 * (q >> 1) + (q & 1);
-          acc[r][q] ^= prmt(t0, t1, sq[0]) ^ prmt(t2, t3, sq[2]) ^ prmt(t4, t4, sq[4]);
-        }
-      } else if (c == 1) {
-        acc[r][0] ^= prmt(x.x, x.y, 0x5140);
-        acc[r][1] ^= prmt(x.x, x.y, 0x7362);
-        acc[r][2] ^= prmt(x.z, x.w, 0x5140);
-        acc[r][3] ^= prmt(x.z, x.w, 0x7362);
-      }
-    }
-  }
+// product of the 16 bytes behind selectors s with the coefficient whose split
+// tables are (t, t2), lane word q (see split_fields)
+__device__ __forceinline__ uint32_t lookup(const uint4 &t, uint32_t t2, const uint32_t *s, int q) {
+  const uint32_t *sq = s + 6 * (q >> 1) + (q & 1);
+  return prmt(t.x, t.y, sq[0]) ^ prmt(t.z, t.w, sq[2]) ^ prmt(t2, t2, sq[4]);
 }
 
 __device__ __forceinline__ uint4 load16(const uint8_t *p, uint64_t off, uint64_t nbytes,
@@ -120,16 +108,24 @@ __global__ void __launch_bounds__(kThreads)
     region_kernel(const __grid_constant__ RegionArgs<MAXP> a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const BlockDesc d = reinterpret_cast<const BlockDesc *>(a.image)[blockIdx.x];
-  const int nin = d.ninputs, nrows = d.nrows;
-  uint8_t *s_coef = smem;
-  uint16_t *s_slot = reinterpret_cast<uint16_t *>(smem + ((nin * R + 15) & ~15));
-  const uint16_t *idx = reinterpret_cast<const uint16_t *>(a.image + a.idx_base);
-  const uint8_t *coef = a.image + a.coef_base + d.coef_off;
-  for (int i = threadIdx.x; i < nin * R; i += kThreads) s_coef[i] = coef[i];
-  for (int i = threadIdx.x; i < nin; i += kThreads) s_slot[i] = idx[d.in_off + i];
-  for (int i = threadIdx.x; i < nrows; i += kThreads) s_slot[nin + i] = idx[d.out_off + i];
+  const int nin = d.ninputs, nrows = d.nrows, nent = nin * R;
+  uint4 *s_tab4 = reinterpret_cast<uint4 *>(smem);
+  uint32_t *s_tab1 = reinterpret_cast<uint32_t *>(smem + (size_t)nent * 16);
+  uint16_t *s_slot = reinterpret_cast<uint16_t *>(smem + (size_t)nent * 20);
+  {
+    const uint4 *g4 = reinterpret_cast<const uint4 *>(a.image + a.tab4_base) + d.tab_off;
+    const uint32_t *g1 = reinterpret_cast<const uint32_t *>(a.image + a.tab1_base) + d.tab_off;
+    const uint16_t *idx = reinterpret_cast<const uint16_t *>(a.image + a.idx_base);
+    for (int i = threadIdx.x; i < nent; i += kThreads) {
+      s_tab4[i] = g4[i];
+      s_tab1[i] = g1[i];
+    }
+    for (int i = threadIdx.x; i < nin; i += kThreads) s_slot[i] = idx[d.in_off + i];
+    for (int i = threadIdx.x; i < nrows; i += kThreads) s_slot[nin + i] = idx[d.out_off + i];
+  }
   __syncthreads();
 
+  const MulConsts k = a.k;
   const bool vec = a.aligned != 0;
   for (uint32_t tile = blockIdx.y; tile < a.ntiles; tile += gridDim.y) {
     const uint64_t off = ((uint64_t)tile * kThreads + threadIdx.x) * kVec;
@@ -139,13 +135,48 @@ __global__ void __launch_bounds__(kThreads)
     for (int r = 0; r < R; r++)
 #pragma unroll
       for (int q = 0; q < 4; q++) acc[r][q] = 0;
-    if (nin > 0) {
-      uint4 x = load16(a.ptr[s_slot[0]], off, a.nbytes, vec);
-      for (int i = 0; i < nin; i++) {
-        uint4 xn = x;
-        if (i + 1 < nin) xn = load16(a.ptr[s_slot[i + 1]], off, a.nbytes, vec);
-        mac_input<R>(acc, x, s_coef + i * R, nrows);
-        x = xn;
+
+    // two inputs per step: their six lookups per lane word fold into
+    // three 3-input XORs with the accumulator
+    int i = 0;
+    uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
+    if (nin > 0) x0 = load16(a.ptr[s_slot[0]], off, a.nbytes, vec);
+    if (nin > 1) x1 = load16(a.ptr[s_slot[1]], off, a.nbytes, vec);
+    for (; i + 1 < nin; i += 2) {
+      uint4 n0 = x0, n1 = x1;
+      if (i + 2 < nin) n0 = load16(a.ptr[s_slot[i + 2]], off, a.nbytes, vec);
+      if (i + 3 < nin) n1 = load16(a.ptr[s_slot[i + 3]], off, a.nbytes, vec);
+      uint32_t s0[12], s1[12];
+      split_fields(x0.x, x0.y, k, s0);
+      split_fields(x0.z, x0.w, k, s0 + 6);
+      split_fields(x1.x, x1.y, k, s1);
+      split_fields(x1.z, x1.w, k, s1 + 6);
+      const uint4 *ta = s_tab4 + i * R;
+      const uint32_t *tb = s_tab1 + i * R;
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        if (r < nrows) {
+          const uint4 u = ta[r], v = ta[R + r];
+          const uint32_t u2 = tb[r], v2 = tb[R + r];
+#pragma unroll
+          for (int q = 0; q < 4; q++) acc[r][q] ^= lookup(u, u2, s0, q) ^ lookup(v, v2, s1, q);
+        }
+      }
+      x0 = n0;
+      x1 = n1;
+    }
+    if (i < nin) {
+      uint32_t s0[12];
+      split_fields(x0.x, x0.y, k, s0);
+      split_fields(x0.z, x0.w, k, s0 + 6);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        if (r < nrows) {
+          const uint4 u = s_tab4[i * R + r];
+          const uint32_t u2 = s_tab1[i * R + r];
+#pragma unroll
+          for (int q = 0; q < 4; q++) acc[r][q] ^= lookup(u, u2, s0, q);
+        }
       }
     }
 #pragma unroll
@@ -171,16 +202,22 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   a.image = static_cast<const uint8_t *>(image);
   a.nbytes = nbytes;
   a.idx_base = (uint32_t)plan.idx_base;
-  a.coef_base = (uint32_t)plan.coef_base;
+  a.tab4_base = (uint32_t)plan.tab4_base;
+  a.tab1_base = (uint32_t)plan.tab1_base;
   const uint64_t tile = (uint64_t)kThreads * kVec;
   a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
   a.aligned = aligned ? 1 : 0;
+  a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
   for (int i = 0; i < plan.nin; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
   for (int j = 0; j < plan.nout; j++) a.ptr[plan.nin + j] = out[j];
   for (int j = plan.nin + plan.nout; j < MAXP; j++) a.ptr[j] = nullptr;
   const dim3 grid((unsigned)plan.blocks.size(), a.ntiles < 65535u ? a.ntiles : 65535u);
-  const size_t smem = (size_t)((plan.max_inputs * R + 15) & ~15) +
-                      (size_t)(plan.max_inputs + R) * sizeof(uint16_t);
+  const size_t smem = (size_t)plan.max_entries * 20 + (size_t)(plan.max_inputs + R) * 2 + 16;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(region_kernel<R, MAXP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   region_kernel<R, MAXP><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }

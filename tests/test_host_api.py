@@ -108,3 +108,29 @@ def test_error_statuses():
     with pytest.raises(P.PMRCError) as e:
         c.decode([0, 1, 2, 9], [0] * 12, [0] * 12, 16)
     assert e.value.rc == P.PMRC_EINVAL
+
+
+def test_plan_structure():
+    """The planner turns PM generators into dense blocks (rows of one slot
+    share the symbols of one column of the message matrix, Sec. 3.1) and keeps
+    block-diagonal matrices (batched helper projections) apart."""
+    import oracle as O2
+    n, k, a = 16, 8, 7
+    G2 = O2.generator(n, k, 1, True)[k * a:]
+    st = P.pmrc_plan_stats(G2)
+    assert st == {"blocks": 7, "R": 8, "entries": 784, "input_splits": 98, "nnz": 784}
+    G = O2.generator(n, k, 0, False)
+    st = P.pmrc_plan_stats(G)
+    assert st["blocks"] == 7 and st["R"] == 16 and st["entries"] == st["nnz"] == 1568
+    phi = O2.helper_coefficients(n, k, 1, 12)
+    M = np.zeros((14, 14 * a), np.uint8)
+    for h in range(14):
+        M[h, h * a:(h + 1) * a] = phi
+    st = P.pmrc_plan_stats(M)
+    assert st["blocks"] == 14 and st["R"] == 1 and st["entries"] == st["nnz"] == 98
+    # a decode matrix: merging may add zero products but never more than it saves
+    c = P.Code(n, k, 1, 1)
+    R = c.decode_matrix([0, 1, 4, 5, 7, 8, 11, 12])
+    miss = [r for r in range(56) if r // a not in (0, 1, 4, 5, 7)]
+    st = P.pmrc_plan_stats(R[miss])
+    assert st["entries"] <= 1.5 * st["nnz"]
