@@ -117,6 +117,16 @@ int pmrc_repair_newcomer(const pmrc_code *code, int failed, const int *helpers,
 int pmrc_decode(const pmrc_code *code, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t block_bytes, pmrc_stream_t stream);
 
+/* Encode kernel of a handle.  PMRC_KERNEL_AUTO (default): the bitsliced
+ * kernel when one was generated at build time for this code (and the call's
+ * pointers are 16-byte aligned, with no NULL output), the nibble-table kernel
+ * otherwise.  PMRC_KERNEL_GENERIC: always the nibble-table kernel.
+ * PMRC_KERNEL_BITSLICED: like AUTO, but PMRC_EUNSUPPORTED here if this code
+ * has no generated kernel.  Results are identical; only speed differs.  Do
+ * not change it while encodes on the handle are being issued. */
+enum { PMRC_KERNEL_AUTO = 0, PMRC_KERNEL_GENERIC = 1, PMRC_KERNEL_BITSLICED = 2 };
+int pmrc_set_encode_kernel(pmrc_code *code, int which);
+
 /* Default helpers for node `failed`: the first d-subset of the survivors,
  * in lexicographic order, whose Psi rows are invertible (the d lowest ids
  * when they qualify).  helpers_out: d ints. */

@@ -29,6 +29,10 @@ PMRC_ECUDA = -5
 PMRC_ETIMEOUT = -6
 PMRC_EBUSY = -7
 
+PMRC_KERNEL_AUTO = 0
+PMRC_KERNEL_GENERIC = 1
+PMRC_KERNEL_BITSLICED = 2
+
 PMRC_VANILLA = 0
 PMRC_SPARSE = 1
 PMRC_NONSYSTEMATIC = 0
@@ -69,6 +73,7 @@ _SIGNATURES = {
     "pmrc_newcomer_matrix": (_i, [_vp, _i, _ip, _u8p]),
     "pmrc_decode_matrix": (_i, [_vp, _ip, _u8p]),
     "pmrc_plan_stats": (_i, [_i, _i, _u8p, ctypes.POINTER(ctypes.c_int64)]),
+    "pmrc_set_encode_kernel": (_i, [_vp, _i]),
 }
 
 
@@ -166,6 +171,10 @@ def pmrc_repair_newcomer(code, failed, helpers, received, out, block_bytes, stre
 def pmrc_decode(code, nodes, node_blocks, data_out, block_bytes, stream=None):
     _check(lib().pmrc_decode(code, _ints(nodes), _ptrs(node_blocks), _ptrs(data_out),
                              block_bytes, _stream(stream)), "pmrc_decode")
+
+
+def pmrc_set_encode_kernel(code, which: int) -> None:
+    _check(lib().pmrc_set_encode_kernel(code, which), "pmrc_set_encode_kernel")
 
 
 def pmrc_default_helpers(code, failed) -> list:
@@ -274,6 +283,9 @@ class Code:
 
     def decode(self, nodes, node_blocks, data_out, block_bytes, stream=None):
         pmrc_decode(self.handle, nodes, node_blocks, data_out, block_bytes, stream)
+
+    def set_encode_kernel(self, which: int):
+        pmrc_set_encode_kernel(self.handle, which)
 
     def default_helpers(self, failed):
         return pmrc_default_helpers(self.handle, failed)

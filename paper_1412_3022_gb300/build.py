@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpmrc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["region.cu", "plan.cpp", "code.cpp", "api.cpp"]
+SOURCES = ["region.cu", "bitslice.cu", "plan.cpp", "code.cpp", "api.cpp"]
 
 
 def nvcc() -> str:
@@ -45,8 +45,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return OUT
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    # 1. generate the bitsliced encode schedules with the library's own
+    #    host construction (gen_bitslice.cpp + code.cpp, plain g++)
+    gen = os.path.join(BUILD, "gen_bitslice")
+    cxx = shutil.which("g++") or "g++"
+    r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", gen,
+                        os.path.join(CSRC, "gen_bitslice.cpp"), os.path.join(CSRC, "code.cpp")],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"g++ failed on gen_bitslice:\n{r.stdout}\n{r.stderr}")
+    r = subprocess.run([gen, os.path.join(BUILD, "bitslice_gen.cuh")], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gen_bitslice failed:\n{r.stdout}\n{r.stderr}")
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-                     "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+                     "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + BUILD]
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src + ".o")

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "bitslice.h"
 #include "code.h"
 #include "plan.h"
 #include "region.h"
@@ -155,6 +156,7 @@ int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out
   std::vector<int> slot(N - first);
   for (int r = 0; r < N - first; r++) slot[r] = r;
   c->encode = make_plan(M, slot, N - first);
+  c->bs_id = bitslice_find(n, k, construction, form, bitslice_checksum(M.v.data(), M.v.size()));
   *out = c.release();
   g_last_error.clear();
   return PMRC_OK;
@@ -235,11 +237,44 @@ int pmrc_default_helpers(const pmrc_code *c, int f, int *helpers_out) {
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
+int pmrc_set_encode_kernel(pmrc_code *c, int which) {
+  if (!c || which < PMRC_KERNEL_AUTO || which > PMRC_KERNEL_BITSLICED)
+    return fail(PMRC_EINVAL, "bad handle or kernel choice");
+  if (which == PMRC_KERNEL_BITSLICED && c->bs_id < 0)
+    return fail(PMRC_EUNSUPPORTED, "no bitsliced kernel was generated for this code");
+  c->encode_kernel = which;
+  return PMRC_OK;
+}
+
 int pmrc_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
                 size_t nbytes, pmrc_stream_t stream) {
   if (!c || !data || !out) return fail(PMRC_EINVAL, "NULL argument");
   std::string err;
-  int rc = launch_region(*c->encode, data, out, nbytes, (cudaStream_t)stream, err);
+  const Plan &P = *c->encode;
+  size_t done = 0;
+  if (c->bs_id >= 0 && c->encode_kernel != PMRC_KERNEL_GENERIC && nbytes >= 32) {
+    bool ok = true;
+    for (int i = 0; i < P.nin && ok; i++) ok = data[i] && ((uintptr_t)data[i] % 16 == 0);
+    for (int j = 0; j < P.nout && ok; j++) ok = out[j] && ((uintptr_t)out[j] % 16 == 0);
+    if (ok) {
+      done = nbytes & ~(size_t)31;
+      cudaError_t e = bitslice_launch(c->bs_id, data, out, done, (cudaStream_t)stream);
+      if (e != cudaSuccess)
+        return fail(PMRC_ECUDA, std::string("bitsliced encode launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (done == nbytes) return PMRC_OK;
+  int rc;
+  if (done == 0) {
+    rc = launch_region(*c->encode, data, out, nbytes, (cudaStream_t)stream, err);
+  } else {  // ragged tail of the blocks
+    std::vector<const uint8_t *> in2(P.nin);
+    std::vector<uint8_t *> out2(P.nout);
+    for (int i = 0; i < P.nin; i++) in2[i] = data[i] + done;
+    for (int j = 0; j < P.nout; j++) out2[j] = out[j] + done;
+    rc = launch_region(*c->encode, in2.data(), out2.data(), nbytes - done, (cudaStream_t)stream,
+                       err);
+  }
   return rc ? fail(rc, err) : PMRC_OK;
 }
 

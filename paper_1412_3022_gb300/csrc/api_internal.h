@@ -14,6 +14,8 @@
 struct pmrc_code {
   pmrc::CodeMatrices m;
   std::shared_ptr<pmrc::Plan> encode;  // built at create
+  int bs_id = -1;                      // generated bitsliced encode kernel, or -1
+  int encode_kernel = 0;               // PMRC_KERNEL_*
   mutable std::mutex mu;               // guards cache
   mutable std::map<std::string, std::shared_ptr<pmrc::Plan>> cache;
 };

@@ -356,3 +356,17 @@ def test_gpu_calls_reject_bad_arguments_without_launching():
     with pytest.raises(P.PMRCError) as e:
         c.encode([0] * 12, b.ptrs(), 64)
     assert e.value.rc == P.PMRC_EINVAL
+
+
+BITSLICED_CODES = [(16, 8, 1, 1), (16, 8, 0, 0), (8, 4, 1, 1), (6, 3, 1, 1), (6, 3, 0, 0)]
+
+
+@pytest.mark.parametrize("nbytes", [32, 33, 8192, 8192 + 32 + 7, 3 * 8192 + 16, 100000])
+@pytest.mark.parametrize("n,k,cons,form", BITSLICED_CODES)
+def test_bitsliced_and_generic_encode_agree_with_oracle(n, k, cons, form, nbytes):
+    X = inputs.blocks(k * (k - 1), nbytes, seed=nbytes + 7 * k)
+    want = oracle_outputs(n, k, cons, form, X)
+    for which in (P.PMRC_KERNEL_BITSLICED, P.PMRC_KERNEL_GENERIC):
+        c = code(n, k, cons, form)
+        c.set_encode_kernel(which)
+        assert np.array_equal(run_encode(c, X), want), which

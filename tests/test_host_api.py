@@ -134,3 +134,15 @@ def test_plan_structure():
     miss = [r for r in range(56) if r // a not in (0, 1, 4, 5, 7)]
     st = P.pmrc_plan_stats(R[miss])
     assert st["entries"] <= 1.5 * st["nnz"]
+
+
+def test_encode_kernel_choice():
+    for n, k, cons, form in [(16, 8, 1, 1), (16, 8, 0, 0), (8, 4, 1, 1)]:
+        c = P.Code(n, k, cons, form)
+        c.set_encode_kernel(P.PMRC_KERNEL_BITSLICED)
+        c.set_encode_kernel(P.PMRC_KERNEL_GENERIC)
+    c = P.Code(24, 12, 1, 1)
+    with pytest.raises(P.PMRCError) as e:
+        c.set_encode_kernel(P.PMRC_KERNEL_BITSLICED)
+    assert e.value.rc == P.PMRC_EUNSUPPORTED
+    c.set_encode_kernel(P.PMRC_KERNEL_AUTO)
