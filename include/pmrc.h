@@ -108,6 +108,20 @@ int pmrc_repair_newcomer(const pmrc_code *code, int failed, const int *helpers,
                          const uint8_t *const *received, uint8_t *const *out,
                          size_t block_bytes, pmrc_stream_t stream);
 
+/* Whole repair of node `failed` on one GPU: the d helper projections of
+ * pmrc_repair_helper and the newcomer apply of pmrc_repair_newcomer in one
+ * launch (same result as the two-step protocol).  The projections stay in a
+ * stream-ordered scratch buffer (cudaMallocAsync/cudaFreeAsync on `stream`)
+ * instead of going through caller memory; when phi_failed is a single 1
+ * (sparse code, failed node among the alpha first, Sec. 3.3) the newcomer
+ * reads the helpers' blocks directly and no scratch is used.
+ * helper_blocks: d*alpha pointers (helper i's alpha blocks at
+ * [i*alpha, i*alpha + alpha)), entries with a zero helper coefficient may be
+ * NULL.  out: alpha pointers.  Requires alpha <= 16. */
+int pmrc_repair(const pmrc_code *code, int failed, const int *helpers,
+                const uint8_t *const *helper_blocks, uint8_t *const *out, size_t block_bytes,
+                pmrc_stream_t stream);
+
 /* Reconstruction from any k nodes (Sec. 2: X = G~^-1 Y~).  nodes: k
  * distinct node ids (host array).  node_blocks: their k*alpha blocks,
  * node-major in the order of nodes.  data_out: k*alpha pointers for X; a
@@ -126,6 +140,50 @@ int pmrc_decode(const pmrc_code *code, const int *nodes, const uint8_t *const *n
  * not change it while encodes on the handle are being issued. */
 enum { PMRC_KERNEL_AUTO = 0, PMRC_KERNEL_GENERIC = 1, PMRC_KERNEL_BITSLICED = 2 };
 int pmrc_set_encode_kernel(pmrc_code *code, int which);
+
+/* ---- batched execution ---------------------------------------------------
+ * Many stripes (any mix of codes, block sizes and operations) run by one
+ * persistent kernel replayed from a CUDA graph.  The same per-stripe results
+ * as the single calls: encode = pmrc_encode, repair = pmrc_repair,
+ * decode = pmrc_decode.  Pointers given to pmrc_batch_add_* are remembered
+ * and must stay valid while the batch is launched; pmrc_batch_launch reads
+ * and writes them again each time.  Add all stripes, build, then launch any
+ * number of times.  A batch is not thread-safe; launches of one batch must
+ * not overlap on the GPU (they share a work counter and scratch). */
+typedef struct pmrc_batch pmrc_batch;
+
+int pmrc_batch_create(pmrc_batch **out);
+void pmrc_batch_destroy(pmrc_batch *batch); /* no launch may still be running */
+
+/* Each returns the stripe index (>= 0) or a negative status. */
+int pmrc_batch_add_encode(pmrc_batch *batch, const pmrc_code *code, const uint8_t *const *data,
+                          uint8_t *const *out, size_t block_bytes);
+int pmrc_batch_add_repair(pmrc_batch *batch, const pmrc_code *code, int failed,
+                          const int *helpers, const uint8_t *const *helper_blocks,
+                          uint8_t *const *out, size_t block_bytes);
+int pmrc_batch_add_decode(pmrc_batch *batch, const pmrc_code *code, const int *nodes,
+                          const uint8_t *const *node_blocks, uint8_t *const *data_out,
+                          size_t block_bytes);
+
+/* Uploads the work list (device allocations) and captures the graph on the
+ * current device.  work_bytes: byte-column span of one work item (rounded to
+ * 4 KiB tiles); ctas_per_sm: persistent CTAs per SM.  0 for either takes
+ * the value pmrc_batch_tune found for a batch of the same shape in this
+ * process, else 64 KiB and 2. */
+int pmrc_batch_build(pmrc_batch *batch, int work_bytes, int ctas_per_sm);
+
+/* One replay of the graph on `stream` (asynchronous). */
+int pmrc_batch_launch(pmrc_batch *batch, pmrc_stream_t stream);
+
+/* Autotuner: times the batch (synchronously, on `stream`) for each candidate
+ * item size (16, 64, 256 KiB) and CTAs per SM (1, 2), rebuilds it with the
+ * fastest and remembers the choice for batches of the same shape.
+ * best_out[2] (optional) = {work_bytes, ctas_per_sm}. */
+int pmrc_batch_tune(pmrc_batch *batch, pmrc_stream_t stream, int *best_out);
+
+/* info_out[8] = {stripes, work items, CTAs, work_bytes, ctas_per_sm,
+ * user bytes per launch, scratch bytes, shared memory bytes per CTA}. */
+int pmrc_batch_info(const pmrc_batch *batch, int64_t *info_out);
 
 /* Default helpers for node `failed`: the first d-subset of the survivors,
  * in lexicographic order, whose Psi rows are invertible (the d lowest ids

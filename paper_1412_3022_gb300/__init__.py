@@ -74,6 +74,16 @@ _SIGNATURES = {
     "pmrc_decode_matrix": (_i, [_vp, _ip, _u8p]),
     "pmrc_plan_stats": (_i, [_i, _i, _u8p, ctypes.POINTER(ctypes.c_int64)]),
     "pmrc_set_encode_kernel": (_i, [_vp, _i]),
+    "pmrc_repair": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_batch_create": (_i, [ctypes.POINTER(_vp)]),
+    "pmrc_batch_destroy": (None, [_vp]),
+    "pmrc_batch_add_encode": (_i, [_vp, _vp, _pp, _pp, _sz]),
+    "pmrc_batch_add_repair": (_i, [_vp, _vp, _i, _ip, _pp, _pp, _sz]),
+    "pmrc_batch_add_decode": (_i, [_vp, _vp, _ip, _pp, _pp, _sz]),
+    "pmrc_batch_build": (_i, [_vp, _i, _i]),
+    "pmrc_batch_launch": (_i, [_vp, _vp]),
+    "pmrc_batch_tune": (_i, [_vp, _vp, _ip]),
+    "pmrc_batch_info": (_i, [_vp, ctypes.POINTER(ctypes.c_int64)]),
 }
 
 
@@ -168,6 +178,11 @@ def pmrc_repair_newcomer(code, failed, helpers, received, out, block_bytes, stre
                                       block_bytes, _stream(stream)), "pmrc_repair_newcomer")
 
 
+def pmrc_repair(code, failed, helpers, helper_blocks, out, block_bytes, stream=None):
+    _check(lib().pmrc_repair(code, failed, _ints(helpers), _ptrs(helper_blocks), _ptrs(out),
+                             block_bytes, _stream(stream)), "pmrc_repair")
+
+
 def pmrc_decode(code, nodes, node_blocks, data_out, block_bytes, stream=None):
     _check(lib().pmrc_decode(code, _ints(nodes), _ptrs(node_blocks), _ptrs(data_out),
                              block_bytes, _stream(stream)), "pmrc_decode")
@@ -242,6 +257,101 @@ def pmrc_plan_stats(m) -> dict:
     return dict(zip(("blocks", "R", "entries", "input_splits", "nnz"), list(out)))
 
 
+# ---------------------------------------------------------------- batch
+def pmrc_batch_create() -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pmrc_batch_create(ctypes.byref(h)), "pmrc_batch_create")
+    return int(h.value)
+
+
+def pmrc_batch_destroy(batch) -> None:
+    if batch:
+        lib().pmrc_batch_destroy(batch)
+
+
+def pmrc_batch_add_encode(batch, code, data, out, block_bytes) -> int:
+    return _check(lib().pmrc_batch_add_encode(batch, code, _ptrs(data), _ptrs(out), block_bytes),
+                  "pmrc_batch_add_encode")
+
+
+def pmrc_batch_add_repair(batch, code, failed, helpers, helper_blocks, out, block_bytes) -> int:
+    return _check(lib().pmrc_batch_add_repair(batch, code, failed, _ints(helpers),
+                                              _ptrs(helper_blocks), _ptrs(out), block_bytes),
+                  "pmrc_batch_add_repair")
+
+
+def pmrc_batch_add_decode(batch, code, nodes, node_blocks, data_out, block_bytes) -> int:
+    return _check(lib().pmrc_batch_add_decode(batch, code, _ints(nodes), _ptrs(node_blocks),
+                                              _ptrs(data_out), block_bytes),
+                  "pmrc_batch_add_decode")
+
+
+def pmrc_batch_build(batch, work_bytes=0, ctas_per_sm=0) -> None:
+    _check(lib().pmrc_batch_build(batch, work_bytes, ctas_per_sm), "pmrc_batch_build")
+
+
+def pmrc_batch_launch(batch, stream=None) -> None:
+    _check(lib().pmrc_batch_launch(batch, _stream(stream)), "pmrc_batch_launch")
+
+
+def pmrc_batch_tune(batch, stream=None) -> tuple:
+    out = (ctypes.c_int * 2)()
+    _check(lib().pmrc_batch_tune(batch, _stream(stream), out), "pmrc_batch_tune")
+    return out[0], out[1]
+
+
+def pmrc_batch_info(batch) -> dict:
+    out = (ctypes.c_int64 * 8)()
+    _check(lib().pmrc_batch_info(batch, out), "pmrc_batch_info")
+    return dict(zip(("stripes", "items", "ctas", "work_bytes", "ctas_per_sm", "user_bytes",
+                     "scratch_bytes", "smem_bytes"), list(out)))
+
+
+class Batch:
+    """Owns a pmrc_batch handle; keeps the codes it references alive."""
+
+    def __init__(self):
+        self.handle = pmrc_batch_create()
+        self._codes = []
+
+    def close(self):
+        if self.handle:
+            pmrc_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_encode(self, code, data, out, block_bytes):
+        self._codes.append(code)
+        return pmrc_batch_add_encode(self.handle, code.handle, data, out, block_bytes)
+
+    def add_repair(self, code, failed, helpers, helper_blocks, out, block_bytes):
+        self._codes.append(code)
+        return pmrc_batch_add_repair(self.handle, code.handle, failed, helpers, helper_blocks,
+                                     out, block_bytes)
+
+    def add_decode(self, code, nodes, node_blocks, data_out, block_bytes):
+        self._codes.append(code)
+        return pmrc_batch_add_decode(self.handle, code.handle, nodes, node_blocks, data_out,
+                                     block_bytes)
+
+    def build(self, work_bytes=0, ctas_per_sm=0):
+        pmrc_batch_build(self.handle, work_bytes, ctas_per_sm)
+
+    def launch(self, stream=None):
+        pmrc_batch_launch(self.handle, stream)
+
+    def tune(self, stream=None):
+        return pmrc_batch_tune(self.handle, stream)
+
+    def info(self):
+        return pmrc_batch_info(self.handle)
+
+
 # ---------------------------------------------------------------- handle
 class Code:
     """Owns a pmrc_code handle; methods are the C calls on it."""
@@ -280,6 +390,9 @@ class Code:
 
     def repair_newcomer(self, failed, helpers, received, out, block_bytes, stream=None):
         pmrc_repair_newcomer(self.handle, failed, helpers, received, out, block_bytes, stream)
+
+    def repair(self, failed, helpers, helper_blocks, out, block_bytes, stream=None):
+        pmrc_repair(self.handle, failed, helpers, helper_blocks, out, block_bytes, stream)
 
     def decode(self, nodes, node_blocks, data_out, block_bytes, stream=None):
         pmrc_decode(self.handle, nodes, node_blocks, data_out, block_bytes, stream)

@@ -115,6 +115,31 @@ int decode_plan(const pmrc_code *c, const int *nodes, const std::vector<char> &w
   return kOk;
 }
 
+int fused_repair_plan(const pmrc_code *c, int f, const int *helpers,
+                      std::shared_ptr<FusedRepairPlan> &out, std::string &err) {
+  std::string key = "r:" + std::to_string(f);
+  for (int i = 0; i < c->m.d; i++) key += "," + std::to_string(helpers[i]);
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->fused.find(key);
+    if (it != c->fused.end()) {
+      out = it->second;
+      return kOk;
+    }
+  }
+  Mat D;
+  int rc = newcomer_matrix(c->m, f, helpers, D, err);
+  if (rc) return rc;
+  std::vector<uint8_t> phi;
+  helper_coefficients(c->m, f, phi);
+  auto p = make_fused_repair_plan(phi, D);
+  std::lock_guard<std::mutex> g(c->mu);
+  if (c->fused.size() >= kPlanCacheCap) c->fused.erase(c->fused.begin());
+  c->fused[key] = p;
+  out = p;
+  return kOk;
+}
+
 // Which data rows a decode call must produce: non-NULL outputs, except a
 // systematic data block whose output pointer is the node block holding it.
 int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
@@ -316,6 +341,37 @@ int pmrc_repair_newcomer(const pmrc_code *c, int f, const int *helpers,
   int rc = newcomer_plan(c, f, helpers, p, err);
   if (rc) return fail(rc, err);
   rc = launch_region(*p, received, out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
+                uint8_t *const *out, size_t nbytes, pmrc_stream_t stream) {
+  if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
+  if (c->m.alpha > 16) return fail(PMRC_EUNSUPPORTED, "pmrc_repair needs alpha <= 16");
+  std::shared_ptr<FusedRepairPlan> p;
+  std::string err;
+  int rc = fused_repair_plan(c, f, helpers, p, err);
+  if (rc) return fail(rc, err);
+  if (nbytes == 0) return PMRC_OK;
+  const uint64_t tile = 256 * 16;
+  const unsigned grid = fused_repair_grid((uint32_t)((nbytes + tile - 1) / tile));
+  const size_t sb = fused_repair_scratch_bytes(p->header, grid);
+  void *scratch = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (sb) {
+    cudaError_t e = cudaMallocAsync(&scratch, sb, st);
+    if (e != cudaSuccess)
+      return fail(e == cudaErrorMemoryAllocation ? PMRC_ENOMEM : PMRC_ECUDA,
+                  std::string("cudaMallocAsync(scratch): ") + cudaGetErrorString(e));
+  }
+  rc = launch_fused_repair(*p, blocks, out, nbytes, st, scratch, sb, err);
+  if (scratch) {
+    cudaError_t e = cudaFreeAsync(scratch, st);
+    if (!rc && e != cudaSuccess) {
+      rc = PMRC_ECUDA;
+      err = std::string("cudaFreeAsync(scratch): ") + cudaGetErrorString(e);
+    }
+  }
   return rc ? fail(rc, err) : PMRC_OK;
 }
 

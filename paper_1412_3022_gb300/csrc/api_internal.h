@@ -10,6 +10,7 @@
 
 #include "code.h"
 #include "plan.h"
+#include "repair.h"
 
 struct pmrc_code {
   pmrc::CodeMatrices m;
@@ -18,6 +19,7 @@ struct pmrc_code {
   int encode_kernel = 0;               // PMRC_KERNEL_*
   mutable std::mutex mu;               // guards cache
   mutable std::map<std::string, std::shared_ptr<pmrc::Plan>> cache;
+  mutable std::map<std::string, std::shared_ptr<pmrc::FusedRepairPlan>> fused;
 };
 
 namespace pmrc {
@@ -33,6 +35,8 @@ int newcomer_plan(const pmrc_code *c, int f, const int *helpers, std::shared_ptr
                   std::string &err);
 int decode_plan(const pmrc_code *c, const int *nodes, const std::vector<char> &want,
                 std::shared_ptr<Plan> &out, std::string &err);
+int fused_repair_plan(const pmrc_code *c, int f, const int *helpers,
+                      std::shared_ptr<FusedRepairPlan> &out, std::string &err);
 int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                   uint8_t *const *data_out, std::vector<char> &want);
 

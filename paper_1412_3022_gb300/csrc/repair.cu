@@ -1,0 +1,249 @@
+// Fused single-node repair on one GPU: the d helper projections
+// p_h = sum_j phi_f[j] Y[alpha h + j] and the newcomer apply
+// node_f = D p (D = [I | lambda_f I] Psi_H^-1) in one kernel.
+//
+// In the paper's system the helpers send p_h over the network (Sec. 2, 3.3).
+// When helpers and newcomer share a GPU, the projections need not visit
+// caller memory: each thread computes its 16 bytes of every p_h, parks them
+// in a scratch slice private to its CTA (the write and the read-back are by
+// the same thread, so no barrier is needed and the slice stays in L2), then
+// applies D.  When phi_f has a single non-zero equal to 1 (sparse code,
+// failed node among the alpha first) p_h is a block the helper already
+// stores, and the newcomer reads it in place.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "gf256.h"
+#include "plan.h"
+#include "repair.h"
+
+namespace pmrc {
+namespace {
+
+#include "region_dev.cuh"
+
+constexpr int kRepMaxPtr = 512;
+
+struct RepairArgs {
+  const uint8_t *image;  // FusedRepairImage (device)
+  uint4 *scratch;        // gridDim.x * d * kThreads vectors (unused if direct)
+  uint64_t nbytes;
+  uint32_t ntiles;
+  int aligned;
+  MulConsts k;
+  uint8_t *ptr[kRepMaxPtr];  // d*alpha helper blocks, then alpha outputs
+};
+
+template <int RN>
+__global__ void __launch_bounds__(kThreads) fused_repair_kernel(const __grid_constant__ RepairArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint16_t s_nz[16];
+  const FusedRepairHeader *hp = reinterpret_cast<const FusedRepairHeader *>(a.image);
+  const int d = hp->d, alpha = hp->alpha, nz = hp->nz;
+  const bool direct = hp->direct != 0;
+  const uint32_t tab4_off = hp->tab4_off, tab1_off = hp->tab1_off;
+  if (threadIdx.x < 16) s_nz[threadIdx.x] = hp->nzidx[threadIdx.x];
+  const int n1 = nz, n2 = d * alpha;
+  uint4 *t1a = reinterpret_cast<uint4 *>(smem);
+  uint4 *t2a = t1a + n1;
+  uint32_t *t1b = reinterpret_cast<uint32_t *>(t2a + n2);
+  uint32_t *t2b = t1b + n1;
+  {
+    const uint4 *g4 = reinterpret_cast<const uint4 *>(a.image + tab4_off);
+    const uint32_t *g1 = reinterpret_cast<const uint32_t *>(a.image + tab1_off);
+    for (int i = threadIdx.x; i < n1 + n2; i += kThreads) {
+      t1a[i] = g4[i];  // t2a follows t1a contiguously, as in the image
+      t1b[i] = g1[i];
+    }
+  }
+  __syncthreads();
+  const MulConsts k = a.k;
+  const bool vec = a.aligned != 0;
+  uint4 *slice = a.scratch + (size_t)blockIdx.x * d * kThreads + threadIdx.x;
+  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const uint64_t off = ((uint64_t)tile * kThreads + threadIdx.x) * kVec;
+    if (off >= a.nbytes) continue;
+    if (!direct) {
+      // stage 1: projections of the d helpers (one row, nz inputs each)
+      for (int q = 0; q < d; q++) {
+        uint32_t acc1[1][4];
+        mac_block<1>(acc1, nz, 1, 1, t1a, t1b, k, [&](int i) {
+          return load16(a.ptr[q * alpha + s_nz[i]], off, a.nbytes, vec);
+        });
+        slice[(size_t)q * kThreads] = acc_bytes(acc1[0]);
+      }
+    }
+    // stage 2: newcomer, alpha rows over the d projections
+    uint32_t acc[RN][4];
+    if (direct) {
+      const int j0 = s_nz[0];
+      mac_block<RN>(acc, d, alpha, alpha, t2a, t2b, k, [&](int q) {
+        return load16(a.ptr[q * alpha + j0], off, a.nbytes, vec);
+      });
+    } else {
+      mac_block<RN>(acc, d, alpha, alpha, t2a, t2b, k,
+                    [&](int q) { return slice[(size_t)q * kThreads]; });
+    }
+#pragma unroll
+    for (int r = 0; r < RN; r++)
+      if (r < alpha) store16(a.ptr[d * alpha + r], off, a.nbytes, vec, acc_bytes(acc[r]));
+  }
+}
+
+}  // namespace
+
+std::shared_ptr<FusedRepairPlan> make_fused_repair_plan(const std::vector<uint8_t> &phi,
+                                                        const Mat &D) {
+  static const SplitTables split = make_split_tables();
+  auto p = std::make_shared<FusedRepairPlan>();
+  const int alpha = D.rows, d = D.cols;
+  FusedRepairHeader h{};
+  h.d = (uint32_t)d;
+  h.alpha = (uint32_t)alpha;
+  std::vector<int> nzl;
+  for (int j = 0; j < (int)phi.size(); j++)
+    if (phi[j]) nzl.push_back(j);
+  h.nz = (uint32_t)nzl.size();
+  for (size_t i = 0; i < nzl.size(); i++) h.nzidx[i] = (uint16_t)nzl[i];
+  h.direct = (nzl.size() == 1 && phi[nzl[0]] == 1) ? 1u : 0u;
+  const size_t n1 = nzl.size(), n2 = (size_t)d * alpha;
+  h.tab4_off = (uint32_t)((sizeof(FusedRepairHeader) + 15) & ~(size_t)15);
+  h.tab1_off = h.tab4_off + (uint32_t)((n1 + n2) * sizeof(TabEntry));
+  p->image.assign(h.tab1_off + (n1 + n2) * 4 + 16, 0);
+  auto put = [&](size_t e, uint8_t c) {
+    const uint32_t *w = split.w[c];
+    TabEntry t{w[0], w[1], w[2], w[3]};
+    memcpy(p->image.data() + h.tab4_off + e * sizeof(TabEntry), &t, sizeof t);
+    memcpy(p->image.data() + h.tab1_off + e * 4, &w[4], 4);
+  };
+  for (size_t i = 0; i < n1; i++) put(i, phi[nzl[i]]);
+  for (int q = 0; q < d; q++)  // entry (input q, row r) at n1 + q * alpha + r
+    for (int r = 0; r < alpha; r++) put(n1 + (size_t)q * alpha + r, D.at(r, q));
+  memcpy(p->image.data(), &h, sizeof h);
+  p->header = h;
+  return p;
+}
+
+size_t fused_repair_smem(const FusedRepairHeader &h) {
+  return (size_t)(h.nz + (size_t)h.d * h.alpha) * 20;
+}
+
+int launch_fused_repair(FusedRepairPlan &plan, const uint8_t *const *helper_blocks,
+                        uint8_t *const *out, size_t nbytes, cudaStream_t stream, void *scratch,
+                        size_t scratch_bytes, std::string &err) {
+  const FusedRepairHeader &h = plan.header;
+  const int d = h.d, alpha = h.alpha;
+  if ((d + 1) * alpha > kRepMaxPtr || alpha > 16 || h.nz > 16) {
+    err = "code too large for the fused repair kernel";
+    return kEUnsupported;
+  }
+  if (nbytes == 0) return kOk;
+  RepairArgs a;
+  memset(a.ptr, 0, sizeof a.ptr);
+  bool aligned = true;
+  for (int q = 0; q < d; q++)
+    for (int j = 0; j < alpha; j++) {
+      const uint8_t *p = helper_blocks[q * alpha + j];
+      a.ptr[q * alpha + j] = const_cast<uint8_t *>(p);
+      bool used = false;
+      for (uint32_t i = 0; i < h.nz; i++) used |= (h.nzidx[i] == j);
+      if (used && !p) {
+        err = "a helper block the repair reads is NULL";
+        return kEInval;
+      }
+      if (p) aligned = aligned && ((uintptr_t)p % kVec == 0);
+    }
+  for (int r = 0; r < alpha; r++) {
+    if (!out[r]) {
+      err = "output block is NULL";
+      return kEInval;
+    }
+    a.ptr[d * alpha + r] = out[r];
+    aligned = aligned && ((uintptr_t)out[r] % kVec == 0);
+  }
+  const void *image = nullptr;
+  int rc = plan.device_image(&image, err);
+  if (rc) return rc;
+  const uint64_t tile = (uint64_t)kThreads * kVec;
+  a.image = static_cast<const uint8_t *>(image);
+  a.nbytes = nbytes;
+  a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
+  a.aligned = aligned ? 1 : 0;
+  a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
+  const unsigned grid = fused_repair_grid(a.ntiles);
+  if (!h.direct && scratch_bytes < fused_repair_scratch_bytes(h, grid)) {
+    err = "scratch buffer too small";
+    return kEInval;
+  }
+  a.scratch = static_cast<uint4 *>(scratch);
+  const size_t smem = fused_repair_smem(h);
+  cudaError_t e;
+  if (alpha <= 8)
+    fused_repair_kernel<8><<<grid, kThreads, smem, stream>>>(a);
+  else
+    fused_repair_kernel<16><<<grid, kThreads, smem, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("fused repair launch: ") + cudaGetErrorString(e);
+    return kECuda;
+  }
+  return kOk;
+}
+
+unsigned fused_repair_grid(uint32_t ntiles) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  }
+  const uint32_t cap = (uint32_t)sms * 2;
+  return ntiles < cap ? (ntiles ? ntiles : 1) : cap;
+}
+
+size_t fused_repair_scratch_bytes(const FusedRepairHeader &h, unsigned grid) {
+  return h.direct ? 0 : (size_t)grid * h.d * kThreads * kVec;
+}
+
+int FusedRepairPlan::device_image(const void **out, std::string &err) {
+  int devid = -1;
+  cudaError_t e = cudaGetDevice(&devid);
+  if (e != cudaSuccess) {
+    err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return kECuda;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  auto it = dev.find(devid);
+  if (it != dev.end()) {
+    *out = it->second;
+    return kOk;
+  }
+  void *p = nullptr;
+  e = cudaMalloc(&p, image.size());
+  if (e != cudaSuccess) {
+    err = std::string("cudaMalloc(repair plan): ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? kENoMem : kECuda;
+  }
+  e = cudaMemcpy(p, image.data(), image.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    err = std::string("cudaMemcpy(repair plan): ") + cudaGetErrorString(e);
+    return kECuda;
+  }
+  dev[devid] = p;
+  *out = p;
+  return kOk;
+}
+
+FusedRepairPlan::~FusedRepairPlan() {
+  for (auto &kv : dev) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaSetDevice(kv.first);
+    cudaFree(kv.second);
+    if (cur >= 0) cudaSetDevice(cur);
+  }
+}
+
+}  // namespace pmrc

@@ -1,0 +1,48 @@
+// Fused single-node repair (repair.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "code.h"
+
+namespace pmrc {
+
+// Device image: header, then split tables (stage 1: nz entries for phi_f's
+// non-zeros; stage 2: entry (q, r) = D[r][q] at nz + q*alpha + r).
+struct FusedRepairHeader {
+  uint32_t d, alpha, nz, direct;
+  uint32_t tab4_off, tab1_off;
+  uint16_t nzidx[16];  // which of a helper's alpha blocks phi_f reads
+};
+
+struct FusedRepairPlan {
+  FusedRepairHeader header;
+  std::vector<uint8_t> image;
+  std::mutex mu;
+  std::map<int, void *> dev;
+  ~FusedRepairPlan();
+  int device_image(const void **out, std::string &err);
+};
+
+std::shared_ptr<FusedRepairPlan> make_fused_repair_plan(const std::vector<uint8_t> &phi,
+                                                        const Mat &D);
+
+// CTAs of a fused repair launch over ntiles 4 KiB tiles.
+unsigned fused_repair_grid(uint32_t ntiles);
+
+// Scratch the launch needs (0 when phi_f is a single 1: no projections).
+size_t fused_repair_scratch_bytes(const FusedRepairHeader &h, unsigned grid);
+
+// Runs the repair.  helper_blocks: d*alpha pointers, out: alpha pointers.
+// scratch: device buffer of at least fused_repair_scratch_bytes(h, grid).
+int launch_fused_repair(FusedRepairPlan &plan, const uint8_t *const *helper_blocks,
+                        uint8_t *const *out, size_t nbytes, cudaStream_t stream, void *scratch,
+                        size_t scratch_bytes, std::string &err);
+
+}  // namespace pmrc

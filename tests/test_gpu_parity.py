@@ -370,3 +370,65 @@ def test_bitsliced_and_generic_encode_agree_with_oracle(n, k, cons, form, nbytes
         c = code(n, k, cons, form)
         c.set_encode_kernel(which)
         assert np.array_equal(run_encode(c, X), want), which
+
+
+# ------------------------------------------------------------------ fused repair
+def fused_repair_gpu(c, Y, f, H, nbytes, shift=0):
+    a = c.alpha
+    store = Blocks(c.n * a, nbytes, shift, Y)
+    out = Blocks(a, nbytes, shift)
+    c.repair(f, H, [store.ptr(a * h + j) for h in H for j in range(a)], out.ptrs(), nbytes)
+    assert out.guards_intact()
+    return out.get()
+
+
+@pytest.mark.parametrize("n,k,cons,form", [(6, 3, 0, 0), (6, 3, 1, 1), (8, 4, 1, 1),
+                                           (16, 8, 1, 1), (16, 8, 0, 0), (24, 12, 1, 1),
+                                           (32, 16, 1, 1)])
+def test_fused_repair_every_node(n, k, cons, form):
+    a = k - 1
+    nbytes = 2 * 4096 + 19
+    X = inputs.blocks(k * a, nbytes, seed=300 + k)
+    Y = O.encode(n, k, cons, bool(form), X)
+    c = code(n, k, cons, form)
+    for f in range(n):
+        H = c.default_helpers(f)
+        got = fused_repair_gpu(c, Y, f, H, nbytes, shift=(f % 3) * 4)
+        assert np.array_equal(got, Y[a * f:a * f + a]), f
+
+
+def test_fused_repair_k3_every_helper_set_and_sizes():
+    n, k, a, d = 6, 3, 2, 4
+    c = code(n, k, 1, 1)
+    for nbytes in (1, 17, 4096, 3 * 4096 + 1):
+        X = inputs.blocks(k * a, nbytes, seed=nbytes)
+        Y = O.encode(n, k, 1, True, X)
+        for f in range(n):
+            for H in itertools.combinations([i for i in range(n) if i != f], d):
+                H = list(H)
+                try:
+                    O.newcomer_matrix(n, k, 1, f, H)
+                except O.OracleError:
+                    continue
+                assert np.array_equal(fused_repair_gpu(c, Y, f, H, nbytes), Y[a * f:a * f + a])
+
+
+def test_fused_repair_full_size_sampled():
+    n, k, a = 16, 8, 7
+    nbytes = 1 << 20
+    c = code(n, k, 1, 1)
+    X = inputs.device_blocks(k * a, nbytes, seed=99)
+    Y = torch.empty((n * a, nbytes), dtype=torch.uint8, device="cuda")
+    Y[:k * a].copy_(X)
+    c.encode([X[i] for i in range(k * a)], [Y[k * a + i] for i in range((n - k) * a)], nbytes)
+    for f in (3, 12):
+        H = c.default_helpers(f)
+        out = torch.empty((a, nbytes), dtype=torch.uint8, device="cuda")
+        c.repair(f, H, [Y[a * h + j] for h in H for j in range(a)], [out[j] for j in range(a)],
+                 nbytes)
+        torch.cuda.synchronize()
+        assert torch.equal(out, Y[a * f:a * f + a])
+        for cs in columns(nbytes):
+            Yc = Y[:, cs].cpu().numpy()
+            sent = np.stack([O.repair_helper(n, k, 1, f, Yc[a * h:a * h + a]) for h in H])
+            assert np.array_equal(out[:, cs].cpu().numpy(), O.repair_newcomer(n, k, 1, f, H, sent))
