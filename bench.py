@@ -56,6 +56,8 @@ def parse():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batch-stripes", type=int, default=4096)
     return p.parse_args()
 
 
@@ -167,6 +169,7 @@ class Workload:
             "sys_encode": (K + K) * B,
             "repair_helpers": (D_ * reads_per_helper + D_) * B,
             "repair_newcomer": (D_ + a) * B,
+            "repair_fused": (D_ * reads_per_helper + a) * B,
             "decode": (dec_inputs + len(missing)) * B,
         }
         self.user = {"gen_encode": K * B, "sys_encode": K * B, "repair": a * B, "decode": K * B}
@@ -273,7 +276,16 @@ def run_ours(args, rank, world, local_rank):
         except (OSError, ValueError):
             pass
 
+    # the fused single-GPU repair (helper projections kept in scratch)
+    fused_ms = time_op(torch, stream, flush, args, lambda: W.sysc.repair(
+        W.f, W.H, W.helper_in, W.node_ptrs, B))
+    per_op["repair_fused"] = {"ms": round(fused_ms, 4),
+                              "user_GBps": round(W.user["repair"] / (fused_ms * 1e-3) / 1e9, 2),
+                              "alg_bytes": W.alg["repair_fused"],
+                              "frac_hbm": round(W.alg["repair_fused"] / (fused_ms * 1e-3) / 1e9
+                                                / hbm, 4)}
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream)
+    batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
@@ -293,11 +305,138 @@ def run_ours(args, rank, world, local_rank):
     }
     if e2e:
         result["e2e"] = e2e
+    if batched:
+        result["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args, W, torch)
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def time_op(torch, stream, flush, args, fn):
+    """Average device time of fn over args.steps runs, L2 flushed before each."""
+    for _ in range(args.warmup):
+        flush.fill_(3)
+        fn()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.fill_(5)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / args.steps
+
+
+def run_batched(torch, P, inputs, args, dev, stream):
+    """Batched workload: stripes with k uniform on {4, 8, 16} (n = 2k, sparse
+    systematic), block sizes log-uniform on [4 KiB, 1 MiB] rounded up to 16 B,
+    half encode and half repair (fused, default helpers of a seeded failed
+    node).  One persistent launch from a CUDA graph, tuned by the library's
+    autotuner, against the same stripes issued as plain per-stripe calls."""
+    import numpy as np
+    mix = inputs.batch_mix(args.batch_stripes, seed=args.seed + 4)
+    codes = {k: P.Code(2 * k, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC) for k in (4, 8, 16)}
+    # one arena for every block of the workload
+    need = 0
+    for m in mix:
+        k, a, nb = m["k"], m["k"] - 1, m["block_bytes"]
+        need += (2 * k * a if m["op"] == "encode" else 2 * k * a + a) * nb
+    free, _ = torch.cuda.mem_get_info()
+    scale_note = None
+    if need > 0.8 * free:
+        keep = max(16, int(len(mix) * 0.8 * free / need))
+        scale_note = f"device memory: {keep} of {len(mix)} stripes"
+        mix = mix[:keep]
+        need = sum((2 * m["k"] * (m["k"] - 1) + (0 if m["op"] == "encode" else m["k"] - 1))
+                   * m["block_bytes"] for m in mix)
+    arena = torch.empty(need, dtype=torch.uint8, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(args.seed + 5)
+    chunk = 1 << 30
+    for o in range(0, need, chunk):  # seeded random fill, in 1 GiB pieces
+        arena[o:o + chunk].random_(0, 256, generator=g)
+    base = arena.data_ptr()
+    ops, off = [], 0
+    for m in mix:
+        k, a, nb = m["k"], m["k"] - 1, m["block_bytes"]
+        c = codes[k]
+        if m["op"] == "encode":
+            ins = [base + off + i * nb for i in range(k * a)]
+            outs = [base + off + (k * a + i) * nb for i in range(k * a)]
+            off += 2 * k * a * nb
+            ops.append(("encode", c, ins, outs, nb, m))
+        else:
+            Y = [base + off + i * nb for i in range(2 * k * a)]
+            outs = [base + off + (2 * k * a + j) * nb for j in range(a)]
+            off += (2 * k * a + a) * nb
+            c.encode(Y[:k * a], Y[k * a:], nb)  # stored codeword
+            f = m["failed"]
+            H = c.default_helpers(f)
+            ops.append(("repair", c, [Y[a * h + j] for h in H for j in range(a)], outs, nb,
+                        dict(m, H=H)))
+    torch.cuda.synchronize()
+    user = sum((m["k"] * (m["k"] - 1) if op == "encode" else m["k"] - 1) * m["block_bytes"]
+               for op, _, _, _, _, m in ops)
+    b = P.Batch()
+    for op, c, ins, outs, nb, m in ops:
+        if op == "encode":
+            b.add_encode(c, ins, outs, nb)
+        else:
+            b.add_repair(c, m["failed"], m["H"], ins, outs, nb)
+    t0 = time.perf_counter()
+    best = b.tune(stream)
+    tune_s = time.perf_counter() - t0
+    info = b.info()
+
+    def run_batch():
+        b.launch(stream)
+
+    def run_plain():
+        for op, c, ins, outs, nb, m in ops:
+            if op == "encode":
+                c.encode(ins, outs, nb, stream)
+            else:
+                c.repair(m["failed"], m["H"], ins, outs, nb, stream)
+
+    reps = 3
+    res = {}
+    for name, fn in (("batched", run_batch), ("plain", run_plain)):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = (e0.elapsed_time(e1) / reps, (time.perf_counter() - t0) * 1e3 / reps)
+    out = {
+        "workload": f"{len(ops)} stripes, k uniform on {{4,8,16}} (n=2k, sparse systematic), "
+                    "block sizes log-uniform 4 KiB-1 MiB, 50% encode / 50% fused repair",
+        "user_GB": round(user / 1e9, 3),
+        "batched_GBps": round(user / (res["batched"][0] * 1e-3) / 1e9, 1),
+        "batched_ms": round(res["batched"][0], 3),
+        "plain_GBps": round(user / (res["plain"][0] * 1e-3) / 1e9, 1),
+        "plain_ms": round(res["plain"][0], 3),
+        "plain_wall_ms": round(res["plain"][1], 3),
+        "speedup": round(res["plain"][0] / res["batched"][0], 3),
+        "launches": {"batched": 1, "plain": len(ops)},
+        "tuned": {"work_bytes": best[0], "ctas_per_sm": best[1], "tune_s": round(tune_s, 2),
+                  "items": info["items"], "ctas": info["ctas"]},
+        "l2": "not flushed (working set far larger than L2)",
+    }
+    if scale_note:
+        out["note"] = scale_note
+    del arena
+    del np
+    return out
 
 
 def run_e2e(torch, W, args, dev, stream):

@@ -122,6 +122,33 @@ int pmrc_repair(const pmrc_code *code, int failed, const int *helpers,
                 const uint8_t *const *helper_blocks, uint8_t *const *out, size_t block_bytes,
                 pmrc_stream_t stream);
 
+/* pmrc_repair_noalloc: the same repair as pmrc_repair (same arguments, same
+ * bytes out) for callers that cannot allocate GPU memory -- for example a
+ * library running inside a process whose device memory is owned by another
+ * allocator (a framework pool that reserves the whole device), or a
+ * latency-critical path where an allocation could block, synchronize the
+ * device or fail part-way through a repair.  The paper has no counterpart:
+ * this is an interface choice of this library.
+ *
+ * It allocates nothing on the device (no cudaMalloc/cudaFree, no
+ * stream-ordered or library allocator).  Its scratch is one fixed array
+ * compiled into the library: 64 KiB for the repair tables plus 16 MiB for
+ * the helper projections, which every GPU that loads the library holds
+ * until the process exits.  Each call copies the repair tables into the
+ * array on `stream`; big blocks are run with fewer CTAs so the projections
+ * fit.  A repair whose tables exceed 64 KiB is rejected with
+ * PMRC_EUNSUPPORTED (no code with alpha <= 16 comes close).
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call uses the same array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (other streams, other
+ * host threads) race and corrupt each other's results: issue them one after
+ * another on one stream. */
+int pmrc_repair_noalloc(const pmrc_code *code, int failed, const int *helpers,
+                        const uint8_t *const *helper_blocks, uint8_t *const *out,
+                        size_t block_bytes, pmrc_stream_t stream);
+
 /* Reconstruction from any k nodes (Sec. 2: X = G~^-1 Y~).  nodes: k
  * distinct node ids (host array).  node_blocks: their k*alpha blocks,
  * node-major in the order of nodes.  data_out: k*alpha pointers for X; a

@@ -75,6 +75,7 @@ _SIGNATURES = {
     "pmrc_plan_stats": (_i, [_i, _i, _u8p, ctypes.POINTER(ctypes.c_int64)]),
     "pmrc_set_encode_kernel": (_i, [_vp, _i]),
     "pmrc_repair": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_repair_noalloc": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
     "pmrc_batch_create": (_i, [ctypes.POINTER(_vp)]),
     "pmrc_batch_destroy": (None, [_vp]),
     "pmrc_batch_add_encode": (_i, [_vp, _vp, _pp, _pp, _sz]),
@@ -181,6 +182,12 @@ def pmrc_repair_newcomer(code, failed, helpers, received, out, block_bytes, stre
 def pmrc_repair(code, failed, helpers, helper_blocks, out, block_bytes, stream=None):
     _check(lib().pmrc_repair(code, failed, _ints(helpers), _ptrs(helper_blocks), _ptrs(out),
                              block_bytes, _stream(stream)), "pmrc_repair")
+
+
+def pmrc_repair_noalloc(code, failed, helpers, helper_blocks, out, block_bytes, stream=None):
+    _check(lib().pmrc_repair_noalloc(code, failed, _ints(helpers), _ptrs(helper_blocks),
+                                     _ptrs(out), block_bytes, _stream(stream)),
+           "pmrc_repair_noalloc")
 
 
 def pmrc_decode(code, nodes, node_blocks, data_out, block_bytes, stream=None):

@@ -375,6 +375,19 @@ int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *co
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
+int pmrc_repair_noalloc(const pmrc_code *c, int f, const int *helpers,
+                        const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
+                        pmrc_stream_t stream) {
+  if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
+  if (c->m.alpha > 16) return fail(PMRC_EUNSUPPORTED, "pmrc_repair_noalloc needs alpha <= 16");
+  std::shared_ptr<FusedRepairPlan> p;
+  std::string err;
+  int rc = fused_repair_plan(c, f, helpers, p, err);
+  if (rc) return fail(rc, err);
+  rc = launch_fused_repair_noalloc(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
 int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream) {
   if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");

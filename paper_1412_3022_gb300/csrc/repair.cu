@@ -93,6 +93,13 @@ __global__ void __launch_bounds__(kThreads) fused_repair_kernel(const __grid_con
 
 }  // namespace
 
+// Fixed scratch of pmrc_repair_noalloc: the repair's split tables in the
+// first kNoAllocTableBytes, the helper projections after them.  Every GPU
+// that loads the library holds it until the process exits.
+constexpr size_t kNoAllocTableBytes = 64u << 10;
+constexpr size_t kNoAllocProjBytes = 16u << 20;
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocTableBytes + kNoAllocProjBytes];
+
 std::shared_ptr<FusedRepairPlan> make_fused_repair_plan(const std::vector<uint8_t> &phi,
                                                         const Mat &D) {
   static const SplitTables split = make_split_tables();
@@ -179,6 +186,100 @@ int launch_fused_repair(FusedRepairPlan &plan, const uint8_t *const *helper_bloc
   a.scratch = static_cast<uint4 *>(scratch);
   const size_t smem = fused_repair_smem(h);
   cudaError_t e;
+  if (alpha <= 8)
+    fused_repair_kernel<8><<<grid, kThreads, smem, stream>>>(a);
+  else
+    fused_repair_kernel<16><<<grid, kThreads, smem, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("fused repair launch: ") + cudaGetErrorString(e);
+    return kECuda;
+  }
+  return kOk;
+}
+
+int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *const *helper_blocks,
+                                uint8_t *const *out, size_t nbytes, cudaStream_t stream,
+                                std::string &err) {
+  const FusedRepairHeader &h = plan.header;
+  const int d = h.d, alpha = h.alpha;
+  if ((d + 1) * alpha > kRepMaxPtr || alpha > 16 || h.nz > 16) {
+    err = "code too large for the fused repair kernel";
+    return kEUnsupported;
+  }
+  if (plan.image.size() > kNoAllocTableBytes) {
+    err = "repair tables exceed the 64 KiB table area of the fixed scratch";
+    return kEUnsupported;
+  }
+  const size_t per_cta = (size_t)d * kThreads * kVec;
+  if (!h.direct && per_cta > kNoAllocProjBytes) {
+    err = "helper projections of one CTA exceed the 16 MiB fixed scratch";
+    return kEUnsupported;
+  }
+  RepairArgs a;
+  memset(a.ptr, 0, sizeof a.ptr);
+  bool aligned = true;
+  for (int q = 0; q < d; q++)
+    for (int j = 0; j < alpha; j++) {
+      const uint8_t *p = helper_blocks[q * alpha + j];
+      a.ptr[q * alpha + j] = const_cast<uint8_t *>(p);
+      bool used = false;
+      for (uint32_t i = 0; i < h.nz; i++) used |= (h.nzidx[i] == j);
+      if (used && !p) {
+        err = "a helper block the repair reads is NULL";
+        return kEInval;
+      }
+      if (p) aligned = aligned && ((uintptr_t)p % kVec == 0);
+    }
+  for (int r = 0; r < alpha; r++) {
+    if (!out[r]) {
+      err = "output block is NULL";
+      return kEInval;
+    }
+    a.ptr[d * alpha + r] = out[r];
+    aligned = aligned && ((uintptr_t)out[r] % kVec == 0);
+  }
+  if (nbytes == 0) return kOk;
+  // device address of the fixed scratch, looked up once per device with
+  // that device current (the host-side name is not a device address)
+  static std::mutex mu;
+  static std::map<int, uint8_t *> base_of;
+  int devid = -1;
+  cudaError_t e = cudaGetDevice(&devid);
+  if (e != cudaSuccess) {
+    err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return kECuda;
+  }
+  uint8_t *base = nullptr;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = base_of.find(devid);
+    if (it == base_of.end()) {
+      e = cudaGetSymbolAddress((void **)&base, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        err = std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e);
+        return kECuda;
+      }
+      base_of[devid] = base;
+    } else {
+      base = it->second;
+    }
+  }
+  e = cudaMemcpyAsync(base, plan.image.data(), plan.image.size(), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) {
+    err = std::string("copy of the repair tables: ") + cudaGetErrorString(e);
+    return kECuda;
+  }
+  const uint64_t tile = (uint64_t)kThreads * kVec;
+  a.image = base;
+  a.scratch = reinterpret_cast<uint4 *>(base + kNoAllocTableBytes);
+  a.nbytes = nbytes;
+  a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
+  a.aligned = aligned ? 1 : 0;
+  a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
+  unsigned grid = fused_repair_grid(a.ntiles);
+  if (!h.direct && grid > kNoAllocProjBytes / per_cta) grid = (unsigned)(kNoAllocProjBytes / per_cta);
+  const size_t smem = fused_repair_smem(h);
   if (alpha <= 8)
     fused_repair_kernel<8><<<grid, kThreads, smem, stream>>>(a);
   else

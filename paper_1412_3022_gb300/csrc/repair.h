@@ -45,4 +45,11 @@ int launch_fused_repair(FusedRepairPlan &plan, const uint8_t *const *helper_bloc
                         uint8_t *const *out, size_t nbytes, cudaStream_t stream, void *scratch,
                         size_t scratch_bytes, std::string &err);
 
+// Same repair with the fixed scratch array compiled into the library
+// instead of a caller-provided buffer; allocates no device memory (see
+// pmrc_repair_noalloc in include/pmrc.h).
+int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *const *helper_blocks,
+                                uint8_t *const *out, size_t nbytes, cudaStream_t stream,
+                                std::string &err);
+
 }  // namespace pmrc
