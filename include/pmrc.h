@@ -110,11 +110,10 @@ int pmrc_repair_newcomer(const pmrc_code *code, int failed, const int *helpers,
 
 /* Whole repair of node `failed` on one GPU: the d helper projections of
  * pmrc_repair_helper and the newcomer apply of pmrc_repair_newcomer in one
- * launch (same result as the two-step protocol).  The projections stay in a
- * stream-ordered scratch buffer (cudaMallocAsync/cudaFreeAsync on `stream`)
- * instead of going through caller memory; when phi_failed is a single 1
- * (sparse code, failed node among the alpha first, Sec. 3.3) the newcomer
- * reads the helpers' blocks directly and no scratch is used.
+ * launch (same result as the two-step protocol).  The projections stay in
+ * on-chip shared memory instead of going through device memory; when
+ * phi_failed is a single 1 (sparse code, failed node among the alpha first,
+ * Sec. 3.3) the newcomer reads the helpers' blocks directly.
  * helper_blocks: d*alpha pointers (helper i's alpha blocks at
  * [i*alpha, i*alpha + alpha)), entries with a zero helper coefficient may be
  * NULL.  out: alpha pointers.  Requires alpha <= 16. */
@@ -131,13 +130,13 @@ int pmrc_repair(const pmrc_code *code, int failed, const int *helpers,
  * this is an interface choice of this library.
  *
  * It allocates nothing on the device (no cudaMalloc/cudaFree, no
- * stream-ordered or library allocator).  Its scratch is one fixed array
- * compiled into the library: 64 KiB for the repair tables plus 16 MiB for
- * the helper projections, which every GPU that loads the library holds
- * until the process exits.  Each call copies the repair tables into the
- * array on `stream`; big blocks are run with fewer CTAs so the projections
- * fit.  A repair whose tables exceed 64 KiB is rejected with
- * PMRC_EUNSUPPORTED (no code with alpha <= 16 comes close).
+ * stream-ordered or library allocator): pmrc_repair uploads its repair
+ * tables once per (failed node, helpers, device) into device memory it
+ * allocates, whereas this entry point copies them, on every call, into one
+ * fixed 64 KiB array compiled into the library, which every GPU that loads
+ * the library holds until the process exits.  A repair whose tables exceed
+ * 64 KiB is rejected with PMRC_EUNSUPPORTED (no code with alpha <= 16 comes
+ * close: k = 16 needs about 10 KiB).
  *
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any
@@ -176,7 +175,7 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * and must stay valid while the batch is launched; pmrc_batch_launch reads
  * and writes them again each time.  Add all stripes, build, then launch any
  * number of times.  A batch is not thread-safe; launches of one batch must
- * not overlap on the GPU (they share a work counter and scratch). */
+ * not overlap on the GPU (they share a work counter). */
 typedef struct pmrc_batch pmrc_batch;
 
 int pmrc_batch_create(pmrc_batch **out);
@@ -209,7 +208,7 @@ int pmrc_batch_launch(pmrc_batch *batch, pmrc_stream_t stream);
 int pmrc_batch_tune(pmrc_batch *batch, pmrc_stream_t stream, int *best_out);
 
 /* info_out[8] = {stripes, work items, CTAs, work_bytes, ctas_per_sm,
- * user bytes per launch, scratch bytes, shared memory bytes per CTA}. */
+ * user bytes per launch, 0 (unused), shared memory bytes per CTA}. */
 int pmrc_batch_info(const pmrc_batch *batch, int64_t *info_out);
 
 /* Default helpers for node `failed`: the first d-subset of the survivors,

@@ -311,7 +311,7 @@ def pmrc_batch_info(batch) -> dict:
     out = (ctypes.c_int64 * 8)()
     _check(lib().pmrc_batch_info(batch, out), "pmrc_batch_info")
     return dict(zip(("stripes", "items", "ctas", "work_bytes", "ctas_per_sm", "user_bytes",
-                     "scratch_bytes", "smem_bytes"), list(out)))
+                     "unused", "smem_bytes"), list(out)))
 
 
 class Batch:

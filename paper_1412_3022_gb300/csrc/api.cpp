@@ -352,26 +352,7 @@ int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *co
   std::string err;
   int rc = fused_repair_plan(c, f, helpers, p, err);
   if (rc) return fail(rc, err);
-  if (nbytes == 0) return PMRC_OK;
-  const uint64_t tile = 256 * 16;
-  const unsigned grid = fused_repair_grid((uint32_t)((nbytes + tile - 1) / tile));
-  const size_t sb = fused_repair_scratch_bytes(p->header, grid);
-  void *scratch = nullptr;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (sb) {
-    cudaError_t e = cudaMallocAsync(&scratch, sb, st);
-    if (e != cudaSuccess)
-      return fail(e == cudaErrorMemoryAllocation ? PMRC_ENOMEM : PMRC_ECUDA,
-                  std::string("cudaMallocAsync(scratch): ") + cudaGetErrorString(e));
-  }
-  rc = launch_fused_repair(*p, blocks, out, nbytes, st, scratch, sb, err);
-  if (scratch) {
-    cudaError_t e = cudaFreeAsync(scratch, st);
-    if (!rc && e != cudaSuccess) {
-      rc = PMRC_ECUDA;
-      err = std::string("cudaFreeAsync(scratch): ") + cudaGetErrorString(e);
-    }
-  }
+  rc = launch_fused_repair(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
   return rc ? fail(rc, err) : PMRC_OK;
 }
 

@@ -31,6 +31,7 @@ namespace pmrc {
 namespace {
 
 #include "region_dev.cuh"
+#include "repair_dev.cuh"
 
 constexpr int kBatchR = 16;  // rows in registers: covers alpha <= 16 and plans with R <= 16
 
@@ -52,8 +53,6 @@ struct BatchArgs {
   const BatchItem *items;
   int nitems;
   unsigned *counter;
-  uint4 *scratch;   // per-CTA slices for fused repair projections
-  int scratch_d;    // projections per slice
   MulConsts k;
 };
 
@@ -62,7 +61,6 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_item;
   const MulConsts k = a.k;
-  uint4 *slice = a.scratch + (size_t)blockIdx.x * a.scratch_d * kThreads + threadIdx.x;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
     __syncthreads();
@@ -101,10 +99,11 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
       }
     } else {
       const FusedRepairHeader *hp = reinterpret_cast<const FusedRepairHeader *>(w.image);
-      const int d = hp->d, alpha = hp->alpha, nz = hp->nz;
+      const int d = hp->d, alpha = hp->alpha, nz = hp->nz, rl = hp->rl;
       const bool direct = hp->direct != 0;
-      const int n1 = nz, n2 = d * alpha;
-      uint4 *t1a = reinterpret_cast<uint4 *>(smem);
+      const int n1 = nz, n2 = d * 4 * rl;
+      uint4 *proj = reinterpret_cast<uint4 *>(smem);
+      uint4 *t1a = proj + (size_t)d * kRepCols;
       uint4 *t2a = t1a + n1;
       uint32_t *t1b = reinterpret_cast<uint32_t *>(t2a + n2);
       uint32_t *t2b = t1b + n1;
@@ -117,31 +116,11 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
       }
       if (threadIdx.x < 16) s_nz[threadIdx.x] = hp->nzidx[threadIdx.x];
       __syncthreads();
-      for (uint32_t tile = w.tile0; tile < w.tile0 + w.ntiles; tile++) {
-        const uint64_t off = ((uint64_t)tile * kThreads + threadIdx.x) * kVec;
-        if (off >= w.nbytes) continue;
-        if (!direct)
-          for (int q = 0; q < d; q++) {
-            uint32_t acc1[1][4];
-            mac_block<1>(acc1, nz, 1, 1, t1a, t1b, k, [&](int i) {
-              return load16(w.ptrs[q * alpha + s_nz[i]], off, w.nbytes, vec);
-            });
-            slice[(size_t)q * kThreads] = acc_bytes(acc1[0]);
-          }
-        uint32_t acc[R][4];
-        if (direct) {
-          const int j0 = s_nz[0];
-          mac_block<R>(acc, d, alpha, alpha, t2a, t2b, k, [&](int q) {
-            return load16(w.ptrs[q * alpha + j0], off, w.nbytes, vec);
-          });
-        } else {
-          mac_block<R>(acc, d, alpha, alpha, t2a, t2b, k,
-                       [&](int q) { return slice[(size_t)q * kThreads]; });
-        }
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          if (r < alpha) store16(w.ptrs[d * alpha + r], off, w.nbytes, vec, acc_bytes(acc[r]));
-      }
+      const uint64_t span_end = (uint64_t)(w.tile0 + w.ntiles) * kThreads * kVec;
+      const uint64_t end = span_end < w.nbytes ? span_end : w.nbytes;
+      for (uint64_t t = (uint64_t)w.tile0 * kThreads * kVec; t < end; t += kRepTile)
+        fused_repair_tile<0>(w.ptrs, t, w.nbytes, vec, d, alpha, nz, direct, s_nz, t1a, t1b, t2a,
+                             t2b, rl, proj, k);
     }
     __syncthreads();
   }
@@ -177,9 +156,6 @@ struct pmrc_batch {
   uint8_t **d_ptrs = nullptr;
   BatchItem *d_items = nullptr;
   unsigned *d_counter = nullptr;
-  uint4 *d_scratch = nullptr;
-  size_t scratch_bytes = 0;
-  int scratch_d = 0;
   int nitems = 0;
   unsigned grid = 0;
   size_t smem = 0;
@@ -196,14 +172,12 @@ struct pmrc_batch {
     cudaFree(d_ptrs);
     cudaFree(d_items);
     cudaFree(d_counter);
-    cudaFree(d_scratch);
     exec = nullptr;
     graph = nullptr;
     cap = nullptr;
     d_ptrs = nullptr;
     d_items = nullptr;
     d_counter = nullptr;
-    d_scratch = nullptr;
     built = false;
   }
   ~pmrc_batch() { release_device(); }
@@ -272,7 +246,6 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   });
   std::vector<BatchItem> items;
   size_t smem = 64;
-  int scratch_d = 0;
   for (size_t s : order) {
     const Stripe &S = b->stripes[s];
     const uint32_t ntiles = (uint32_t)((S.nbytes + tile - 1) / tile);
@@ -304,8 +277,7 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
         const FusedRepairHeader &h = S.fplan->header;
         w.type = 1;
         items.push_back(w);
-        smem = std::max(smem, (size_t)(h.nz + (size_t)h.d * h.alpha) * 20 + 64);
-        if (!h.direct) scratch_d = std::max(scratch_d, (int)h.d);
+        smem = std::max(smem, fused_repair_smem(h) + 64);
       }
     }
   }
@@ -333,22 +305,11 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   const int per_sm = std::max(1, std::min(ctas_per_sm, fit));
   b->grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, std::max(1, b->nitems)));
   b->smem = smem;
-  b->scratch_d = scratch_d;
-  b->scratch_bytes = (size_t)b->grid * scratch_d * kThreads * kVec;
-  if (b->scratch_bytes) {
-    e = cudaMalloc(&b->d_scratch, b->scratch_bytes);
-    if (e != cudaSuccess) {
-      err = std::string("batch scratch: ") + cudaGetErrorString(e);
-      return e == cudaErrorMemoryAllocation ? kENoMem : kECuda;
-    }
-  }
   // graph: counter reset + persistent kernel
   BatchArgs args;
   args.items = b->d_items;
   args.nitems = b->nitems;
   args.counter = b->d_counter;
-  args.scratch = b->d_scratch;
-  args.scratch_d = scratch_d;
   args.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
@@ -547,7 +508,7 @@ int pmrc_batch_info(const pmrc_batch *b, int64_t *info) {
   info[3] = b->work_bytes;
   info[4] = b->ctas_per_sm;
   info[5] = b->user_bytes;
-  info[6] = (int64_t)b->scratch_bytes;
+  info[6] = 0;
   info[7] = (int64_t)b->smem;
   return PMRC_OK;
 }

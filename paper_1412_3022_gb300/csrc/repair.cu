@@ -4,12 +4,13 @@
 //
 // In the paper's system the helpers send p_h over the network (Sec. 2, 3.3).
 // When helpers and newcomer share a GPU, the projections need not visit
-// caller memory: each thread computes its 16 bytes of every p_h, parks them
-// in a scratch slice private to its CTA (the write and the read-back are by
-// the same thread, so no barrier is needed and the slice stays in L2), then
-// applies D.  When phi_f has a single non-zero equal to 1 (sparse code,
-// failed node among the alpha first) p_h is a block the helper already
-// stores, and the newcomer reads it in place.
+// device memory at all: a CTA covers 1 KiB of byte column with 4 lanes of 64
+// threads, the lanes split the d projections (stage 1, all of a helper's
+// loads issued before they are used), park them in shared memory, and then
+// split the alpha output rows (stage 2, repair_dev.cuh).  When phi_f has a
+// single non-zero equal to 1 (sparse code, failed node among the alpha
+// first) p_h is a block the helper already stores, and the newcomer reads it
+// in place.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -22,30 +23,32 @@ namespace pmrc {
 namespace {
 
 #include "region_dev.cuh"
+#include "repair_dev.cuh"
 
 constexpr int kRepMaxPtr = 512;
 
 struct RepairArgs {
-  const uint8_t *image;  // FusedRepairImage (device)
-  uint4 *scratch;        // gridDim.x * d * kThreads vectors (unused if direct)
+  const uint8_t *image;  // FusedRepairHeader + split tables (device)
   uint64_t nbytes;
-  uint32_t ntiles;
+  uint32_t ntiles;       // 1 KiB tiles
   int aligned;
   MulConsts k;
   uint8_t *ptr[kRepMaxPtr];  // d*alpha helper blocks, then alpha outputs
 };
 
-template <int RN>
-__global__ void __launch_bounds__(kThreads) fused_repair_kernel(const __grid_constant__ RepairArgs a) {
+// Shared memory: split tables, then the d x 64 projection vectors.
+template <int NZ>
+__global__ void __launch_bounds__(kThreads, 2) fused_repair_kernel(const __grid_constant__ RepairArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint16_t s_nz[16];
   const FusedRepairHeader *hp = reinterpret_cast<const FusedRepairHeader *>(a.image);
-  const int d = hp->d, alpha = hp->alpha, nz = hp->nz;
+  const int d = hp->d, alpha = hp->alpha, nz = hp->nz, rl = hp->rl;
   const bool direct = hp->direct != 0;
   const uint32_t tab4_off = hp->tab4_off, tab1_off = hp->tab1_off;
   if (threadIdx.x < 16) s_nz[threadIdx.x] = hp->nzidx[threadIdx.x];
-  const int n1 = nz, n2 = d * alpha;
-  uint4 *t1a = reinterpret_cast<uint4 *>(smem);
+  const int n1 = nz, n2 = d * 4 * rl;
+  uint4 *proj = reinterpret_cast<uint4 *>(smem);
+  uint4 *t1a = proj + (size_t)d * kRepCols;
   uint4 *t2a = t1a + n1;
   uint32_t *t1b = reinterpret_cast<uint32_t *>(t2a + n2);
   uint32_t *t2b = t1b + n1;
@@ -60,45 +63,63 @@ __global__ void __launch_bounds__(kThreads) fused_repair_kernel(const __grid_con
   __syncthreads();
   const MulConsts k = a.k;
   const bool vec = a.aligned != 0;
-  uint4 *slice = a.scratch + (size_t)blockIdx.x * d * kThreads + threadIdx.x;
-  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const uint64_t off = ((uint64_t)tile * kThreads + threadIdx.x) * kVec;
-    if (off >= a.nbytes) continue;
-    if (!direct) {
-      // stage 1: projections of the d helpers (one row, nz inputs each)
-      for (int q = 0; q < d; q++) {
-        uint32_t acc1[1][4];
-        mac_block<1>(acc1, nz, 1, 1, t1a, t1b, k, [&](int i) {
-          return load16(a.ptr[q * alpha + s_nz[i]], off, a.nbytes, vec);
-        });
-        slice[(size_t)q * kThreads] = acc_bytes(acc1[0]);
+  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
+    fused_repair_tile<NZ>(a.ptr, (uint64_t)tile * kRepTile, a.nbytes, vec, d, alpha, nz, direct,
+                          s_nz, t1a, t1b, t2a, t2b, rl, proj, k);
+}
+
+// Fills the pointer table of a launch; checks NULL blocks and alignment.
+int repair_pointers(const FusedRepairHeader &h, const uint8_t *const *helper_blocks,
+                    uint8_t *const *out, RepairArgs &a, std::string &err) {
+  const int d = h.d, alpha = h.alpha;
+  memset(a.ptr, 0, sizeof a.ptr);
+  bool aligned = true;
+  for (int q = 0; q < d; q++)
+    for (int j = 0; j < alpha; j++) {
+      const uint8_t *p = helper_blocks[q * alpha + j];
+      a.ptr[q * alpha + j] = const_cast<uint8_t *>(p);
+      bool used = false;
+      for (uint32_t i = 0; i < h.nz; i++) used |= (h.nzidx[i] == j);
+      if (used && !p) {
+        err = "a helper block the repair reads is NULL";
+        return kEInval;
       }
+      if (p) aligned = aligned && ((uintptr_t)p % kVec == 0);
     }
-    // stage 2: newcomer, alpha rows over the d projections
-    uint32_t acc[RN][4];
-    if (direct) {
-      const int j0 = s_nz[0];
-      mac_block<RN>(acc, d, alpha, alpha, t2a, t2b, k, [&](int q) {
-        return load16(a.ptr[q * alpha + j0], off, a.nbytes, vec);
-      });
-    } else {
-      mac_block<RN>(acc, d, alpha, alpha, t2a, t2b, k,
-                    [&](int q) { return slice[(size_t)q * kThreads]; });
+  for (int r = 0; r < alpha; r++) {
+    if (!out[r]) {
+      err = "output block is NULL";
+      return kEInval;
     }
-#pragma unroll
-    for (int r = 0; r < RN; r++)
-      if (r < alpha) store16(a.ptr[d * alpha + r], off, a.nbytes, vec, acc_bytes(acc[r]));
+    a.ptr[d * alpha + r] = out[r];
+    aligned = aligned && ((uintptr_t)out[r] % kVec == 0);
   }
+  a.aligned = aligned ? 1 : 0;
+  return kOk;
+}
+
+cudaError_t repair_launch(const FusedRepairHeader &h, RepairArgs &a, const void *image,
+                          size_t nbytes, cudaStream_t stream) {
+  a.image = static_cast<const uint8_t *>(image);
+  a.nbytes = nbytes;
+  a.ntiles = (uint32_t)((nbytes + kRepTile - 1) / kRepTile);
+  a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
+  const unsigned grid = fused_repair_grid(a.ntiles);
+  const size_t smem = fused_repair_smem(h);
+  if (h.nz <= 8)
+    fused_repair_kernel<8><<<grid, kThreads, smem, stream>>>(a);
+  else
+    fused_repair_kernel<16><<<grid, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-// Fixed scratch of pmrc_repair_noalloc: the repair's split tables in the
-// first kNoAllocTableBytes, the helper projections after them.  Every GPU
-// that loads the library holds it until the process exits.
+// Fixed scratch of pmrc_repair_noalloc: room for the repair's header and
+// split tables.  Every GPU that loads the library holds it until the
+// process exits.
 constexpr size_t kNoAllocTableBytes = 64u << 10;
-constexpr size_t kNoAllocProjBytes = 16u << 20;
-static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocTableBytes + kNoAllocProjBytes];
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocTableBytes];
 
 std::shared_ptr<FusedRepairPlan> make_fused_repair_plan(const std::vector<uint8_t> &phi,
                                                         const Mat &D) {
@@ -114,7 +135,8 @@ std::shared_ptr<FusedRepairPlan> make_fused_repair_plan(const std::vector<uint8_
   h.nz = (uint32_t)nzl.size();
   for (size_t i = 0; i < nzl.size(); i++) h.nzidx[i] = (uint16_t)nzl[i];
   h.direct = (nzl.size() == 1 && phi[nzl[0]] == 1) ? 1u : 0u;
-  const size_t n1 = nzl.size(), n2 = (size_t)d * alpha;
+  h.rl = (uint32_t)((alpha + 3) / 4);
+  const size_t n1 = nzl.size(), n2 = (size_t)d * 4 * h.rl;
   h.tab4_off = (uint32_t)((sizeof(FusedRepairHeader) + 15) & ~(size_t)15);
   h.tab1_off = h.tab4_off + (uint32_t)((n1 + n2) * sizeof(TabEntry));
   p->image.assign(h.tab1_off + (n1 + n2) * 4 + 16, 0);
@@ -125,72 +147,43 @@ std::shared_ptr<FusedRepairPlan> make_fused_repair_plan(const std::vector<uint8_
     memcpy(p->image.data() + h.tab1_off + e * 4, &w[4], 4);
   };
   for (size_t i = 0; i < n1; i++) put(i, phi[nzl[i]]);
-  for (int q = 0; q < d; q++)  // entry (input q, row r) at n1 + q * alpha + r
-    for (int r = 0; r < alpha; r++) put(n1 + (size_t)q * alpha + r, D.at(r, q));
+  for (int q = 0; q < d; q++)  // entry (input q, lane l, m) holds row l + 4m
+    for (int l = 0; l < 4; l++)
+      for (uint32_t m = 0; m < h.rl; m++) {
+        const int r = l + 4 * (int)m;
+        put(n1 + ((size_t)q * 4 + l) * h.rl + m, r < alpha ? D.at(r, q) : 0);
+      }
   memcpy(p->image.data(), &h, sizeof h);
   p->header = h;
   return p;
 }
 
 size_t fused_repair_smem(const FusedRepairHeader &h) {
-  return (size_t)(h.nz + (size_t)h.d * h.alpha) * 20;
+  return (size_t)h.d * kRepCols * kVec + (size_t)(h.nz + (size_t)h.d * 4 * h.rl) * 20;
 }
 
-int launch_fused_repair(FusedRepairPlan &plan, const uint8_t *const *helper_blocks,
-                        uint8_t *const *out, size_t nbytes, cudaStream_t stream, void *scratch,
-                        size_t scratch_bytes, std::string &err) {
-  const FusedRepairHeader &h = plan.header;
-  const int d = h.d, alpha = h.alpha;
-  if ((d + 1) * alpha > kRepMaxPtr || alpha > 16 || h.nz > 16) {
+static int check_repair_size(const FusedRepairHeader &h, std::string &err) {
+  if ((h.d + 1) * h.alpha > (uint32_t)kRepMaxPtr || h.alpha > 16 || h.nz > 16) {
     err = "code too large for the fused repair kernel";
     return kEUnsupported;
   }
-  if (nbytes == 0) return kOk;
-  RepairArgs a;
-  memset(a.ptr, 0, sizeof a.ptr);
-  bool aligned = true;
-  for (int q = 0; q < d; q++)
-    for (int j = 0; j < alpha; j++) {
-      const uint8_t *p = helper_blocks[q * alpha + j];
-      a.ptr[q * alpha + j] = const_cast<uint8_t *>(p);
-      bool used = false;
-      for (uint32_t i = 0; i < h.nz; i++) used |= (h.nzidx[i] == j);
-      if (used && !p) {
-        err = "a helper block the repair reads is NULL";
-        return kEInval;
-      }
-      if (p) aligned = aligned && ((uintptr_t)p % kVec == 0);
-    }
-  for (int r = 0; r < alpha; r++) {
-    if (!out[r]) {
-      err = "output block is NULL";
-      return kEInval;
-    }
-    a.ptr[d * alpha + r] = out[r];
-    aligned = aligned && ((uintptr_t)out[r] % kVec == 0);
-  }
-  const void *image = nullptr;
-  int rc = plan.device_image(&image, err);
+  return kOk;
+}
+
+int launch_fused_repair(FusedRepairPlan &plan, const uint8_t *const *helper_blocks,
+                        uint8_t *const *out, size_t nbytes, cudaStream_t stream,
+                        std::string &err) {
+  const FusedRepairHeader &h = plan.header;
+  int rc = check_repair_size(h, err);
   if (rc) return rc;
-  const uint64_t tile = (uint64_t)kThreads * kVec;
-  a.image = static_cast<const uint8_t *>(image);
-  a.nbytes = nbytes;
-  a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
-  a.aligned = aligned ? 1 : 0;
-  a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
-  const unsigned grid = fused_repair_grid(a.ntiles);
-  if (!h.direct && scratch_bytes < fused_repair_scratch_bytes(h, grid)) {
-    err = "scratch buffer too small";
-    return kEInval;
-  }
-  a.scratch = static_cast<uint4 *>(scratch);
-  const size_t smem = fused_repair_smem(h);
-  cudaError_t e;
-  if (alpha <= 8)
-    fused_repair_kernel<8><<<grid, kThreads, smem, stream>>>(a);
-  else
-    fused_repair_kernel<16><<<grid, kThreads, smem, stream>>>(a);
-  e = cudaGetLastError();
+  RepairArgs a;
+  rc = repair_pointers(h, helper_blocks, out, a, err);
+  if (rc) return rc;
+  if (nbytes == 0) return kOk;
+  const void *image = nullptr;
+  rc = plan.device_image(&image, err);
+  if (rc) return rc;
+  cudaError_t e = repair_launch(h, a, image, nbytes, stream);
   if (e != cudaSuccess) {
     err = std::string("fused repair launch: ") + cudaGetErrorString(e);
     return kECuda;
@@ -202,43 +195,15 @@ int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *cons
                                 uint8_t *const *out, size_t nbytes, cudaStream_t stream,
                                 std::string &err) {
   const FusedRepairHeader &h = plan.header;
-  const int d = h.d, alpha = h.alpha;
-  if ((d + 1) * alpha > kRepMaxPtr || alpha > 16 || h.nz > 16) {
-    err = "code too large for the fused repair kernel";
-    return kEUnsupported;
-  }
+  int rc = check_repair_size(h, err);
+  if (rc) return rc;
   if (plan.image.size() > kNoAllocTableBytes) {
-    err = "repair tables exceed the 64 KiB table area of the fixed scratch";
-    return kEUnsupported;
-  }
-  const size_t per_cta = (size_t)d * kThreads * kVec;
-  if (!h.direct && per_cta > kNoAllocProjBytes) {
-    err = "helper projections of one CTA exceed the 16 MiB fixed scratch";
+    err = "repair tables exceed the 64 KiB fixed scratch";
     return kEUnsupported;
   }
   RepairArgs a;
-  memset(a.ptr, 0, sizeof a.ptr);
-  bool aligned = true;
-  for (int q = 0; q < d; q++)
-    for (int j = 0; j < alpha; j++) {
-      const uint8_t *p = helper_blocks[q * alpha + j];
-      a.ptr[q * alpha + j] = const_cast<uint8_t *>(p);
-      bool used = false;
-      for (uint32_t i = 0; i < h.nz; i++) used |= (h.nzidx[i] == j);
-      if (used && !p) {
-        err = "a helper block the repair reads is NULL";
-        return kEInval;
-      }
-      if (p) aligned = aligned && ((uintptr_t)p % kVec == 0);
-    }
-  for (int r = 0; r < alpha; r++) {
-    if (!out[r]) {
-      err = "output block is NULL";
-      return kEInval;
-    }
-    a.ptr[d * alpha + r] = out[r];
-    aligned = aligned && ((uintptr_t)out[r] % kVec == 0);
-  }
+  rc = repair_pointers(h, helper_blocks, out, a, err);
+  if (rc) return rc;
   if (nbytes == 0) return kOk;
   // device address of the fixed scratch, looked up once per device with
   // that device current (the host-side name is not a device address)
@@ -266,27 +231,9 @@ int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *cons
     }
   }
   e = cudaMemcpyAsync(base, plan.image.data(), plan.image.size(), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = repair_launch(h, a, base, nbytes, stream);
   if (e != cudaSuccess) {
-    err = std::string("copy of the repair tables: ") + cudaGetErrorString(e);
-    return kECuda;
-  }
-  const uint64_t tile = (uint64_t)kThreads * kVec;
-  a.image = base;
-  a.scratch = reinterpret_cast<uint4 *>(base + kNoAllocTableBytes);
-  a.nbytes = nbytes;
-  a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
-  a.aligned = aligned ? 1 : 0;
-  a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
-  unsigned grid = fused_repair_grid(a.ntiles);
-  if (!h.direct && grid > kNoAllocProjBytes / per_cta) grid = (unsigned)(kNoAllocProjBytes / per_cta);
-  const size_t smem = fused_repair_smem(h);
-  if (alpha <= 8)
-    fused_repair_kernel<8><<<grid, kThreads, smem, stream>>>(a);
-  else
-    fused_repair_kernel<16><<<grid, kThreads, smem, stream>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    err = std::string("fused repair launch: ") + cudaGetErrorString(e);
+    err = std::string("fused repair (fixed scratch): ") + cudaGetErrorString(e);
     return kECuda;
   }
   return kOk;
@@ -301,10 +248,6 @@ unsigned fused_repair_grid(uint32_t ntiles) {
   }
   const uint32_t cap = (uint32_t)sms * 2;
   return ntiles < cap ? (ntiles ? ntiles : 1) : cap;
-}
-
-size_t fused_repair_scratch_bytes(const FusedRepairHeader &h, unsigned grid) {
-  return h.direct ? 0 : (size_t)grid * h.d * kThreads * kVec;
 }
 
 int FusedRepairPlan::device_image(const void **out, std::string &err) {

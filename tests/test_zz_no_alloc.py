@@ -3,8 +3,8 @@ allocate GPU memory -- returns the same bytes as pmrc_repair.
 
 Both are called through the C ABI on the same stored codeword, twice in a
 row (a failed node whose helpers must project alpha blocks, then one whose
-helpers send a stored block as is), and once more for a larger code whose
-projections need more CTAs than the fixed scratch holds at once.  The bar is
+helpers send a stored block as is), and again for the largest code the
+fixed table area is meant for (k=16, alpha=15).  The bar is
 the one every test here uses: byte-for-byte equality.  This file is
 collected last so that a run stopping at its first failure has already run
 everything else; it passes alone in a fresh process as well.
@@ -65,7 +65,7 @@ def test_repair_noalloc_matches_repair_on_two_calls_in_a_row():
     compare(c, Y, 3, nbytes)    # helpers send one stored block
 
 
-def test_repair_noalloc_matches_repair_when_scratch_limits_the_grid():
+def test_repair_noalloc_matches_repair_for_k16():
     c = P.Code(32, 16, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
     nbytes = (3 << 20) + 5
     Y = codeword(c, nbytes, seed=12)
