@@ -211,6 +211,69 @@ int pmrc_batch_tune(pmrc_batch *batch, pmrc_stream_t stream, int *best_out);
  * user bytes per launch, 0 (unused), shared memory bytes per CTA}. */
 int pmrc_batch_info(const pmrc_batch *batch, int64_t *info_out);
 
+/* ---- serving -------------------------------------------------------------
+ * A request loop with continuous batching: a scheduler thread admits
+ * requests in arrival order while a slot is free and the device budget has
+ * room for the request's inputs and outputs, copies their inputs in while
+ * the previous iteration computes, runs every request whose inputs have
+ * landed in one persistent launch (the batched kernel), and copies results
+ * back, recording submit-to-completion latency.  Each request gives the same
+ * bytes as the corresponding single call.  Requests use HOST buffers; make
+ * them pinned (cudaMallocHost / cudaHostRegister) so the copies run
+ * asynchronously, and keep them alive until the request is finished. */
+typedef struct pmrc_server pmrc_server;
+
+enum { PMRC_OP_ENCODE = 0, PMRC_OP_REPAIR = 1, PMRC_OP_DECODE = 2 };
+
+typedef struct {
+  int op;                 /* PMRC_OP_*                                          */
+  const pmrc_code *code;  /* must outlive the request                           */
+  size_t block_bytes;     /* B                                                  */
+  const uint8_t *in;      /* host, contiguous blocks of B bytes:
+                             ENCODE: k*alpha data blocks;
+                             REPAIR: d*alpha blocks, helper i's alpha blocks at
+                                     [i*alpha, i*alpha + alpha) (all alpha sent);
+                             DECODE: k*alpha blocks of `nodes`, node-major      */
+  uint8_t *out;           /* host: ENCODE: the pmrc_encode outputs ((n-k)*alpha
+                             or n*alpha blocks); REPAIR: alpha blocks of node
+                             `failed`; DECODE: k*alpha data blocks             */
+  int failed;             /* REPAIR                                             */
+  const int *helpers;     /* REPAIR: d node ids (copied at submit)              */
+  const int *nodes;       /* DECODE: k node ids (copied at submit)              */
+} pmrc_request;
+
+/* Starts a server on the current device with a device arena of
+ * budget_bytes (allocated once, the HBM budget of in-flight requests) and at
+ * most max_slots requests admitted at a time. */
+int pmrc_server_create(size_t budget_bytes, int max_slots, pmrc_server **out);
+
+/* Finishes every submitted request, stops the scheduler and frees the
+ * server.  NULL is ignored. */
+void pmrc_server_destroy(pmrc_server *server);
+
+/* Queues a request (validated now: PMRC_ENOMEM if it cannot fit the budget
+ * even alone, PMRC_ESINGULAR for bad helper/node sets).  *id_out receives
+ * its id. */
+int pmrc_server_submit(pmrc_server *server, const pmrc_request *request, uint64_t *id_out);
+
+/* 1 if the request finished (status and latency filled in; the record is
+ * then dropped and the id becomes unknown), 0 if not yet. */
+int pmrc_server_poll(pmrc_server *server, uint64_t id, int *status, double *latency_ms);
+
+/* Waits up to timeout_ms (< 0: forever) for the request; PMRC_ETIMEOUT if it
+ * is still running.  On success the record is dropped as in poll. */
+int pmrc_server_wait(pmrc_server *server, uint64_t id, int timeout_ms, int *status,
+                     double *latency_ms);
+
+/* Withdraws a request that is still queued (PMRC_EBUSY once admitted). */
+int pmrc_server_cancel(pmrc_server *server, uint64_t id);
+
+/* stats_out[10] = {completed, failed, p50 latency ms, p99 ms, max ms, user
+ * bytes completed, user GB/s from first submit to last completion, peak
+ * device bytes in use, iterations launched, budget bytes}. */
+int pmrc_server_stats(pmrc_server *server, double *stats_out);
+int pmrc_server_reset_stats(pmrc_server *server);
+
 /* Default helpers for node `failed`: the first d-subset of the survivors,
  * in lexicographic order, whose Psi rows are invertible (the d lowest ids
  * when they qualify).  helpers_out: d ints. */

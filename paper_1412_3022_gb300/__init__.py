@@ -33,6 +33,10 @@ PMRC_KERNEL_AUTO = 0
 PMRC_KERNEL_GENERIC = 1
 PMRC_KERNEL_BITSLICED = 2
 
+PMRC_OP_ENCODE = 0
+PMRC_OP_REPAIR = 1
+PMRC_OP_DECODE = 2
+
 PMRC_VANILLA = 0
 PMRC_SPARSE = 1
 PMRC_NONSYSTEMATIC = 0
@@ -56,6 +60,12 @@ _vp = ctypes.c_void_p
 _pp = ctypes.POINTER(ctypes.c_void_p)
 _ip = ctypes.POINTER(ctypes.c_int)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
+
+class pmrc_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("code", ctypes.c_void_p), ("block_bytes", ctypes.c_size_t),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("failed", ctypes.c_int),
+                ("helpers", ctypes.POINTER(ctypes.c_int)), ("nodes", ctypes.POINTER(ctypes.c_int))]
+
 
 _SIGNATURES = {
     "pmrc_create": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
@@ -85,6 +95,14 @@ _SIGNATURES = {
     "pmrc_batch_launch": (_i, [_vp, _vp]),
     "pmrc_batch_tune": (_i, [_vp, _vp, _ip]),
     "pmrc_batch_info": (_i, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "pmrc_server_create": (_i, [_sz, _i, ctypes.POINTER(_vp)]),
+    "pmrc_server_destroy": (None, [_vp]),
+    "pmrc_server_submit": (_i, [_vp, ctypes.POINTER(pmrc_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "pmrc_server_poll": (_i, [_vp, ctypes.c_uint64, _ip, ctypes.POINTER(ctypes.c_double)]),
+    "pmrc_server_wait": (_i, [_vp, ctypes.c_uint64, _i, _ip, ctypes.POINTER(ctypes.c_double)]),
+    "pmrc_server_cancel": (_i, [_vp, ctypes.c_uint64]),
+    "pmrc_server_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "pmrc_server_reset_stats": (_i, [_vp]),
 }
 
 
@@ -357,6 +375,100 @@ class Batch:
 
     def info(self):
         return pmrc_batch_info(self.handle)
+
+
+# ---------------------------------------------------------------- serving
+def pmrc_server_create(budget_bytes: int, max_slots: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pmrc_server_create(budget_bytes, max_slots, ctypes.byref(h)),
+           "pmrc_server_create")
+    return int(h.value)
+
+
+def pmrc_server_destroy(server) -> None:
+    if server:
+        lib().pmrc_server_destroy(server)
+
+
+def pmrc_server_submit(server, op, code, block_bytes, in_ptr, out_ptr, failed=-1,
+                       helpers=None, nodes=None) -> int:
+    hs = _ints(helpers) if helpers is not None else None
+    ns = _ints(nodes) if nodes is not None else None
+    req = pmrc_request(op, code, block_bytes, _addr(in_ptr), _addr(out_ptr), failed,
+                       ctypes.cast(hs, ctypes.POINTER(ctypes.c_int)) if hs is not None else None,
+                       ctypes.cast(ns, ctypes.POINTER(ctypes.c_int)) if ns is not None else None)
+    rid = ctypes.c_uint64()
+    _check(lib().pmrc_server_submit(server, ctypes.byref(req), ctypes.byref(rid)),
+           "pmrc_server_submit")
+    return rid.value
+
+
+def pmrc_server_poll(server, rid):
+    st, lat = ctypes.c_int(), ctypes.c_double()
+    done = _check(lib().pmrc_server_poll(server, rid, ctypes.byref(st), ctypes.byref(lat)),
+                  "pmrc_server_poll")
+    return (st.value, lat.value) if done else None
+
+
+def pmrc_server_wait(server, rid, timeout_ms=-1):
+    st, lat = ctypes.c_int(), ctypes.c_double()
+    _check(lib().pmrc_server_wait(server, rid, timeout_ms, ctypes.byref(st), ctypes.byref(lat)),
+           "pmrc_server_wait")
+    return st.value, lat.value
+
+
+def pmrc_server_cancel(server, rid) -> None:
+    _check(lib().pmrc_server_cancel(server, rid), "pmrc_server_cancel")
+
+
+def pmrc_server_stats(server) -> dict:
+    out = (ctypes.c_double * 10)()
+    _check(lib().pmrc_server_stats(server, out), "pmrc_server_stats")
+    keys = ("completed", "failed", "p50_ms", "p99_ms", "max_ms", "user_bytes", "user_GBps",
+            "peak_bytes", "iterations", "budget_bytes")
+    return dict(zip(keys, list(out)))
+
+
+def pmrc_server_reset_stats(server) -> None:
+    _check(lib().pmrc_server_reset_stats(server), "pmrc_server_reset_stats")
+
+
+class Server:
+    """Owns a pmrc_server; submit() takes host buffers (tensors or addresses)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64):
+        self.handle = pmrc_server_create(budget_bytes, max_slots)
+
+    def close(self):
+        if self.handle:
+            pmrc_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, op, code, block_bytes, in_buf, out_buf, failed=-1, helpers=None,
+               nodes=None):
+        return pmrc_server_submit(self.handle, op, code.handle, block_bytes, in_buf, out_buf,
+                                  failed, helpers, nodes)
+
+    def poll(self, rid):
+        return pmrc_server_poll(self.handle, rid)
+
+    def wait(self, rid, timeout_ms=-1):
+        return pmrc_server_wait(self.handle, rid, timeout_ms)
+
+    def cancel(self, rid):
+        pmrc_server_cancel(self.handle, rid)
+
+    def stats(self):
+        return pmrc_server_stats(self.handle)
+
+    def reset_stats(self):
+        pmrc_server_reset_stats(self.handle)
 
 
 # ---------------------------------------------------------------- handle

@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpmrc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["region.cu", "bitslice.cu", "repair.cu", "batch.cu", "plan.cpp", "code.cpp",
-           "api.cpp"]
+SOURCES = ["region.cu", "bitslice.cu", "repair.cu", "batch.cu", "serve.cu", "plan.cpp",
+           "code.cpp", "api.cpp"]
 
 
 def nvcc() -> str:

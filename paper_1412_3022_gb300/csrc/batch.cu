@@ -5,27 +5,27 @@
 // range of 4 KiB byte tiles) for encode and decode, (fused repair x range of
 // tiles) for repair.  A persistent grid pulls items from an atomic counter
 // (reset by a memset node in the same graph), stages the item's split tables
-// in shared memory and runs the same inner loop as the single-stripe
-// kernels (region_dev.cuh).  Items are listed biggest stripe first so the
-// dynamic pull balances the tail.  Item size and CTAs per SM are tunable
-// (pmrc_batch_tune times candidates on the device and keeps the fastest).
+// in shared memory and runs the same inner loops as the single-stripe
+// kernels (region_dev.cuh, repair_dev.cuh).  Items are listed biggest stripe
+// first so the dynamic pull balances the tail.  Item size and CTAs per SM
+// are tunable (pmrc_batch_tune times candidates on the device and keeps the
+// fastest).  The serving loop (serve.cu) launches the same kernel on work
+// lists it rebuilds every iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <chrono>
-#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
 #include "../../include/pmrc.h"
 #include "api_internal.h"
+#include "batch_internal.h"
 #include "gf256.h"
-#include "plan.h"
-#include "repair.h"
 
 namespace pmrc {
 namespace {
@@ -35,23 +35,10 @@ namespace {
 
 constexpr int kBatchR = 16;  // rows in registers: covers alpha <= 16 and plans with R <= 16
 
-struct BatchItem {
-  const uint8_t *image;   // region plan image, or fused repair image
-  uint8_t *const *ptrs;   // this stripe's pointers: inputs, then outputs
-  uint64_t nbytes;        // block size of the stripe
-  uint32_t tile0, ntiles; // tile range
-  uint32_t idx_base, tab4_base, tab1_base;  // region image offsets
-  uint16_t type;          // 0 region block, 1 fused repair
-  uint16_t block;         // region: block index
-  uint16_t nin;           // region: input slots (outputs follow)
-  uint16_t stride;        // region: table stride (the plan's R)
-  uint16_t aligned;
-  uint16_t pad[3];
-};
-
 struct BatchArgs {
-  const BatchItem *items;
+  const WorkItem *items;
   int nitems;
+  uint8_t *const *ptrs;  // pointer table of the launch
   unsigned *counter;
   MulConsts k;
 };
@@ -66,7 +53,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
     __syncthreads();
     const int it = s_item;
     if (it >= a.nitems) break;
-    const BatchItem w = a.items[it];
+    const WorkItem w = a.items[it];
+    uint8_t *const *ptrs = a.ptrs + w.ptr_off;
     const bool vec = w.aligned != 0;
     if (w.type == 0) {
       const BlockDesc d = reinterpret_cast<const BlockDesc *>(w.image)[w.block];
@@ -89,11 +77,11 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
         if (off >= w.nbytes) continue;
         uint32_t acc[R][4];
         mac_block<R>(acc, nin, nrows, w.stride, t4, t1, k,
-                     [&](int i) { return load16(w.ptrs[slot[i]], off, w.nbytes, vec); });
+                     [&](int i) { return load16(ptrs[slot[i]], off, w.nbytes, vec); });
 #pragma unroll
         for (int r = 0; r < R; r++)
           if (r < nrows) {
-            uint8_t *o = w.ptrs[slot[nin + r]];
+            uint8_t *o = ptrs[slot[nin + r]];
             if (o) store16(o, off, w.nbytes, vec, acc_bytes(acc[r]));
           }
       }
@@ -119,42 +107,198 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
       const uint64_t span_end = (uint64_t)(w.tile0 + w.ntiles) * kThreads * kVec;
       const uint64_t end = span_end < w.nbytes ? span_end : w.nbytes;
       for (uint64_t t = (uint64_t)w.tile0 * kThreads * kVec; t < end; t += kRepTile)
-        fused_repair_tile<0>(w.ptrs, t, w.nbytes, vec, d, alpha, nz, direct, s_nz, t1a, t1b, t2a,
+        fused_repair_tile<0>(ptrs, t, w.nbytes, vec, d, alpha, nz, direct, s_nz, t1a, t1b, t2a,
                              t2b, rl, proj, k);
     }
     __syncthreads();
   }
 }
 
-struct Stripe {
-  int type = 0;  // 0 region plan, 1 fused repair
-  std::shared_ptr<Plan> plan;
-  std::shared_ptr<FusedRepairPlan> fplan;
-  std::vector<uint8_t *> ptrs;
-  size_t nbytes = 0;
-  int64_t user_bytes = 0;
-  int64_t work = 0;  // products per byte column (cost model)
-  bool aligned = true;
-};
+bool ptr_aligned(const void *p) { return ((uintptr_t)p % 16) == 0; }
 
-
-std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tune;  // signature -> (work_bytes, ctas_per_sm)
-
-const char *kErrBuilt = "batch already built: create a new batch to add stripes";
+void finish_stripe(WorkStripe &s) {
+  for (auto *p : s.ptrs)
+    if (p && !ptr_aligned(p)) s.aligned = false;
+}
 
 }  // namespace
+
+int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                  size_t nbytes, WorkStripe &s, std::string &err) {
+  s = WorkStripe();
+  s.type = 0;
+  s.plan = c->encode;
+  for (int i = 0; i < s.plan->nin; i++) {
+    if (!data[i]) {
+      err = "data block is NULL";
+      return kEInval;
+    }
+    s.ptrs.push_back(const_cast<uint8_t *>(data[i]));
+  }
+  for (int j = 0; j < s.plan->nout; j++) s.ptrs.push_back(out[j]);
+  s.nbytes = nbytes;
+  s.user_bytes = (int64_t)c->m.k * c->m.alpha * nbytes;
+  s.work = s.plan->nnz;
+  finish_stripe(s);
+  return kOk;
+}
+
+int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
+                  uint8_t *const *out, size_t nbytes, WorkStripe &s, std::string &err) {
+  s = WorkStripe();
+  if (c->m.alpha > 16) {
+    err = "batched repair needs alpha <= 16";
+    return kEUnsupported;
+  }
+  s.type = 1;
+  int rc = fused_repair_plan(c, f, helpers, s.fplan, err);
+  if (rc) return rc;
+  const FusedRepairHeader &h = s.fplan->header;
+  for (uint32_t q = 0; q < h.d; q++)
+    for (uint32_t j = 0; j < h.alpha; j++) {
+      const uint8_t *p = blocks[q * h.alpha + j];
+      bool used = false;
+      for (uint32_t i = 0; i < h.nz; i++) used |= h.nzidx[i] == j;
+      if (used && !p) {
+        err = "a helper block the repair reads is NULL";
+        return kEInval;
+      }
+      s.ptrs.push_back(const_cast<uint8_t *>(p));
+    }
+  for (uint32_t r = 0; r < h.alpha; r++) {
+    if (!out[r]) {
+      err = "output block is NULL";
+      return kEInval;
+    }
+    s.ptrs.push_back(out[r]);
+  }
+  s.nbytes = nbytes;
+  s.user_bytes = (int64_t)c->m.alpha * nbytes;
+  s.work = (int64_t)h.d * (h.direct ? 0 : h.nz) + (int64_t)h.d * h.alpha;
+  finish_stripe(s);
+  return kOk;
+}
+
+int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                  uint8_t *const *data_out, size_t nbytes, WorkStripe &s, std::string &err) {
+  s = WorkStripe();
+  {
+    std::vector<char> seen(c->m.n, 0);
+    for (int i = 0; i < c->m.k; i++) {
+      if (nodes[i] < 0 || nodes[i] >= c->m.n || seen[nodes[i]]) {
+        err = "nodes: out of range or repeated node id";
+        return kEInval;
+      }
+      seen[nodes[i]] = 1;
+    }
+  }
+  std::vector<char> want;
+  decode_wanted(c, nodes, node_blocks, data_out, want);
+  s.type = 0;
+  int rc = decode_plan(c, nodes, want, s.plan, err);
+  if (rc) return rc;
+  const int K = c->m.k * c->m.alpha;
+  for (int i = 0; i < K; i++) s.ptrs.push_back(const_cast<uint8_t *>(node_blocks[i]));
+  for (int r = 0; r < K; r++) s.ptrs.push_back(want[r] ? data_out[r] : nullptr);
+  for (const auto &blk : s.plan->blocks)
+    for (uint16_t in : blk.inputs)
+      if (!node_blocks[in]) {
+        err = "a block the decode reads is NULL";
+        return kEInval;
+      }
+  s.nbytes = nbytes;
+  s.user_bytes = (int64_t)K * nbytes;
+  s.work = s.plan->nnz;
+  finish_stripe(s);
+  return kOk;
+}
+
+int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_bytes, WorkList &wl,
+                   std::string &err) {
+  const uint64_t tile = (uint64_t)kThreads * kVec;
+  const uint32_t tiles_per_item = (uint32_t)std::max<uint64_t>(1, (uint64_t)work_bytes / tile);
+  std::vector<const WorkStripe *> order(stripes);
+  std::stable_sort(order.begin(), order.end(), [](const WorkStripe *x, const WorkStripe *y) {
+    return (double)x->work * x->nbytes > (double)y->work * y->nbytes;
+  });
+  for (const WorkStripe *S : order) {
+    if (S->nbytes == 0) continue;
+    const uint32_t base = (uint32_t)wl.ptrs.size();
+    wl.ptrs.insert(wl.ptrs.end(), S->ptrs.begin(), S->ptrs.end());
+    wl.user_bytes += S->user_bytes;
+    const uint32_t ntiles = (uint32_t)((S->nbytes + tile - 1) / tile);
+    const void *image = nullptr;
+    int rc = S->type == 0 ? S->plan->device_image(&image, err) : S->fplan->device_image(&image, err);
+    if (rc) return rc;
+    for (uint32_t t0 = 0; t0 < ntiles; t0 += tiles_per_item) {
+      WorkItem w{};
+      w.image = static_cast<const uint8_t *>(image);
+      w.nbytes = S->nbytes;
+      w.ptr_off = base;
+      w.tile0 = t0;
+      w.ntiles = std::min(tiles_per_item, ntiles - t0);
+      w.aligned = S->aligned ? 1 : 0;
+      if (S->type == 0) {
+        const Plan &P = *S->plan;
+        w.type = 0;
+        w.stride = (uint16_t)P.R;
+        w.idx_base = (uint32_t)P.idx_base;
+        w.tab4_base = (uint32_t)P.tab4_base;
+        w.tab1_base = (uint32_t)P.tab1_base;
+        for (size_t blk = 0; blk < P.blocks.size(); blk++) {
+          w.block = (uint16_t)blk;
+          wl.items.push_back(w);
+        }
+        wl.smem = std::max(wl.smem,
+                           (size_t)P.max_entries * 20 + (size_t)(P.max_inputs + P.R) * 2 + 16);
+      } else {
+        w.type = 1;
+        wl.items.push_back(w);
+        wl.smem = std::max(wl.smem, fused_repair_smem(S->fplan->header) + 64);
+      }
+    }
+  }
+  return kOk;
+}
+
+int worklist_ctas_per_sm(size_t smem) {
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(batch_kernel<kBatchR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  int fit = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<kBatchR>, kThreads, smem);
+  return fit < 1 ? 1 : fit;
+}
+
+cudaError_t worklist_launch(const WorkItem *d_items, int nitems, uint8_t *const *d_ptrs,
+                            unsigned *d_counter, unsigned grid, size_t smem, cudaStream_t stream) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(
+        batch_kernel<kBatchR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  BatchArgs args;
+  args.items = d_items;
+  args.nitems = nitems;
+  args.ptrs = d_ptrs;
+  args.counter = d_counter;
+  args.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  batch_kernel<kBatchR><<<grid, kThreads, smem, stream>>>(args);
+  return cudaGetLastError();
+}
+
 }  // namespace pmrc
 
 using namespace pmrc;
 
 struct pmrc_batch {
-  std::vector<Stripe> stripes;
-  int device = -1;
+  std::vector<WorkStripe> stripes;
   bool built = false;
   // device state
   uint8_t **d_ptrs = nullptr;
-  BatchItem *d_items = nullptr;
+  WorkItem *d_items = nullptr;
   unsigned *d_counter = nullptr;
   int nitems = 0;
   unsigned grid = 0;
@@ -185,19 +329,20 @@ struct pmrc_batch {
 
 namespace {
 
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;  // shape -> (work_bytes, ctas_per_sm)
+
 int bfail(int rc, const std::string &msg) {
   pmrc::set_last_error(msg);
   return rc;
 }
-
-bool ptr_aligned(const void *p) { return ((uintptr_t)p % 16) == 0; }
 
 std::string signature(const pmrc_batch *b) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, dev);
-  // k mix and size buckets of the batch
+  // operation kinds, work per column and size buckets present in the batch
   std::map<std::string, int> cnt;
   for (auto &s : b->stripes) {
     int lg = 0;
@@ -205,118 +350,51 @@ std::string signature(const pmrc_batch *b) {
     cnt[std::to_string(s.type) + "/" + std::to_string(s.work) + "/" + std::to_string(lg / 2)]++;
   }
   std::string sig = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount);
-  for (auto &kv : cnt) sig += "|" + kv.first + ":" + std::to_string(kv.second > 0);
+  for (auto &kv : cnt) sig += "|" + kv.first;
   return sig;
 }
 
 int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &err) {
   b->release_device();
-  cudaError_t e;
-  int dev = 0;
-  e = cudaGetDevice(&dev);
+  int dev = 0, sms = 1;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
     err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
     return kECuda;
   }
-  b->device = dev;
-  int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t tile = (uint64_t)kThreads * kVec;
-  const uint32_t tiles_per_item = (uint32_t)std::max<uint64_t>(1, (uint64_t)work_bytes / tile);
-  // pointer array
-  std::vector<uint8_t *> hp;
-  std::vector<size_t> base(b->stripes.size());
-  for (size_t s = 0; s < b->stripes.size(); s++) {
-    base[s] = hp.size();
-    hp.insert(hp.end(), b->stripes[s].ptrs.begin(), b->stripes[s].ptrs.end());
-  }
-  e = cudaMalloc(&b->d_ptrs, std::max<size_t>(1, hp.size()) * sizeof(uint8_t *));
-  if (e == cudaSuccess && !hp.empty())
-    e = cudaMemcpy(b->d_ptrs, hp.data(), hp.size() * sizeof(uint8_t *), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    err = std::string("batch pointer upload: ") + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? kENoMem : kECuda;
-  }
-  // items: biggest stripes first; the blocks of one tile range adjacent
-  std::vector<size_t> order(b->stripes.size());
-  for (size_t s = 0; s < order.size(); s++) order[s] = s;
-  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
-    const auto &X = b->stripes[x], &Y = b->stripes[y];
-    return (double)X.work * X.nbytes > (double)Y.work * Y.nbytes;
-  });
-  std::vector<BatchItem> items;
-  size_t smem = 64;
-  for (size_t s : order) {
-    const Stripe &S = b->stripes[s];
-    const uint32_t ntiles = (uint32_t)((S.nbytes + tile - 1) / tile);
-    const void *image = nullptr;
-    int rc = S.type == 0 ? S.plan->device_image(&image, err) : S.fplan->device_image(&image, err);
-    if (rc) return rc;
-    for (uint32_t t0 = 0; t0 < ntiles; t0 += tiles_per_item) {
-      BatchItem w{};
-      w.image = static_cast<const uint8_t *>(image);
-      w.ptrs = b->d_ptrs + base[s];
-      w.nbytes = S.nbytes;
-      w.tile0 = t0;
-      w.ntiles = std::min(tiles_per_item, ntiles - t0);
-      w.aligned = S.aligned ? 1 : 0;
-      if (S.type == 0) {
-        const Plan &P = *S.plan;
-        w.type = 0;
-        w.nin = (uint16_t)P.nin;
-        w.stride = (uint16_t)P.R;
-        w.idx_base = (uint32_t)P.idx_base;
-        w.tab4_base = (uint32_t)P.tab4_base;
-        w.tab1_base = (uint32_t)P.tab1_base;
-        for (size_t blk = 0; blk < P.blocks.size(); blk++) {
-          w.block = (uint16_t)blk;
-          items.push_back(w);
-        }
-        smem = std::max(smem, (size_t)P.max_entries * 20 + (size_t)(P.max_inputs + P.R) * 2 + 16);
-      } else {
-        const FusedRepairHeader &h = S.fplan->header;
-        w.type = 1;
-        items.push_back(w);
-        smem = std::max(smem, fused_repair_smem(h) + 64);
-      }
-    }
-  }
-  b->nitems = (int)items.size();
-  e = cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem));
-  if (e == cudaSuccess && !items.empty())
-    e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem),
+  std::vector<const WorkStripe *> sp;
+  for (auto &s : b->stripes) sp.push_back(&s);
+  WorkList wl;
+  int rc = worklist_build(sp, work_bytes, wl, err);
+  if (rc) return rc;
+  e = cudaMalloc(&b->d_ptrs, std::max<size_t>(1, wl.ptrs.size()) * sizeof(uint8_t *));
+  if (e == cudaSuccess && !wl.ptrs.empty())
+    e = cudaMemcpy(b->d_ptrs, wl.ptrs.data(), wl.ptrs.size() * sizeof(uint8_t *),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&b->d_items, std::max<size_t>(1, wl.items.size()) * sizeof(WorkItem));
+  if (e == cudaSuccess && !wl.items.empty())
+    e = cudaMemcpy(b->d_items, wl.items.data(), wl.items.size() * sizeof(WorkItem),
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned));
   if (e != cudaSuccess) {
     err = std::string("batch work list upload: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? kENoMem : kECuda;
   }
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(batch_kernel<kBatchR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) {
-      err = std::string("batch smem opt-in: ") + cudaGetErrorString(e);
-      return kECuda;
-    }
-  }
-  int fit = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<kBatchR>, kThreads, smem);
-  if (fit < 1) fit = 1;
-  const int per_sm = std::max(1, std::min(ctas_per_sm, fit));
-  b->grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, std::max(1, b->nitems)));
-  b->smem = smem;
+  b->nitems = (int)wl.items.size();
+  b->smem = wl.smem;
+  const int per_sm = std::max(1, std::min(ctas_per_sm, worklist_ctas_per_sm(wl.smem)));
+  b->grid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms * per_sm, std::max(1, b->nitems)));
   // graph: counter reset + persistent kernel
-  BatchArgs args;
-  args.items = b->d_items;
-  args.nitems = b->nitems;
-  args.counter = b->d_counter;
-  args.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), b->cap);
-    batch_kernel<kBatchR><<<b->grid, kThreads, smem, b->cap>>>(args);
+    cudaError_t le = worklist_launch(b->d_items, b->nitems, b->d_ptrs, b->d_counter, b->grid,
+                                     b->smem, b->cap);
     e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (le != cudaSuccess) e = le;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) {
@@ -329,14 +407,14 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   return kOk;
 }
 
-int add_stripe(pmrc_batch *b, Stripe &&s) {
-  if (b->built) return bfail(PMRC_EBUSY, kErrBuilt);
-  for (auto *p : s.ptrs)
-    if (p && !ptr_aligned(p)) s.aligned = false;
+int add(pmrc_batch *b, int rc, WorkStripe &&s, const std::string &err) {
+  if (rc) return bfail(rc, err);
   b->user_bytes += s.user_bytes;
   b->stripes.push_back(std::move(s));
   return (int)b->stripes.size() - 1;
 }
+
+const char *kErrBuilt = "batch already built: create a new batch to add stripes";
 
 }  // namespace
 
@@ -353,77 +431,32 @@ void pmrc_batch_destroy(pmrc_batch *b) { delete b; }
 int pmrc_batch_add_encode(pmrc_batch *b, const pmrc_code *c, const uint8_t *const *data,
                           uint8_t *const *out, size_t nbytes) {
   if (!b || !c || !data || !out) return bfail(PMRC_EINVAL, "NULL argument");
-  Stripe s;
-  s.type = 0;
-  s.plan = c->encode;
-  for (int i = 0; i < s.plan->nin; i++) {
-    if (!data[i]) return bfail(PMRC_EINVAL, "data block is NULL");
-    s.ptrs.push_back(const_cast<uint8_t *>(data[i]));
-  }
-  for (int j = 0; j < s.plan->nout; j++) s.ptrs.push_back(out[j]);
-  s.nbytes = nbytes;
-  s.user_bytes = (int64_t)c->m.k * c->m.alpha * nbytes;
-  s.work = s.plan->nnz;
-  return add_stripe(b, std::move(s));
+  if (b->built) return bfail(PMRC_EBUSY, kErrBuilt);
+  WorkStripe s;
+  std::string err;
+  int rc = stripe_encode(c, data, out, nbytes, s, err);
+  return add(b, rc, std::move(s), err);
 }
 
 int pmrc_batch_add_repair(pmrc_batch *b, const pmrc_code *c, int f, const int *helpers,
                           const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes) {
   if (!b || !c || !helpers || !blocks || !out) return bfail(PMRC_EINVAL, "NULL argument");
-  if (c->m.alpha > 16) return bfail(PMRC_EUNSUPPORTED, "batched repair needs alpha <= 16");
-  Stripe s;
-  s.type = 1;
+  if (b->built) return bfail(PMRC_EBUSY, kErrBuilt);
+  WorkStripe s;
   std::string err;
-  int rc = fused_repair_plan(c, f, helpers, s.fplan, err);
-  if (rc) return bfail(rc, err);
-  const FusedRepairHeader &h = s.fplan->header;
-  for (uint32_t q = 0; q < h.d; q++)
-    for (uint32_t j = 0; j < h.alpha; j++) {
-      const uint8_t *p = blocks[q * h.alpha + j];
-      bool used = false;
-      for (uint32_t i = 0; i < h.nz; i++) used |= h.nzidx[i] == j;
-      if (used && !p) return bfail(PMRC_EINVAL, "a helper block the repair reads is NULL");
-      s.ptrs.push_back(const_cast<uint8_t *>(p));
-    }
-  for (uint32_t r = 0; r < h.alpha; r++) {
-    if (!out[r]) return bfail(PMRC_EINVAL, "output block is NULL");
-    s.ptrs.push_back(out[r]);
-  }
-  s.nbytes = nbytes;
-  s.user_bytes = (int64_t)c->m.alpha * nbytes;
-  s.work = (int64_t)h.d * (h.direct ? 0 : h.nz) + (int64_t)h.d * h.alpha;
-  return add_stripe(b, std::move(s));
+  int rc = stripe_repair(c, f, helpers, blocks, out, nbytes, s, err);
+  return add(b, rc, std::move(s), err);
 }
 
 int pmrc_batch_add_decode(pmrc_batch *b, const pmrc_code *c, const int *nodes,
                           const uint8_t *const *node_blocks, uint8_t *const *data_out,
                           size_t nbytes) {
   if (!b || !c || !nodes || !node_blocks || !data_out) return bfail(PMRC_EINVAL, "NULL argument");
-  {
-    std::vector<char> seen(c->m.n, 0);
-    for (int i = 0; i < c->m.k; i++) {
-      if (nodes[i] < 0 || nodes[i] >= c->m.n || seen[nodes[i]])
-        return bfail(PMRC_EINVAL, "nodes: out of range or repeated node id");
-      seen[nodes[i]] = 1;
-    }
-  }
-  std::vector<char> want;
-  decode_wanted(c, nodes, node_blocks, data_out, want);
-  Stripe s;
-  s.type = 0;
+  if (b->built) return bfail(PMRC_EBUSY, kErrBuilt);
+  WorkStripe s;
   std::string err;
-  int rc = decode_plan(c, nodes, want, s.plan, err);
-  if (rc) return bfail(rc, err);
-  const int K = c->m.k * c->m.alpha;
-  for (int i = 0; i < K; i++) s.ptrs.push_back(const_cast<uint8_t *>(node_blocks[i]));
-  for (int r = 0; r < K; r++) s.ptrs.push_back(want[r] ? data_out[r] : nullptr);
-  for (const auto &blk : s.plan->blocks)
-    for (uint16_t in : blk.inputs)
-      if (!node_blocks[in]) return bfail(PMRC_EINVAL, "a block the decode reads is NULL");
-  s.nbytes = nbytes;
-  s.user_bytes = (int64_t)K * nbytes;
-  s.work = s.plan->nnz;
-  return add_stripe(b, std::move(s));
+  int rc = stripe_decode(c, nodes, node_blocks, data_out, nbytes, s, err);
+  return add(b, rc, std::move(s), err);
 }
 
 int pmrc_batch_build(pmrc_batch *b, int work_bytes, int ctas_per_sm) {

@@ -1,0 +1,70 @@
+// Work lists of the persistent kernel in batch.cu, shared by the batched
+// API (pmrc_batch_*) and the serving loop (serve.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "repair.h"
+
+struct pmrc_code;
+
+namespace pmrc {
+
+// One stripe operation, ready to be cut into work items.
+struct WorkStripe {
+  int type = 0;  // 0: region plan (encode, decode), 1: fused repair
+  std::shared_ptr<Plan> plan;
+  std::shared_ptr<FusedRepairPlan> fplan;
+  std::vector<uint8_t *> ptrs;  // inputs, then outputs (device pointers)
+  size_t nbytes = 0;
+  int64_t user_bytes = 0;       // k*alpha*B (encode, decode) or alpha*B (repair)
+  int64_t work = 0;             // products per byte column (cost model)
+  bool aligned = true;
+};
+
+int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                  size_t nbytes, WorkStripe &s, std::string &err);
+int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
+                  uint8_t *const *out, size_t nbytes, WorkStripe &s, std::string &err);
+int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                  uint8_t *const *data_out, size_t nbytes, WorkStripe &s, std::string &err);
+
+// Device work item (16-byte aligned, position independent: pointers are
+// offsets into the launch's pointer table).
+struct WorkItem {
+  const uint8_t *image;    // region plan image or fused repair image (device)
+  uint64_t nbytes;         // block size of the stripe
+  uint32_t ptr_off;        // first pointer of the stripe in the table
+  uint32_t tile0, ntiles;  // 4 KiB tile range
+  uint32_t idx_base, tab4_base, tab1_base;  // region image offsets
+  uint16_t type;           // 0 region block, 1 fused repair
+  uint16_t block;          // region: block index
+  uint16_t stride;         // region: table stride (the plan's R)
+  uint16_t aligned;
+};
+
+struct WorkList {
+  std::vector<uint8_t *> ptrs;
+  std::vector<WorkItem> items;
+  size_t smem = 64;        // dynamic shared memory per CTA
+  int64_t user_bytes = 0;
+};
+
+// Appends the stripes' items (biggest stripes first, blocks of one tile
+// range adjacent) and pointers; plan images are uploaded on first use.
+int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_bytes, WorkList &wl,
+                   std::string &err);
+
+// Persistent CTAs per SM that fit the kernel with this shared memory.
+int worklist_ctas_per_sm(size_t smem);
+
+// Counter reset + persistent kernel over nitems items already on the device.
+cudaError_t worklist_launch(const WorkItem *d_items, int nitems, uint8_t *const *d_ptrs,
+                            unsigned *d_counter, unsigned grid, size_t smem, cudaStream_t stream);
+
+}  // namespace pmrc

@@ -1,0 +1,580 @@
+// Serving loop: continuous batching of encode, repair and reconstruction
+// requests on one GPU.
+//
+// A scheduler thread owns three streams (host-to-device copies, compute,
+// device-to-host copies) and a device arena whose size is the HBM budget.
+// Each pass of its loop:
+//   1. admits queued requests in arrival order while a slot is free and the
+//      arena has room for the request's inputs and outputs (first fit);
+//      their input copies start at once on the copy stream;
+//   2. marks requests whose inputs have landed as ready;
+//   3. when fewer than two iterations are in flight, launches one iteration:
+//      the work items of every ready request (batch.cu's persistent kernel)
+//      in one launch, followed on the copy-back stream by the output copies
+//      of those requests;
+//   4. retires requests whose outputs are back: frees their arena range and
+//      records submit-to-completion latency.
+// Requests that arrive while an iteration runs are admitted and copied in
+// meanwhile and join the next iteration, so transfers overlap compute and
+// the work of many requests overlaps in one launch.  Coefficient plans stay
+// on the device in the code handles.  All waits on the device are event
+// queries polled by the host: no device-side wait exists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/pmrc.h"
+#include "api_internal.h"
+#include "batch_internal.h"
+
+using namespace pmrc;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t kAlign = 256;
+
+// First-fit allocator over [0, size) with coalescing free list.
+class Arena {
+ public:
+  explicit Arena(size_t size) : size_(size) { free_[0] = size; }
+  bool alloc(size_t n, size_t &off) {
+    n = (n + kAlign - 1) & ~(kAlign - 1);
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= n) {
+        off = it->first;
+        const size_t rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        used_ += n;
+        peak_ = std::max(peak_, used_);
+        return true;
+      }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = (n + kAlign - 1) & ~(kAlign - 1);
+    used_ -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t size() const { return size_; }
+  size_t peak() const { return peak_; }
+  size_t used() const { return used_; }
+
+ private:
+  size_t size_, used_ = 0, peak_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+enum State { kQueued, kCopyIn, kReady, kRunning, kDone, kFailed, kCancelled };
+
+struct Req {
+  uint64_t id = 0;
+  int op = 0;
+  const pmrc_code *code = nullptr;
+  size_t B = 0;
+  const uint8_t *in = nullptr;
+  uint8_t *out = nullptr;
+  int failed = -1;
+  std::vector<int> helpers, nodes;
+  size_t in_bytes = 0, out_bytes = 0, nin = 0, nout = 0;
+  size_t in_span = 0;  // in_bytes rounded up: outputs start 256-byte aligned
+  size_t off = 0;
+  int64_t user_bytes = 0;
+  State state = kQueued;
+  int status = PMRC_OK;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  Clock::time_point t_submit, t_done;
+};
+
+struct Iteration {
+  cudaEvent_t done = nullptr;  // kernel finished
+  std::vector<Req *> reqs;
+  std::vector<WorkStripe> stripes;  // keeps the plans the kernel reads alive
+  int buf = 0;
+};
+
+}  // namespace
+
+struct pmrc_server {
+  int device = 0;
+  int max_slots = 0;
+  uint8_t *arena_base = nullptr;
+  std::unique_ptr<Arena> arena;
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  // double-buffered work lists (device + pinned staging)
+  WorkItem *d_items[2] = {nullptr, nullptr};
+  uint8_t **d_ptrs[2] = {nullptr, nullptr};
+  unsigned *d_counter[2] = {nullptr, nullptr};
+  WorkItem *h_items[2] = {nullptr, nullptr};
+  uint8_t **h_ptrs[2] = {nullptr, nullptr};
+  cudaEvent_t buf_free[2] = {nullptr, nullptr};
+  size_t item_cap = 0, ptr_cap = 0;
+  int sms = 1;
+
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req *> queue;
+  std::vector<Req *> active;
+  std::map<uint64_t, std::unique_ptr<Req>> reqs;
+  std::deque<Iteration> inflight;
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::thread worker;
+  int next_buf = 0;
+
+  // statistics
+  std::vector<double> lat_ms;
+  int64_t done_bytes = 0, done_count = 0, failed_count = 0, iterations = 0;
+  Clock::time_point t_first, t_last;
+  bool any_done = false;
+
+  void run();
+  bool launch_iteration(std::vector<Req *> &ready, std::string &err);
+};
+
+namespace {
+
+int sfail(int rc, const std::string &msg) {
+  set_last_error(msg);
+  return rc;
+}
+
+// Drops the record of a finished request once its result was collected.
+void forget(pmrc_server *s, std::map<uint64_t, std::unique_ptr<Req>>::iterator it) {
+  cudaEventDestroy(it->second->ev_in);
+  cudaEventDestroy(it->second->ev_out);
+  s->reqs.erase(it);
+}
+
+// Device pointers of a request's blocks inside the arena.
+void block_ptrs(pmrc_server *s, Req *r, std::vector<const uint8_t *> &in,
+                std::vector<uint8_t *> &out) {
+  uint8_t *base = s->arena_base + r->off;
+  in.resize(r->nin);
+  out.resize(r->nout);
+  for (size_t i = 0; i < r->nin; i++) in[i] = base + i * r->B;
+  for (size_t j = 0; j < r->nout; j++) out[j] = base + r->in_span + j * r->B;
+}
+
+}  // namespace
+
+bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) {
+  // the staging buffer must be free of its previous upload
+  const int b = next_buf;
+  if (cudaEventQuery(buf_free[b]) == cudaErrorNotReady) return false;
+  std::vector<WorkStripe> stripes(ready.size());
+  std::vector<const WorkStripe *> sp;
+  std::vector<Req *> ok;
+  for (size_t i = 0; i < ready.size(); i++) {
+    Req *r = ready[i];
+    std::vector<const uint8_t *> in;
+    std::vector<uint8_t *> out;
+    block_ptrs(this, r, in, out);
+    std::string e2;
+    int rc;
+    if (r->op == PMRC_OP_ENCODE)
+      rc = stripe_encode(r->code, in.data(), out.data(), r->B, stripes[i], e2);
+    else if (r->op == PMRC_OP_REPAIR)
+      rc = stripe_repair(r->code, r->failed, r->helpers.data(), in.data(), out.data(), r->B,
+                         stripes[i], e2);
+    else
+      rc = stripe_decode(r->code, r->nodes.data(), in.data(), out.data(), r->B, stripes[i], e2);
+    if (rc) {
+      r->status = rc;
+      r->state = kFailed;
+      continue;
+    }
+    sp.push_back(&stripes[i]);
+    ok.push_back(r);
+  }
+  WorkList wl;
+  if (!sp.empty()) {
+    int rc = worklist_build(sp, 64 << 10, wl, err);
+    if (rc) {
+      for (Req *r : ok) {
+        r->status = rc;
+        r->state = kFailed;
+      }
+      ok.clear();
+    }
+  }
+  if (wl.items.size() > item_cap || wl.ptrs.size() > ptr_cap) {
+    err = "iteration larger than the server's work-list capacity";
+    for (Req *r : ok) {
+      r->status = PMRC_EUNSUPPORTED;
+      r->state = kFailed;
+    }
+    ok.clear();
+  }
+  Iteration it;
+  it.buf = b;
+  cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
+  if (!ok.empty() && !wl.items.empty()) {
+    memcpy(h_items[b], wl.items.data(), wl.items.size() * sizeof(WorkItem));
+    memcpy(h_ptrs[b], wl.ptrs.data(), wl.ptrs.size() * sizeof(uint8_t *));
+    cudaMemcpyAsync(d_items[b], h_items[b], wl.items.size() * sizeof(WorkItem),
+                    cudaMemcpyHostToDevice, s_comp);
+    cudaMemcpyAsync(d_ptrs[b], h_ptrs[b], wl.ptrs.size() * sizeof(uint8_t *),
+                    cudaMemcpyHostToDevice, s_comp);
+    cudaEventRecord(buf_free[b], s_comp);
+    const int per_sm = std::min(2, worklist_ctas_per_sm(wl.smem));
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)wl.items.size()));
+    cudaError_t e = worklist_launch(d_items[b], (int)wl.items.size(), d_ptrs[b], d_counter[b],
+                                    grid, wl.smem, s_comp);
+    if (e != cudaSuccess) {
+      err = std::string("serving launch: ") + cudaGetErrorString(e);
+      for (Req *r : ok) {
+        r->status = PMRC_ECUDA;
+        r->state = kFailed;
+      }
+      ok.clear();
+    }
+  }
+  cudaEventRecord(it.done, s_comp);
+  // outputs go back as soon as the iteration's kernel is done
+  cudaStreamWaitEvent(s_out, it.done, 0);
+  for (Req *r : ok) {
+    cudaMemcpyAsync(r->out, arena_base + r->off + r->in_span, r->out_bytes,
+                    cudaMemcpyDeviceToHost, s_out);
+    cudaEventRecord(r->ev_out, s_out);
+    r->state = kRunning;
+  }
+  it.reqs = ok;
+  it.stripes = std::move(stripes);
+  inflight.push_back(std::move(it));
+  next_buf ^= 1;
+  iterations++;
+  return true;
+}
+
+void pmrc_server::run() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    bool progress = false;
+    // 1. admit
+    while (!queue.empty() && (int)active.size() < max_slots) {
+      Req *r = queue.front();
+      size_t off;
+      if (!arena->alloc(r->in_span + r->out_bytes, off)) break;
+      queue.pop_front();
+      r->off = off;
+      cudaMemcpyAsync(arena_base + off, r->in, r->in_bytes, cudaMemcpyHostToDevice, s_in);
+      cudaEventRecord(r->ev_in, s_in);
+      r->state = kCopyIn;
+      active.push_back(r);
+      progress = true;
+    }
+    // 2. inputs landed
+    std::vector<Req *> ready;
+    for (Req *r : active) {
+      if (r->state == kCopyIn && cudaEventQuery(r->ev_in) == cudaSuccess) r->state = kReady;
+      if (r->state == kReady) ready.push_back(r);
+    }
+    // 3. launch an iteration over every ready request
+    if (!ready.empty() && inflight.size() < 2) {
+      std::string err;
+      if (launch_iteration(ready, err)) progress = true;
+      if (!err.empty()) set_last_error(err);
+    }
+    // 4. retire requests whose outputs are back
+    while (!inflight.empty() && cudaEventQuery(inflight.front().done) == cudaSuccess) {
+      cudaEventDestroy(inflight.front().done);
+      inflight.pop_front();
+      progress = true;
+    }
+    for (size_t i = 0; i < active.size();) {
+      Req *r = active[i];
+      bool fin = false;
+      if (r->state == kRunning && cudaEventQuery(r->ev_out) == cudaSuccess) {
+        r->state = kDone;
+        fin = true;
+      } else if (r->state == kFailed) {
+        fin = true;
+      }
+      if (fin) {
+        bool in_flight_iter = false;  // a failed request may still be in an iteration
+        for (auto &it : inflight)
+          for (Req *q : it.reqs) in_flight_iter |= (q == r);
+        if (in_flight_iter) {
+          i++;
+          continue;
+        }
+        arena->release(r->off, r->in_span + r->out_bytes);
+        r->t_done = Clock::now();
+        if (r->state == kDone) {
+          lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit)
+                               .count());
+          done_bytes += r->user_bytes;
+          done_count++;
+          if (!any_done) t_first = r->t_submit;
+          any_done = true;
+          t_last = r->t_done;
+        } else {
+          failed_count++;
+        }
+        active.erase(active.begin() + i);
+        progress = true;
+        cv_done.notify_all();
+      } else {
+        i++;
+      }
+    }
+    if (stop && queue.empty() && active.empty() && inflight.empty()) break;
+    if (!progress) {
+      if (queue.empty() && active.empty() && inflight.empty())
+        cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+      else
+        cv_work.wait_for(lk, std::chrono::microseconds(20));
+    }
+  }
+}
+
+extern "C" {
+
+int pmrc_server_create(size_t budget_bytes, int max_slots, pmrc_server **out) {
+  if (!out || budget_bytes < kAlign || max_slots < 1)
+    return sfail(PMRC_EINVAL, "server needs out, a budget and at least one slot");
+  *out = nullptr;
+  std::unique_ptr<pmrc_server> s(new (std::nothrow) pmrc_server());
+  if (!s) return sfail(PMRC_ENOMEM, "out of host memory");
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->arena_base, budget_bytes);
+  if (e != cudaSuccess)
+    return sfail(e == cudaErrorMemoryAllocation ? PMRC_ENOMEM : PMRC_ECUDA,
+                 std::string("server arena: ") + cudaGetErrorString(e));
+  s->arena.reset(new Arena(budget_bytes));
+  s->max_slots = max_slots;
+  // generous work-list capacity: items are 4 KiB x 16 tiles per block
+  s->item_cap = 1 << 20;
+  s->ptr_cap = 1 << 20;
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+    e = cudaMalloc(&s->d_items[b], s->item_cap * sizeof(WorkItem));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ptrs[b], s->ptr_cap * sizeof(uint8_t *));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter[b], sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_items[b], s->item_cap * sizeof(WorkItem));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_ptrs[b], s->ptr_cap * sizeof(uint8_t *));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->buf_free[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    pmrc_server_destroy(s.release());
+    return sfail(PMRC_ECUDA, std::string("server setup: ") + cudaGetErrorString(e));
+  }
+  pmrc_server *raw = s.get();
+  raw->worker = std::thread([raw] { raw->run(); });
+  *out = s.release();
+  return PMRC_OK;
+}
+
+void pmrc_server_destroy(pmrc_server *s) {
+  if (!s) return;
+  if (s->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->worker.join();
+  }
+  for (auto &kv : s->reqs) {
+    if (kv.second->ev_in) cudaEventDestroy(kv.second->ev_in);
+    if (kv.second->ev_out) cudaEventDestroy(kv.second->ev_out);
+  }
+  for (int b = 0; b < 2; b++) {
+    cudaFree(s->d_items[b]);
+    cudaFree(s->d_ptrs[b]);
+    cudaFree(s->d_counter[b]);
+    cudaFreeHost(s->h_items[b]);
+    cudaFreeHost(s->h_ptrs[b]);
+    if (s->buf_free[b]) cudaEventDestroy(s->buf_free[b]);
+  }
+  if (s->s_in) cudaStreamDestroy(s->s_in);
+  if (s->s_comp) cudaStreamDestroy(s->s_comp);
+  if (s->s_out) cudaStreamDestroy(s->s_out);
+  cudaFree(s->arena_base);
+  delete s;
+}
+
+int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) {
+  if (!s || !q || !q->code || !q->in || !q->out || q->block_bytes == 0)
+    return sfail(PMRC_EINVAL, "NULL argument or empty block");
+  const pmrc_code *c = q->code;
+  std::unique_ptr<Req> r(new (std::nothrow) Req());
+  if (!r) return sfail(PMRC_ENOMEM, "out of host memory");
+  r->op = q->op;
+  r->code = c;
+  r->B = q->block_bytes;
+  r->in = q->in;
+  r->out = q->out;
+  const size_t a = c->m.alpha, K = c->m.k * a, N = c->m.n * a;
+  switch (q->op) {
+    case PMRC_OP_ENCODE:
+      r->nin = K;
+      r->nout = c->m.systematic ? N - K : N;
+      r->user_bytes = (int64_t)K * r->B;
+      break;
+    case PMRC_OP_REPAIR: {
+      if (!q->helpers) return sfail(PMRC_EINVAL, "repair needs helpers");
+      r->failed = q->failed;
+      r->helpers.assign(q->helpers, q->helpers + c->m.d);
+      Mat D;
+      std::string err;
+      int rc = newcomer_matrix(c->m, q->failed, q->helpers, D, err);
+      if (rc) return sfail(rc, err);
+      if (a > 16) return sfail(PMRC_EUNSUPPORTED, "served repair needs alpha <= 16");
+      r->nin = (size_t)c->m.d * a;
+      r->nout = a;
+      r->user_bytes = (int64_t)a * r->B;
+      break;
+    }
+    case PMRC_OP_DECODE: {
+      if (!q->nodes) return sfail(PMRC_EINVAL, "decode needs nodes");
+      r->nodes.assign(q->nodes, q->nodes + c->m.k);
+      Mat R;
+      std::string err;
+      int rc = decode_matrix(c->m, q->nodes, R, err);
+      if (rc) return sfail(rc, err);
+      r->nin = K;
+      r->nout = K;
+      r->user_bytes = (int64_t)K * r->B;
+      break;
+    }
+    default:
+      return sfail(PMRC_EINVAL, "unknown operation");
+  }
+  r->in_bytes = r->nin * r->B;
+  r->out_bytes = r->nout * r->B;
+  r->in_span = (r->in_bytes + kAlign - 1) & ~(kAlign - 1);
+  if (r->in_span + r->out_bytes > s->arena->size())
+    return sfail(PMRC_ENOMEM, "request larger than the server's HBM budget");
+  if (cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return sfail(PMRC_ECUDA, "cudaEventCreate");
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->stop) return sfail(PMRC_EBUSY, "server is stopping");
+    r->id = s->next_id++;
+    if (id_out) *id_out = r->id;
+    s->queue.push_back(r.get());
+    s->reqs[r->id] = std::move(r);
+  }
+  s->cv_work.notify_one();
+  return PMRC_OK;
+}
+
+int pmrc_server_poll(pmrc_server *s, uint64_t id, int *status, double *latency_ms) {
+  if (!s) return sfail(PMRC_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(PMRC_EINVAL, "unknown request id");
+  Req *r = it->second.get();
+  const bool fin = r->state == kDone || r->state == kFailed || r->state == kCancelled;
+  if (status) *status = r->state == kDone ? PMRC_OK : r->status;
+  if (latency_ms)
+    *latency_ms = fin ? std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count()
+                      : -1.0;
+  if (fin) forget(s, it);
+  return fin ? 1 : 0;
+}
+
+int pmrc_server_wait(pmrc_server *s, uint64_t id, int timeout_ms, int *status,
+                     double *latency_ms) {
+  if (!s) return sfail(PMRC_EINVAL, "NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(PMRC_EINVAL, "unknown request id");
+  Req *r = it->second.get();
+  auto fin = [&] { return r->state == kDone || r->state == kFailed || r->state == kCancelled; };
+  if (timeout_ms < 0)
+    s->cv_done.wait(lk, fin);
+  else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), fin))
+    return sfail(PMRC_ETIMEOUT, "request not finished within the timeout");
+  if (status) *status = r->state == kDone ? PMRC_OK : r->status;
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  forget(s, it);
+  return PMRC_OK;
+}
+
+int pmrc_server_cancel(pmrc_server *s, uint64_t id) {
+  if (!s) return sfail(PMRC_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(PMRC_EINVAL, "unknown request id");
+  Req *r = it->second.get();
+  if (r->state != kQueued) return sfail(PMRC_EBUSY, "request already admitted");
+  s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+  r->state = kCancelled;
+  r->status = PMRC_EBUSY;
+  r->t_done = Clock::now();
+  s->cv_done.notify_all();
+  return PMRC_OK;
+}
+
+int pmrc_server_stats(pmrc_server *s, double *out) {
+  if (!s || !out) return sfail(PMRC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  std::vector<double> v = s->lat_ms;
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double p) {
+    if (v.empty()) return 0.0;
+    size_t i = (size_t)std::min<double>(v.size() - 1, std::max(0.0, p * v.size() - 1e-9));
+    return v[i];
+  };
+  const double span =
+      s->any_done ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
+  out[0] = (double)s->done_count;
+  out[1] = (double)s->failed_count;
+  out[2] = pct(0.50);
+  out[3] = pct(0.99);
+  out[4] = v.empty() ? 0.0 : v.back();
+  out[5] = (double)s->done_bytes;
+  out[6] = span > 0 ? s->done_bytes / span / 1e9 : 0.0;
+  out[7] = (double)s->arena->peak();
+  out[8] = (double)s->iterations;
+  out[9] = (double)s->arena->size();
+  return PMRC_OK;
+}
+
+int pmrc_server_reset_stats(pmrc_server *s) {
+  if (!s) return sfail(PMRC_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  s->lat_ms.clear();
+  s->done_bytes = s->done_count = s->failed_count = s->iterations = 0;
+  s->any_done = false;
+  return PMRC_OK;
+}
+
+}  // extern "C"
