@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch-stripes", type=int, default=4096)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=400,
+                   help="requests per offered-load level")
     return p.parse_args()
 
 
@@ -286,6 +289,7 @@ def run_ours(args, rank, world, local_rank):
                                                 / hbm, 4)}
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
+    serving = None if args.no_serving else run_serving(torch, P, inputs, args)
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
@@ -307,6 +311,8 @@ def run_ours(args, rank, world, local_rank):
         result["e2e"] = e2e
     if batched:
         result["batched"] = batched
+    if serving:
+        result["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args, W, torch)
     if dist:
@@ -435,6 +441,95 @@ def run_batched(torch, P, inputs, args, dev, stream):
     if scale_note:
         out["note"] = scale_note
     del arena
+    del np
+    return out
+
+
+def run_serving(torch, P, inputs, args):
+    """Serving workload: Poisson arrivals of encode / repair / reconstruct
+    requests (60/25/15), k uniform on {4, 8, 12, 16} (n = 2k, sparse
+    systematic), stripes log-uniform on [64 KiB, 64 MiB] split into k*alpha
+    blocks (the last one zero-padded), host buffers pinned.  First the
+    saturated rate (all requests submitted at once), then offered loads of
+    25/50/75/90% of it; latency is submit to completion seen by the host."""
+    import numpy as np
+    reqs_all = inputs.serve_requests(args.serve_requests * 5, seed=args.seed + 6)
+    codes = {k: P.Code(2 * k, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC) for k in (4, 8, 12, 16)}
+
+    def sizes(q):
+        k = q["k"]
+        a, d = k - 1, 2 * k - 2
+        B = q["block_bytes"]
+        if q["op"] == "encode":
+            return k * a * B, k * a * B, k * a * B
+        if q["op"] == "repair":
+            return d * a * B, a * B, a * B
+        return k * a * B, k * a * B, k * a * B
+
+    max_in = max(sizes(q)[0] for q in reqs_all)
+    max_out = max(sizes(q)[1] for q in reqs_all)
+    g = torch.Generator()
+    g.manual_seed(args.seed + 7)
+    hin = torch.randint(0, 256, (max_in,), dtype=torch.uint8, generator=g).pin_memory()
+    hout = torch.empty(max_out, dtype=torch.uint8).pin_memory()
+    helpers = {}
+    for k, c in codes.items():
+        for f in range(2 * k):
+            helpers[(k, f)] = c.default_helpers(f)
+    srv = P.Server(budget_bytes=16 << 30, max_slots=64)
+    opcode = {"encode": P.PMRC_OP_ENCODE, "repair": P.PMRC_OP_REPAIR,
+              "decode": P.PMRC_OP_DECODE}
+
+    def submit(q):
+        k = q["k"]
+        return srv.submit(opcode[q["op"]], codes[k], q["block_bytes"], hin, hout,
+                          failed=q["failed"], helpers=helpers[(k, q["failed"])],
+                          nodes=q["nodes"])
+
+    def run(batch, rate):
+        srv.reset_stats()
+        ids = []
+        t0 = time.perf_counter()
+        tq = 0.0
+        rng = np.random.default_rng(args.seed + 8)
+        for q in batch:
+            if rate:
+                tq += rng.exponential(1.0 / rate)
+                dt = t0 + tq - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            ids.append(submit(q))
+        lost = 0
+        for rid in ids:
+            try:
+                srv.wait(rid, timeout_ms=60000)
+            except P.PMRCError:
+                lost += 1
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        if lost or st["failed"]:
+            raise RuntimeError(f"serving: {lost} requests timed out, {int(st['failed'])} failed")
+        user = sum(sizes(q)[2] for q in batch)
+        return {"requests": len(batch), "p50_ms": round(st["p50_ms"], 3),
+                "p99_ms": round(st["p99_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                "GBps": round(user / wall / 1e9, 2), "iterations": int(st["iterations"]),
+                "peak_GB": round(st["peak_bytes"] / 1e9, 2)}
+
+    n = args.serve_requests
+    run(reqs_all[:min(32, n)], 0)  # warm-up: plans, pools
+    sat = run(reqs_all[:n], 0)
+    mean_user = sum(sizes(q)[2] for q in reqs_all[:n]) / n
+    out = {"workload": "Poisson arrivals; encode/repair/reconstruct 60/25/15; k in {4,8,12,16} "
+                       "(n=2k, sparse systematic); stripes log-uniform 64 KiB-64 MiB; pinned "
+                       "host buffers; HBM budget 16 GiB, 64 slots",
+           "saturated": sat, "loads": {}}
+    for i, load in enumerate((0.25, 0.5, 0.75, 0.9)):
+        rate = load * sat["GBps"] * 1e9 / mean_user
+        batch = reqs_all[(i + 1) * n:(i + 2) * n]
+        r = run(batch, rate)
+        r["offered_GBps"] = round(load * sat["GBps"], 2)
+        out["loads"][f"{int(load * 100)}%"] = r
+    srv.close()
     del np
     return out
 

@@ -198,15 +198,54 @@ int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::strin
   int rc = check_distinct(nodes, c.k, c.n, -1, err, "nodes");
   if (rc) return rc;
   const int a = c.alpha, K = c.k * a;
-  Mat GR(K, K);
+  if (!c.systematic) {
+    Mat GR(K, K);
+    for (int i = 0; i < c.k; i++)
+      for (int j = 0; j < a; j++)
+        std::copy(c.Gcode.v.begin() + (size_t)(a * nodes[i] + j) * K,
+                  c.Gcode.v.begin() + (size_t)(a * nodes[i] + j + 1) * K,
+                  GR.v.begin() + (size_t)(a * i + j) * K);
+    if (!mat_inverse(GR, Rinv)) {
+      err = "these k nodes do not determine the data";
+      return kESingular;
+    }
+    return kOk;
+  }
+  // Systematic form: a present data block is its own row of G' (a unit
+  // row), so only the missing data columns M need solving.  With Q the
+  // parity rows received, y_Q = A x_P + B x_M (A = G'[Q][present columns],
+  // B = G'[Q][M], |Q| = |M|) and x_P = y_P, hence x_M = B^-1 y_Q + B^-1 A y_P
+  // (characteristic 2): the same rows as the full inverse, for an |M|^3
+  // elimination instead of a K^3 one.
+  std::vector<int> pos_of_col(K, -1), qpos, mcols, pcols;
   for (int i = 0; i < c.k; i++)
-    for (int j = 0; j < a; j++)
-      std::copy(c.Gcode.v.begin() + (size_t)(a * nodes[i] + j) * K,
-                c.Gcode.v.begin() + (size_t)(a * nodes[i] + j + 1) * K,
-                GR.v.begin() + (size_t)(a * i + j) * K);
-  if (!mat_inverse(GR, Rinv)) {
+    for (int j = 0; j < a; j++) {
+      if (nodes[i] < c.k)
+        pos_of_col[a * nodes[i] + j] = a * i + j;
+      else
+        qpos.push_back(a * i + j);
+    }
+  for (int col = 0; col < K; col++) (pos_of_col[col] < 0 ? mcols : pcols).push_back(col);
+  Rinv = Mat(K, K);
+  for (int col : pcols) Rinv.at(col, pos_of_col[col]) = 1;
+  const int m = (int)mcols.size();
+  if (m == 0) return kOk;
+  Mat B(m, m), A(m, (int)pcols.size()), Binv;
+  for (int qi = 0; qi < m; qi++) {
+    const int row = a * nodes[qpos[qi] / a] + qpos[qi] % a;  // row of G'
+    for (int mi = 0; mi < m; mi++) B.at(qi, mi) = c.Gcode.at(row, mcols[mi]);
+    for (size_t pi = 0; pi < pcols.size(); pi++) A.at(qi, (int)pi) = c.Gcode.at(row, pcols[pi]);
+  }
+  if (!mat_inverse(B, Binv)) {
     err = "these k nodes do not determine the data";
     return kESingular;
+  }
+  Mat BA = pcols.empty() ? Mat(m, 0) : mat_mul(Binv, A);
+  for (int mi = 0; mi < m; mi++) {
+    const int col = mcols[mi];
+    for (int qi = 0; qi < m; qi++) Rinv.at(col, qpos[qi]) = Binv.at(mi, qi);
+    for (size_t pi = 0; pi < pcols.size(); pi++)
+      Rinv.at(col, pos_of_col[pcols[pi]]) = BA.at(mi, (int)pi);
   }
   return kOk;
 }

@@ -312,21 +312,13 @@ void pmrc_server::run() {
     }
     for (size_t i = 0; i < active.size();) {
       Req *r = active[i];
-      bool fin = false;
-      if (r->state == kRunning && cudaEventQuery(r->ev_out) == cudaSuccess) {
-        r->state = kDone;
-        fin = true;
-      } else if (r->state == kFailed) {
-        fin = true;
-      }
+      // finished: outputs copied back (the copy follows the iteration's
+      // kernel on the copy-back stream), or refused while building the
+      // iteration (then it was never part of one)
+      const bool fin = (r->state == kRunning && cudaEventQuery(r->ev_out) == cudaSuccess) ||
+                       r->state == kFailed;
       if (fin) {
-        bool in_flight_iter = false;  // a failed request may still be in an iteration
-        for (auto &it : inflight)
-          for (Req *q : it.reqs) in_flight_iter |= (q == r);
-        if (in_flight_iter) {
-          i++;
-          continue;
-        }
+        if (r->state == kRunning) r->state = kDone;
         arena->release(r->off, r->in_span + r->out_bytes);
         r->t_done = Clock::now();
         if (r->state == kDone) {
@@ -427,6 +419,7 @@ void pmrc_server_destroy(pmrc_server *s) {
 }
 
 int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) {
+  const Clock::time_point t_submit = Clock::now();
   if (!s || !q || !q->code || !q->in || !q->out || q->block_bytes == 0)
     return sfail(PMRC_EINVAL, "NULL argument or empty block");
   const pmrc_code *c = q->code;
@@ -438,41 +431,75 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   r->in = q->in;
   r->out = q->out;
   const size_t a = c->m.alpha, K = c->m.k * a, N = c->m.n * a;
+  // Build (or find) the request's coefficient plan here, on the caller's
+  // thread, and upload it to the server's device: the scheduler then only
+  // assembles work items.  Plan time counts in the request's latency.
+  std::string err;
+  int rc = kOk;
+  const void *image = nullptr;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != s->device) cudaSetDevice(s->device);
   switch (q->op) {
     case PMRC_OP_ENCODE:
       r->nin = K;
       r->nout = c->m.systematic ? N - K : N;
       r->user_bytes = (int64_t)K * r->B;
+      rc = c->encode->device_image(&image, err);
       break;
     case PMRC_OP_REPAIR: {
-      if (!q->helpers) return sfail(PMRC_EINVAL, "repair needs helpers");
+      if (!q->helpers) {
+        rc = kEInval;
+        err = "repair needs helpers";
+        break;
+      }
+      if (a > 16) {
+        rc = kEUnsupported;
+        err = "served repair needs alpha <= 16";
+        break;
+      }
       r->failed = q->failed;
       r->helpers.assign(q->helpers, q->helpers + c->m.d);
-      Mat D;
-      std::string err;
-      int rc = newcomer_matrix(c->m, q->failed, q->helpers, D, err);
-      if (rc) return sfail(rc, err);
-      if (a > 16) return sfail(PMRC_EUNSUPPORTED, "served repair needs alpha <= 16");
+      std::shared_ptr<FusedRepairPlan> fp;
+      rc = fused_repair_plan(c, q->failed, q->helpers, fp, err);
+      if (!rc) rc = fp->device_image(&image, err);
       r->nin = (size_t)c->m.d * a;
       r->nout = a;
       r->user_bytes = (int64_t)a * r->B;
       break;
     }
     case PMRC_OP_DECODE: {
-      if (!q->nodes) return sfail(PMRC_EINVAL, "decode needs nodes");
+      if (!q->nodes) {
+        rc = kEInval;
+        err = "decode needs nodes";
+        break;
+      }
       r->nodes.assign(q->nodes, q->nodes + c->m.k);
-      Mat R;
-      std::string err;
-      int rc = decode_matrix(c->m, q->nodes, R, err);
-      if (rc) return sfail(rc, err);
+      std::vector<char> seen(c->m.n, 0);
+      for (int i = 0; i < c->m.k && !rc; i++) {
+        if (q->nodes[i] < 0 || q->nodes[i] >= c->m.n || seen[q->nodes[i]]) {
+          rc = kEInval;
+          err = "nodes: out of range or repeated node id";
+        } else {
+          seen[q->nodes[i]] = 1;
+        }
+      }
+      if (!rc) {
+        std::shared_ptr<Plan> dp;
+        rc = decode_plan(c, q->nodes, std::vector<char>(K, 1), dp, err);
+        if (!rc) rc = dp->device_image(&image, err);
+      }
       r->nin = K;
       r->nout = K;
       r->user_bytes = (int64_t)K * r->B;
       break;
     }
     default:
-      return sfail(PMRC_EINVAL, "unknown operation");
+      rc = kEInval;
+      err = "unknown operation";
   }
+  if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+  if (rc) return sfail(rc, err);
   r->in_bytes = r->nin * r->B;
   r->out_bytes = r->nout * r->B;
   r->in_span = (r->in_bytes + kAlign - 1) & ~(kAlign - 1);
@@ -481,7 +508,7 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   if (cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return sfail(PMRC_ECUDA, "cudaEventCreate");
-  r->t_submit = Clock::now();
+  r->t_submit = t_submit;
   {
     std::lock_guard<std::mutex> g(s->mu);
     if (s->stop) return sfail(PMRC_EBUSY, "server is stopping");

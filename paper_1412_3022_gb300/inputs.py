@@ -60,14 +60,18 @@ def batch_mix(nstripes: int, seed: int, ks=(4, 8, 16), lo=4096, hi=1 << 20,
 
 
 def serve_requests(count: int, seed: int, ks=(4, 8, 12, 16), lo=64 << 10, hi=64 << 20,
-                   mix=(0.60, 0.25, 0.15), rate_per_s: float = 1000.0):
+                   mix=(0.60, 0.25, 0.15), rate_per_s: float = 1000.0, patterns: int = 4):
     """Serving workload: Poisson arrivals (exponential gaps at `rate_per_s`),
     k uniform on `ks`, stripe size log-uniform on [lo, hi], operation mix
     (encode, repair, reconstruct).  Block size = ceil(stripe / (k*alpha))
-    rounded up to 16 bytes; the last data block is zero-padded."""
+    rounded up to 16 bytes; the last data block is zero-padded.  A
+    reconstruction reads the k nodes of one of `patterns` seeded node sets
+    per k (the nodes up while a few others are down serve many stripes)."""
     r = rng(seed)
     t = 0.0
     out = []
+    pools = {k: [sorted(int(x) for x in r.choice(2 * k, k, replace=False))
+                 for _ in range(patterns)] for k in ks}
     for i in range(count):
         t += r.exponential(1.0 / rate_per_s)
         k = int(r.choice(ks))
@@ -80,6 +84,6 @@ def serve_requests(count: int, seed: int, ks=(4, 8, 12, 16), lo=64 << 10, hi=64 
         n = 2 * k
         out.append({"id": i, "t": t, "op": op, "k": k, "stripe_bytes": stripe,
                     "block_bytes": nb, "failed": int(r.integers(0, n)),
-                    "nodes": sorted(int(x) for x in r.choice(n, k, replace=False)),
+                    "nodes": pools[k][int(r.integers(0, patterns))],
                     "seed": int(r.integers(0, 2**31 - 1))})
     return out

@@ -154,3 +154,23 @@ def test_serving_refuses_bad_requests_and_cancels_queued():
     st, _ = srv.wait(b, timeout_ms=0)
     assert st == P.PMRC_EBUSY                       # cancelled before admission
     srv.close()
+
+
+def test_serving_many_small_requests_all_complete():
+    """Hundreds of tiny requests finish within microseconds of each other,
+    so output copies often complete while their iteration is still being
+    retired; every request must still be retired exactly once."""
+    c = P.Code(8, 4, 1, 1)
+    B = 256
+    X = inputs.blocks(12, B, seed=5)
+    want = O.encode(8, 4, 1, True, X)[12:]
+    xin = pinned(X)
+    outs = [torch.zeros((12, B), dtype=torch.uint8).pin_memory() for _ in range(300)]
+    srv = P.Server(budget_bytes=8 << 20, max_slots=32)
+    ids = [srv.submit(P.PMRC_OP_ENCODE, c, B, xin, o) for o in outs]
+    for rid in ids:
+        assert srv.wait(rid, timeout_ms=20000)[0] == P.PMRC_OK
+    assert srv.stats()["completed"] == 300
+    for o in outs:
+        assert np.array_equal(o.numpy(), want)
+    srv.close()

@@ -146,3 +146,13 @@ def test_encode_kernel_choice():
         c.set_encode_kernel(P.PMRC_KERNEL_BITSLICED)
     assert e.value.rc == P.PMRC_EUNSUPPORTED
     c.set_encode_kernel(P.PMRC_KERNEL_AUTO)
+
+
+@pytest.mark.parametrize("S", [list(range(16)), list(range(16, 32)),
+                               [0, 2, 3, 5, 7, 11, 13, 17, 19, 20, 21, 22, 23, 27, 29, 31],
+                               [31, 1, 17, 4, 30, 6, 8, 25, 10, 12, 14, 15, 18, 20, 22, 24]])
+def test_k16_systematic_decode_matrix_matches_full_inverse(S):
+    """The library inverts only the block of missing data columns for the
+    systematic form; the rows must equal the oracle's full inverse."""
+    c = P.Code(32, 16, 1, 1)
+    assert np.array_equal(c.decode_matrix(S), O.decode_matrix(32, 16, 1, True, S))
