@@ -137,6 +137,8 @@ def _addr(x) -> int:
 
 
 def _ptrs(seq):
+    if isinstance(seq, ctypes.Array):   # built once by ptr_array()
+        return seq
     arr = (ctypes.c_void_p * len(seq))()
     for i, x in enumerate(seq):
         arr[i] = _addr(x) or None
@@ -144,10 +146,24 @@ def _ptrs(seq):
 
 
 def _ints(seq):
+    if isinstance(seq, ctypes.Array):   # built once by int_array()
+        return seq
     arr = (ctypes.c_int * len(seq))()
     for i, x in enumerate(seq):
         arr[i] = int(x)
     return arr
+
+
+def ptr_array(seq):
+    """A pointer array (tensors, addresses or None) converted once, for
+    callers that repeat a call on the same blocks: every call below accepts
+    it in place of a sequence and skips the per-call conversion."""
+    return _ptrs(list(seq))
+
+
+def int_array(seq):
+    """A node-id list converted once (see ptr_array)."""
+    return _ints(list(seq))
 
 
 def _stream(s) -> int:

@@ -3,9 +3,13 @@
 // Same operation as region.cu (out[r] = sum_c M[r][c] * in[c], Sec. 2/3.1),
 // for an encode matrix fixed at build time, with a different inner loop:
 //
-//   * each thread owns 32 consecutive bytes of every block of a tile and
-//     turns them into eight 32-bit bit planes (plane i = bit i of the 32
-//     bytes) with a 3-stage delta-swap transpose of the 8 words;
+//   * each thread owns 32 consecutive bytes of every block of a tile; it
+//     streams its inputs through a 5-slot shared-memory ring with cp.async,
+//     four inputs ahead of the one in use (the XOR work per input is short,
+//     so the loads must be in flight well before they are needed), and
+//     turns each into eight 32-bit bit planes (plane i = bit i of the 32
+//     bytes) with a 3-stage transpose of the 8 words, each stage a pair of
+//     bit-field selects (one 3-input logic op each) on shifted copies;
 //   * from the planes it forms Q[s] (XOR of the subset s of planes 0-3) and
 //     R[s] (subset of planes 4-7);
 //   * output plane i of a row gains Q[a] ^ R[b] per input, where a and b are
@@ -13,13 +17,21 @@
 //     XOR per (row, plane, input), against three table lookups and two XORs
 //     per 4 bytes in region.cu;
 //   * accumulated planes go back to bytes with the same transpose (it is its
-//     own inverse) and are stored with 16-byte streaming stores.
+//     own inverse) and are stored with 16-byte streaming stores;
+//   * the inputs of a block are walked by a loop whose body switches on the
+//     input only for the accumulate XORs, halving the code of a block;
+//   * the grid is persistent, one 512-thread CTA per SM: each CTA stays on
+//     one block of the matrix and its warps loop over that block's 1 KiB
+//     column tiles, so an SM holds one block's straight-line code (tens of
+//     KiB), fetched into its instruction caches once and then re-executed;
+//     blocks get CTAs in proportion to their cost.
 //
 // The XOR schedules are generated at build time from the library's own
 // construction (gen_bitslice.cpp); the launcher only uses a kernel whose
 // matrix checksum equals the code's encode matrix.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "bitslice.h"
@@ -27,14 +39,19 @@
 namespace pmrc {
 namespace {
 
-constexpr int kBsThreads = 256;
+constexpr int kBsThreads = 512;       // one CTA per SM (128 registers a thread)
 constexpr int kBsBytes = 32;          // bytes per thread per tile
 constexpr int kBsMaxPtr = 256;
+constexpr int kBsAhead = 4;           // inputs prefetched ahead of the one in use
+constexpr int kBsSlots = kBsAhead + 1;  // shared-memory ring (never the slot being read)
+constexpr uint32_t kBsUnit = 32 * kBsBytes;  // bytes of column per warp tile
+constexpr int kBsMaxBlocks = 32;
 
 struct BsArgs {
   uint64_t nbytes;  // bytes covered by this launch (multiple of kBsBytes)
   uint32_t hi28, hi30, hi31;  // 2^28, 2^30, 2^31: right shifts as multiply-high
   uint32_t x16, x4, x2;       // left shifts as multiplies
+  uint16_t cta_start[kBsMaxBlocks + 1];  // CTAs [cta_start[b], cta_start[b+1]) run block b
   uint8_t *ptr[kBsMaxPtr];    // K input blocks, then the output blocks
 };
 
@@ -43,9 +60,9 @@ struct BsCtx {
   uint64_t off;
 };
 
-__device__ __forceinline__ bool bs_ctx(const BsArgs &a, BsCtx &x) {
+__device__ __forceinline__ bool bs_ctx(const BsArgs &a, BsCtx &x, uint32_t unit) {
   x.a = &a;
-  x.off = ((uint64_t)blockIdx.x * kBsThreads + threadIdx.x) * kBsBytes;
+  x.off = (uint64_t)unit * kBsUnit + (threadIdx.x % 32) * kBsBytes;
   return x.off < a.nbytes;
 }
 
@@ -58,34 +75,63 @@ __device__ __forceinline__ void bs_zero(uint32_t (&acc)[8][8]) {
 
 // 8x8 bit transpose inside each byte lane of 8 words: afterwards word i
 // holds bit i of the 32 bytes (bit 8m+j = bit i of byte m of word j).  The
-// transform is an involution.  Shifts run as multiplies on the FMA pipe.
+// transform is an involution.  Each stage exchanges the bit fields `mask` of
+// the lower word with the fields `mask << s` of the upper one: both words are
+// rebuilt as a select between the word and a shifted copy of its partner (one
+// 3-input logic op each); the shifts run as multiplies on the FMA pipe.
 __device__ __forceinline__ void bs_transpose(uint32_t (&w)[8], const BsArgs &a) {
 #pragma unroll
   for (int j = 0; j < 4; j++) {
-    const uint32_t t = (__umulhi(w[j], a.hi28) ^ w[j + 4]) & 0x0F0F0F0Fu;
-    w[j + 4] ^= t;
-    w[j] ^= t * a.x16;
+    const uint32_t sl = __umulhi(w[j], a.hi28), sh = w[j + 4] * a.x16;
+    w[j + 4] = (sl & 0x0F0F0F0Fu) | (w[j + 4] & ~0x0F0F0F0Fu);
+    w[j] = (sh & 0xF0F0F0F0u) | (w[j] & ~0xF0F0F0F0u);
   }
 #pragma unroll
   for (int j = 0; j < 8; j += 4)
 #pragma unroll
     for (int q = 0; q < 2; q++) {
-      const uint32_t t = (__umulhi(w[j + q], a.hi30) ^ w[j + q + 2]) & 0x33333333u;
-      w[j + q + 2] ^= t;
-      w[j + q] ^= t * a.x4;
+      const uint32_t sl = __umulhi(w[j + q], a.hi30), sh = w[j + q + 2] * a.x4;
+      w[j + q + 2] = (sl & 0x33333333u) | (w[j + q + 2] & ~0x33333333u);
+      w[j + q] = (sh & 0xCCCCCCCCu) | (w[j + q] & ~0xCCCCCCCCu);
     }
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
-    const uint32_t t = (__umulhi(w[j], a.hi31) ^ w[j + 1]) & 0x55555555u;
-    w[j + 1] ^= t;
-    w[j] ^= t * a.x2;
+    const uint32_t sl = __umulhi(w[j], a.hi31), sh = w[j + 1] * a.x2;
+    w[j + 1] = (sl & 0x55555555u) | (w[j + 1] & ~0x55555555u);
+    w[j] = (sh & 0xAAAAAAAAu) | (w[j] & ~0xAAAAAAAAu);
   }
 }
 
-__device__ __forceinline__ void bs_planes(const BsCtx &x, int col, uint32_t (&Q)[16],
+// Asynchronous copy of this thread's 32 bytes of input `col` into ring slot
+// `slot` of the shared-memory staging area (cp.async, one commit group per
+// input).  Each thread reads back only what it copied, so no barrier is
+// needed; cp.async.wait_group orders the read after the copy.
+__device__ __forceinline__ void bs_prefetch(const BsCtx &x, int col, int slot) {
+  extern __shared__ __align__(16) uint8_t bs_smem[];
+  const uint8_t *src = x.a->ptr[col] + x.off;
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(
+      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16), "l"(src + 16)
+               : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// An empty commit group: keeps the number of groups in flight the same for
+// every input of a block shorter than the prefetch distance.
+__device__ __forceinline__ void bs_commit_empty() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bs_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bs_planes(const BsCtx &x, int slot, uint32_t (&Q)[16],
                                           uint32_t (&R)[16]) {
-  const uint4 *p = reinterpret_cast<const uint4 *>(x.a->ptr[col] + x.off);
-  const uint4 u = __ldg(p), v = __ldg(p + 1);
+  extern __shared__ __align__(16) uint8_t bs_smem[];
+  const uint4 *p = reinterpret_cast<const uint4 *>(
+      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
+  const uint4 u = p[0], v = p[1];
   uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
   bs_transpose(w, *x.a);
   Q[0] = 0;
@@ -128,6 +174,7 @@ struct BsKernel {
   unsigned long long checksum;
   long long xors;
   void (*fn)(BsArgs);
+  const int *cost;  // relative cost of each block per tile
 };
 
 #include "bitslice_gen.cuh"
@@ -168,9 +215,46 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
   memset(a.ptr, 0, sizeof a.ptr);
   for (int i = 0; i < b.ninputs; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
   for (int j = 0; j < b.noutputs; j++) a.ptr[b.ninputs + j] = out[j];
-  const uint64_t tile = (uint64_t)kBsThreads * kBsBytes;
-  const dim3 grid((unsigned)((nbytes + tile - 1) / tile), (unsigned)b.nblocks);
-  b.fn<<<grid, kBsThreads, 0, stream>>>(a);
+  // one CTA per SM; each block gets CTAs in proportion to its cost, at
+  // least one, and no more than it has warp tiles to hand out
+  static int sms = 0;
+  static bool smem_set[64] = {};
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  }
+  const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes;  // 80 KiB
+  if (!smem_set[id]) {
+    cudaError_t e = cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set[id] = true;
+  }
+  const uint64_t units = (nbytes + kBsUnit - 1) / kBsUnit;
+  const uint64_t cap = std::max<uint64_t>(1, (units + kBsThreads / 32 - 1) / (kBsThreads / 32));
+  double total = 0;
+  for (int i = 0; i < b.nblocks; i++) total += b.cost[i];
+  int cnt[kBsMaxBlocks];
+  int used = 0;
+  for (int i = 0; i < b.nblocks; i++) {
+    cnt[i] = std::max(1, (int)(sms * b.cost[i] / total));
+    cnt[i] = (int)std::min<uint64_t>(cnt[i], cap);
+    used += cnt[i];
+  }
+  for (; used < sms; used++) {  // hand out the rest to the slowest block
+    int best = -1;
+    double worst = 0;
+    for (int i = 0; i < b.nblocks; i++) {
+      const double t = (double)b.cost[i] / cnt[i];
+      if ((uint64_t)cnt[i] < cap && t > worst) worst = t, best = i;
+    }
+    if (best < 0) break;
+    cnt[best]++;
+  }
+  a.cta_start[0] = 0;
+  for (int i = 0; i < b.nblocks; i++) a.cta_start[i + 1] = (uint16_t)(a.cta_start[i] + cnt[i]);
+  for (int i = b.nblocks + 1; i <= kBsMaxBlocks; i++) a.cta_start[i] = a.cta_start[b.nblocks];
+  b.fn<<<a.cta_start[b.nblocks], kBsThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
