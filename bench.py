@@ -44,6 +44,30 @@ WORKLOAD = ("PM-MSR n=16 k=8 d=14 alpha=7 GF(2^8)/0x11D, 56 data blocks x 1 MiB 
 FLUSH_BYTES = 512 << 20
 
 
+# ------------------------------------------------------------ multi-rank
+# Stripes are independent, so N ranks run N replicas of the step on their own
+# seeded stripes (weak scaling) with no collective on the data path; the only
+# communication is the timing reduction below.
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s stripe (distinct stripes per rank)."""
+    return seed + 1000 * rank
+
+
+def ranks_max(dist, x: float, device) -> float:
+    """Largest x over all ranks (x itself when running alone)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbps(user_bytes_per_rank: int, world: int, max_ms: float) -> float:
+    """Aggregate user-data throughput of all ranks over the slowest rank's time."""
+    return user_bytes_per_rank * world / (max_ms * 1e-3) / 1e9
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -214,7 +238,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B = args.block_bytes
-    W = Workload(torch, P, inputs, B, args.seed + 1000 * rank, dev)
+    W = Workload(torch, P, inputs, B, rank_seed(args.seed, rank), dev)
     ops = W.ops()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -251,13 +275,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     ck = clocks.stop()
     op_ms = {n: sum(a.elapsed_time(b) for a, b in ev[n]) / args.steps for n in names}
-    step_ms = sum(op_ms.values())
-    if dist:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = ranks_max(dist, sum(op_ms.values()), dev)
     user_step = sum(W.user.values())
-    value = user_step * world / (step_ms * 1e-3) / 1e9
+    value = whole_job_gbps(user_step, world, step_ms)
     hbm, peak_src = measured_peaks()
 
     per_op = {}
@@ -297,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
                               "alg_bytes": W.alg["repair_fused"],
                               "frac_hbm": round(W.alg["repair_fused"] / (fused_ms * 1e-3) / 1e9
                                                 / hbm, 4)}
-    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream)
+    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
     result = {
@@ -544,7 +564,7 @@ def run_serving(torch, P, inputs, args):
     return out
 
 
-def run_e2e(torch, W, args, dev, stream):
+def run_e2e(torch, W, args, dev, stream, dist=None, world=1):
     """Same step through the public API with host buffers: pinned H2D of the
     stripe, every operation, D2H of every block the step produced."""
     B, K, a = W.B, K_ * A_, A_
@@ -574,6 +594,8 @@ def run_e2e(torch, W, args, dev, stream):
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -581,10 +603,13 @@ def run_e2e(torch, W, args, dev, stream):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        dist.barrier()
+    ms = ranks_max(dist, e0.elapsed_time(e1) / args.steps, dev)
     user = sum(W.user.values())
-    return {"value": round(user / (ms * 1e-3) / 1e9, 2), "unit": "GB/s", "ms_per_step": round(ms, 4),
-            "h2d_bytes_per_step": K * B, "d2h_bytes_per_step": out_rows * B}
+    return {"value": round(whole_job_gbps(user, world, ms), 2), "unit": "GB/s",
+            "ms_per_step": round(ms, 4), "h2d_bytes_per_step": K * B,
+            "d2h_bytes_per_step": out_rows * B}
 
 
 # ------------------------------------------------------------------ oracle
