@@ -22,6 +22,11 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
   region_apply / encode      pinned: brute-force definition on tiny inputs
   repair_*                   pinned: repair reproduces every node exactly
   decode                     pinned: every k-subset recovers the data
+  dc_decode / decode_specific
+                             pinned: every k-subset (n <= 8) and sampled
+                             subsets at n = 16 recover the data exactly
+  encode_precode             pinned: data as nodes 0..k-1 re-decodes to itself
+                             and every k-subset of the result recovers the data
 """
 from __future__ import annotations
 
@@ -95,6 +100,9 @@ def lib():
                 "or_repair_newcomer": (i, [i, i, i, i, ip, u8p, u8p, sz]),
                 "or_decode_matrix": (i, [i, i, i, i, ip, u8p]),
                 "or_decode": (i, [i, i, i, i, ip, u8p, u8p, sz]),
+                "or_dc_decode": (i, [i, i, i, ip, u8p, u8p, sz]),
+                "or_decode_specific": (i, [i, i, i, i, ip, u8p, u8p, sz]),
+                "or_encode_precode": (i, [i, i, i, u8p, u8p, sz]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -278,4 +286,41 @@ def decode(n: int, k: int, construction: int, systematic: bool, nodes, node_bloc
     out = np.zeros((k * a, B), np.uint8)
     _check(lib().or_decode(n, k, construction, int(systematic), _ip(s), _u8(node_blocks),
                            _u8(out), B), "decode")
+    return out
+
+
+def dc_decode(n: int, k: int, construction: int, nodes, node_blocks: np.ndarray) -> np.ndarray:
+    """The data collector's message recovery (k*alpha message blocks)."""
+    d, a = params(n, k)
+    s = _ints(nodes)
+    node_blocks = np.ascontiguousarray(node_blocks, dtype=np.uint8)
+    assert node_blocks.shape[0] == k * a and s.size == k
+    B = node_blocks.shape[1]
+    out = np.zeros((k * a, B), np.uint8)
+    _check(lib().or_dc_decode(n, k, construction, _ip(s), _u8(node_blocks), _u8(out), B),
+           "dc_decode")
+    return out
+
+
+def decode_specific(n: int, k: int, construction: int, systematic: bool, nodes,
+                    node_blocks: np.ndarray) -> np.ndarray:
+    d, a = params(n, k)
+    s = _ints(nodes)
+    node_blocks = np.ascontiguousarray(node_blocks, dtype=np.uint8)
+    assert node_blocks.shape[0] == k * a and s.size == k
+    B = node_blocks.shape[1]
+    out = np.zeros((k * a, B), np.uint8)
+    _check(lib().or_decode_specific(n, k, construction, int(systematic), _ip(s),
+                                    _u8(node_blocks), _u8(out), B), "decode_specific")
+    return out
+
+
+def encode_precode(n: int, k: int, construction: int, data: np.ndarray) -> np.ndarray:
+    """Parity blocks ((n-k)*alpha) of the systematic code, by decoding then encoding."""
+    d, a = params(n, k)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    assert data.shape[0] == k * a
+    B = data.shape[1]
+    out = np.zeros(((n - k) * a, B), np.uint8)
+    _check(lib().or_encode_precode(n, k, construction, _u8(data), _u8(out), B), "encode_precode")
     return out

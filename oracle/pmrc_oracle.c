@@ -513,3 +513,194 @@ int or_decode(int n, int k, int construction, int systematic, const int *nodes,
     free(Rinv);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The product-matrix algorithms that Sec. 4 calls "specific" (as opposed    */
+/* to linearized): the data collector of the seminal PM paper, and the      */
+/* systematic encode built from it by decoding then encoding (Sec. 3.2).    */
+/* The paper defers the data collector to the seminal paper; the steps      */
+/* below are restated from the definitions of Sec. 2-3.                     */
+/* ------------------------------------------------------------------------ */
+
+/* Message recovery from the k*alpha blocks of nodes[] (node-major, in list
+ * order), one byte column at a time.  With DC the listed nodes:
+ *   1. Y_DC = Phi_DC S1 + Lambda_DC Phi_DC S2 (k x alpha), so
+ *      A = Y_DC Phi_DC^t = P + Lambda_DC Q, where P = Phi_DC S1 Phi_DC^t and
+ *      Q = Phi_DC S2 Phi_DC^t are symmetric k x k;
+ *   2. for i != j:  A_ij = P_ij + lambda_i Q_ij  and  A_ji = P_ij + lambda_j Q_ij,
+ *      so Q_ij = (A_ij + A_ji) / (lambda_i + lambda_j), P_ij = A_ij + lambda_i Q_ij
+ *      (the diagonals of P and Q are never needed);
+ *   3. for each of the first alpha listed nodes i, the alpha values P_ij
+ *      (j != i, in list order) are phi_i^t S1 phi_j: with F_i the alpha x
+ *      alpha matrix whose columns are those phi_j, phi_i^t S1 = [P_ij]_j F_i^-1;
+ *      likewise phi_i^t S2 = [Q_ij]_j F_i^-1;
+ *   4. stacking these rows, Phi_sub S1 = U and Phi_sub S2 = V with Phi_sub the
+ *      rows phi_i of those alpha nodes, so S1 = Phi_sub^-1 U, S2 = Phi_sub^-1 V;
+ *   5. the message symbols are read out of S1 and S2 through L (Sec. 3.1).
+ * msg receives the k*alpha message blocks. */
+int or_dc_decode(int n, int k, int construction, const int *nodes, const uint8_t *node_blocks,
+                 uint8_t *msg, size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    for (int i = 0; i < k; i++) {
+        if (nodes[i] < 0 || nodes[i] >= n)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (nodes[j] == nodes[i])
+                return OR_EINVAL;
+    }
+    uint8_t *phi = (uint8_t *)malloc((size_t)n * a);
+    uint8_t *lam = (uint8_t *)malloc((size_t)n);
+    int *L = (int *)malloc(sizeof(int) * d * a);
+    uint8_t *Finv = (uint8_t *)malloc((size_t)a * a * a);   /* F_i^-1, i < alpha */
+    uint8_t *F = (uint8_t *)malloc((size_t)a * a);
+    uint8_t *Psub = (uint8_t *)malloc((size_t)a * a);
+    uint8_t *Psubinv = (uint8_t *)malloc((size_t)a * a);
+    uint8_t *Y = (uint8_t *)malloc((size_t)k * a);
+    uint8_t *A = (uint8_t *)malloc((size_t)k * k);
+    uint8_t *P = (uint8_t *)malloc((size_t)k * k);
+    uint8_t *Q = (uint8_t *)malloc((size_t)k * k);
+    uint8_t *U = (uint8_t *)malloc((size_t)a * a);
+    uint8_t *V = (uint8_t *)malloc((size_t)a * a);
+    int rc = or_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK)
+        or_index_matrix(k, L);
+    /* lambda_i + lambda_j must be invertible for every listed pair */
+    for (int i = 0; i < k && rc == OR_OK; i++)
+        for (int j = 0; j < i && rc == OR_OK; j++)
+            if (or_add(lam[nodes[i]], lam[nodes[j]]) == 0)
+                rc = OR_ESINGULAR;
+    /* F_i: column c is phi of the c-th listed node other than i */
+    for (int i = 0; i < a && rc == OR_OK; i++) {
+        for (int c = 0, j = 0; j < k; j++) {
+            if (j == i)
+                continue;
+            for (int l = 0; l < a; l++)
+                F[l * a + c] = phi[(size_t)nodes[j] * a + l];
+            c++;
+        }
+        rc = or_invert(a, F, Finv + (size_t)i * a * a);
+    }
+    if (rc == OR_OK) {
+        for (int i = 0; i < a; i++)
+            memcpy(Psub + (size_t)i * a, phi + (size_t)nodes[i] * a, (size_t)a);
+        rc = or_invert(a, Psub, Psubinv);
+    }
+    for (size_t t = 0; t < nbytes && rc == OR_OK; t++) {
+        for (int i = 0; i < k; i++)
+            for (int l = 0; l < a; l++)
+                Y[i * a + l] = node_blocks[(size_t)(a * i + l) * nbytes + t];
+        /* step 1 */
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) {
+                uint8_t s = 0;
+                for (int l = 0; l < a; l++)
+                    s = or_add(s, or_gf_mul(Y[i * a + l], phi[(size_t)nodes[j] * a + l]));
+                A[i * k + j] = s;
+            }
+        /* step 2 */
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < k; j++) {
+                if (i == j)
+                    continue;
+                uint8_t q = or_gf_mul(or_add(A[i * k + j], A[j * k + i]),
+                                      or_gf_inv(or_add(lam[nodes[i]], lam[nodes[j]])));
+                Q[i * k + j] = q;
+                P[i * k + j] = or_add(A[i * k + j], or_gf_mul(lam[nodes[i]], q));
+            }
+        /* step 3 */
+        for (int i = 0; i < a; i++)
+            for (int b = 0; b < a; b++) {
+                uint8_t u = 0, v = 0;
+                for (int c = 0, j = 0; j < k; j++) {
+                    if (j == i)
+                        continue;
+                    uint8_t f = Finv[(size_t)i * a * a + c * a + b];
+                    u = or_add(u, or_gf_mul(P[i * k + j], f));
+                    v = or_add(v, or_gf_mul(Q[i * k + j], f));
+                    c++;
+                }
+                U[i * a + b] = u;
+                V[i * a + b] = v;
+            }
+        /* steps 4 and 5 */
+        for (int x = 0; x < a; x++)
+            for (int b = 0; b < a; b++) {
+                uint8_t s1 = 0, s2 = 0;
+                for (int i = 0; i < a; i++) {
+                    s1 = or_add(s1, or_gf_mul(Psubinv[x * a + i], U[i * a + b]));
+                    s2 = or_add(s2, or_gf_mul(Psubinv[x * a + i], V[i * a + b]));
+                }
+                msg[(size_t)L[x * a + b] * nbytes + t] = s1;
+                msg[(size_t)L[(a + x) * a + b] * nbytes + t] = s2;
+            }
+    }
+    free(phi);
+    free(lam);
+    free(L);
+    free(Finv);
+    free(F);
+    free(Psub);
+    free(Psubinv);
+    free(Y);
+    free(A);
+    free(P);
+    free(Q);
+    free(U);
+    free(V);
+    return rc;
+}
+
+/* Specific decode.  For the non-systematic code the message is the data.
+ * The systematic code stores, on nodes 0..k-1, the PM codeword of the
+ * precoded message Z (Sec. 3.2), so the data is X = G~ Z: the data collector
+ * finds Z and the first k*alpha rows of G re-encode it. */
+int or_decode_specific(int n, int k, int construction, int systematic, const int *nodes,
+                       const uint8_t *node_blocks, uint8_t *data, size_t nbytes)
+{
+    if (!systematic)
+        return or_dc_decode(n, k, construction, nodes, node_blocks, data, nbytes);
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a, N = n * a;
+    uint8_t *Z = (uint8_t *)malloc((size_t)K * (nbytes ? nbytes : 1));
+    uint8_t *G = (uint8_t *)malloc((size_t)N * K);
+    int rc = or_dc_decode(n, k, construction, nodes, node_blocks, Z, nbytes);
+    if (rc == OR_OK)
+        rc = or_generator(n, k, construction, G);
+    if (rc == OR_OK)
+        or_region_apply(K, K, G, Z, nbytes, data, nbytes, nbytes);
+    free(Z);
+    free(G);
+    return rc;
+}
+
+/* Systematic encode by decoding then encoding (Sec. 3.2): the data blocks
+ * are taken as the contents of nodes 0..k-1, the data collector recovers the
+ * precoded message Z from them, and the remaining (n-k)*alpha rows of G
+ * encode Z into the parity blocks. */
+int or_encode_precode(int n, int k, int construction, const uint8_t *data, uint8_t *parity,
+                      size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a, N = n * a;
+    int *nodes = (int *)malloc(sizeof(int) * k);
+    uint8_t *Z = (uint8_t *)malloc((size_t)K * (nbytes ? nbytes : 1));
+    uint8_t *G = (uint8_t *)malloc((size_t)N * K);
+    for (int i = 0; i < k; i++)
+        nodes[i] = i;
+    int rc = or_dc_decode(n, k, construction, nodes, data, Z, nbytes);
+    if (rc == OR_OK)
+        rc = or_generator(n, k, construction, G);
+    if (rc == OR_OK)
+        or_region_apply(N - K, K, G + (size_t)K * K, Z, nbytes, parity, nbytes, nbytes);
+    free(nodes);
+    free(Z);
+    free(G);
+    return rc;
+}

@@ -326,6 +326,79 @@ def test_decode_k8_sampled_subsets(cons):
     _decode_subsets(n, k, cons, True, subsets)
 
 
+def _decode_specific_subsets(n, k, cons, systematic, subsets, B=6, seed=6):
+    a = k - 1
+    X = np.random.default_rng(seed).integers(0, 256, (k * a, B), dtype=np.uint8)
+    Y = O.encode(n, k, cons, systematic, X)
+    for S in subsets:
+        rows = [a * i + j for i in S for j in range(a)]
+        got = O.decode_specific(n, k, cons, systematic, list(S), Y[rows])
+        assert np.array_equal(got, X), S
+
+
+@pytest.mark.parametrize("systematic", [False, True])
+@pytest.mark.parametrize("cons", [O.VANILLA, O.SPARSE])
+@pytest.mark.parametrize("n,k", [(5, 3), (6, 3), (8, 4)])
+def test_data_collector_every_k_subset(n, k, cons, systematic):
+    """The data collector (P + Lambda Q split, alpha x alpha solves) returns
+    the unique data from every k nodes, in any listed order."""
+    subs = list(itertools.combinations(range(n), k))
+    subs += [tuple(reversed(S)) for S in subs[:5]]
+    _decode_specific_subsets(n, k, cons, systematic, subs)
+
+
+@pytest.mark.parametrize("cons", [O.VANILLA, O.SPARSE])
+def test_data_collector_k8_sampled_subsets(cons):
+    n, k = 16, 8
+    rng = np.random.default_rng(9)
+    subsets = [rng.permutation(rng.choice(n, k, replace=False)).tolist() for _ in range(12)]
+    subsets += [list(range(k)), list(range(n - k, n))]
+    _decode_specific_subsets(n, k, cons, True, subsets, B=3)
+    _decode_specific_subsets(n, k, cons, False, subsets[:4], B=3)
+
+
+def test_data_collector_message_is_pm_message():
+    """Non-systematic: the recovered message M(X) re-encodes, as Psi M, to
+    exactly the stored node contents (Sec. 3.1 product form)."""
+    n, k = 8, 4
+    d, a = O.params(n, k)
+    X = np.random.default_rng(3).integers(0, 256, (k * a, 5), dtype=np.uint8)
+    Y = O.encode(n, k, O.SPARSE, False, X)
+    S = [7, 2, 5, 0]
+    msg = O.dc_decode(n, k, O.SPARSE, S, Y[[a * i + j for i in S for j in range(a)]])
+    L = O.index_matrix(k)
+    Psi = O.psi(n, k, O.SPARSE)
+    T = O.gf_mul_table()
+    for t in range(X.shape[1]):
+        M = msg[L, t]                            # d x alpha message matrix
+        C = np.zeros((n, a), np.uint8)
+        for i in range(n):
+            for j in range(a):
+                acc = 0
+                for l in range(d):
+                    acc ^= int(T[Psi[i, l], M[l, j]])
+                C[i, j] = acc
+        assert np.array_equal(C.reshape(-1), Y[:, t])
+
+
+@pytest.mark.parametrize("cons", [O.VANILLA, O.SPARSE])
+@pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (16, 8)])
+def test_precode_encode_is_the_systematic_code(n, k, cons):
+    """Decoding the data as nodes 0..k-1 and encoding the rest (Sec. 3.2)
+    yields the systematic codeword G' X: the same parity as the linearized
+    G'' and a codeword whose every sampled k-subset decodes to the data."""
+    a = k - 1
+    X = np.random.default_rng(11).integers(0, 256, (k * a, 4), dtype=np.uint8)
+    par = O.encode_precode(n, k, cons, X)
+    assert np.array_equal(par, O.encode(n, k, cons, True, X)[k * a:])
+    Y = np.concatenate([X, par])
+    rng = np.random.default_rng(12)
+    for _ in range(6):
+        S = sorted(rng.choice(n, k, replace=False).tolist())
+        got = O.decode(n, k, cons, True, S, Y[[a * i + j for i in S for j in range(a)]])
+        assert np.array_equal(got, X)
+
+
 @pytest.mark.slow
 def test_decode_k8_every_subset_invertible():
     """All C(16,8) = 12870 node sets of the sparse systematic k=8 code have an
