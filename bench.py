@@ -317,6 +317,24 @@ def run_ours(args, rank, world, local_rank):
                               "alg_bytes": W.alg["repair_fused"],
                               "frac_hbm": round(W.alg["repair_fused"] / (fused_ms * 1e-3) / 1e9
                                                 / hbm, 4)}
+    # the paper's "specific" algorithms (Sec. 4) beside the linearized ones:
+    # data-collector decode of the same node set, precode systematic encode
+    ws_bytes = W.sysc.specific_workspace_bytes(B)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    spec = {
+        "decode_specific": (lambda: W.sysc.decode_specific(
+            W.c_S, W.c_args["dec_in"], W.c_args["dec_out"], B, ws.data_ptr(), ws_bytes, W.stream),
+            "decode", W.user["decode"]),
+        "encode_precode": (lambda: W.sysc.encode_precode(
+            W.c_args["x_ptrs"], W.c_args["par_ptrs"], B, ws.data_ptr(), ws_bytes, W.stream),
+            "sys_encode", W.user["sys_encode"]),
+    }
+    for name, (fn, linear, user) in spec.items():
+        ms = time_op(torch, stream, flush, args, fn)
+        per_op[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
+                        "linear_op": linear, "linear_over_specific": round(op_ms[linear] / ms, 3),
+                        "launches": 5 if name == "encode_precode" else 4 + (W.decode_missing > 0)}
+    del ws
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)

@@ -157,6 +157,51 @@ int pmrc_repair_noalloc(const pmrc_code *code, int failed, const int *helpers,
 int pmrc_decode(const pmrc_code *code, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t block_bytes, pmrc_stream_t stream);
 
+/* ---- "Specific" product-matrix algorithms (Sec. 4: "PM Spec." codes) ----
+ *
+ * The linearized calls above apply one matrix per operation (Sec. 3.1).  The
+ * two calls below run the seminal PM paper's own algorithms instead, which
+ * Sec. 3.2 and Sec. 4 compare against linearization:
+ *
+ *   data collector (pmrc_decode_specific): with DC the k listed nodes,
+ *     A = Y_DC Phi_DC^t = P + Lambda_DC Q with P, Q symmetric; the pairs
+ *     (A_ij, A_ji) give P_ij and Q_ij (i != j); alpha x alpha solves give
+ *     phi_i^t S1 and phi_i^t S2 for alpha of the nodes, and one more solve
+ *     gives S1 and S2, i.e. the message.  Systematic codes then re-encode
+ *     the missing data nodes from the precoded message (Sec. 3.2).
+ *   precode encode (pmrc_encode_precode): the systematic encode "by
+ *     successively decoding and encoding" (Sec. 3.2): the data blocks are
+ *     decoded as the contents of nodes 0..k-1 into the precoded message Z,
+ *     and Z is encoded into the parity nodes.  Same result as pmrc_encode on
+ *     a systematic handle (G'' X), computed the specific way.
+ *
+ * Each stage is one launch on `stream`; intermediate blocks live in a
+ * caller-owned device workspace of at least pmrc_specific_workspace_bytes()
+ * bytes (contents undefined afterwards; 256-byte alignment keeps every
+ * stage on the vectorized path).  Calls that share a workspace must not
+ * overlap on the GPU. */
+
+/* Workspace bytes the specific calls need for blocks of block_bytes bytes:
+ * (max(k(k-1), 2 alpha^2) + k(k-1) [+ k alpha if systematic]) blocks, each
+ * rounded up to 256 bytes.  0 if code is NULL. */
+size_t pmrc_specific_workspace_bytes(const pmrc_code *code, size_t block_bytes);
+
+/* Reconstruction from k nodes by the data collector.  Arguments and the
+ * data_out conventions (NULL entries skipped, aliased systematic blocks left
+ * in place) are those of pmrc_decode; present systematic blocks that are
+ * not aliased are copied.  PMRC_EINVAL for a missing or short workspace. */
+int pmrc_decode_specific(const pmrc_code *code, const int *nodes,
+                         const uint8_t *const *node_blocks, uint8_t *const *data_out,
+                         size_t block_bytes, void *workspace, size_t workspace_bytes,
+                         pmrc_stream_t stream);
+
+/* Systematic encode by decoding then encoding.  data: k*alpha device
+ * pointers; parity: (n-k)*alpha device pointers (none NULL).  The handle
+ * must be systematic (PMRC_EINVAL otherwise). */
+int pmrc_encode_precode(const pmrc_code *code, const uint8_t *const *data,
+                        uint8_t *const *parity, size_t block_bytes, void *workspace,
+                        size_t workspace_bytes, pmrc_stream_t stream);
+
 /* Encode kernel of a handle.  PMRC_KERNEL_AUTO (default): the bitsliced
  * kernel when one was generated at build time for this code (and the call's
  * pointers are 16-byte aligned, with no NULL output), the nibble-table kernel

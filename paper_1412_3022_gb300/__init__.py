@@ -75,6 +75,9 @@ _SIGNATURES = {
     "pmrc_repair_helpers": (_i, [_vp, _i, _i, _ip, _pp, _pp, _sz, _vp]),
     "pmrc_repair_newcomer": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
     "pmrc_decode": (_i, [_vp, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_specific_workspace_bytes": (_sz, [_vp, _sz]),
+    "pmrc_decode_specific": (_i, [_vp, _ip, _pp, _pp, _sz, _vp, _sz, _vp]),
+    "pmrc_encode_precode": (_i, [_vp, _pp, _pp, _sz, _vp, _sz, _vp]),
     "pmrc_default_helpers": (_i, [_vp, _i, _ip]),
     "pmrc_last_error": (ctypes.c_char_p, []),
     "pmrc_code_params": (_i, [_vp, _ip]),
@@ -227,6 +230,24 @@ def pmrc_repair_noalloc(code, failed, helpers, helper_blocks, out, block_bytes, 
 def pmrc_decode(code, nodes, node_blocks, data_out, block_bytes, stream=None):
     _check(lib().pmrc_decode(code, _ints(nodes), _ptrs(node_blocks), _ptrs(data_out),
                              block_bytes, _stream(stream)), "pmrc_decode")
+
+
+def pmrc_specific_workspace_bytes(code, block_bytes) -> int:
+    return int(lib().pmrc_specific_workspace_bytes(code, block_bytes))
+
+
+def pmrc_decode_specific(code, nodes, node_blocks, data_out, block_bytes, workspace,
+                         workspace_bytes, stream=None):
+    _check(lib().pmrc_decode_specific(code, _ints(nodes), _ptrs(node_blocks), _ptrs(data_out),
+                                      block_bytes, _addr(workspace), workspace_bytes,
+                                      _stream(stream)), "pmrc_decode_specific")
+
+
+def pmrc_encode_precode(code, data, parity, block_bytes, workspace, workspace_bytes,
+                        stream=None):
+    _check(lib().pmrc_encode_precode(code, _ptrs(data), _ptrs(parity), block_bytes,
+                                     _addr(workspace), workspace_bytes, _stream(stream)),
+           "pmrc_encode_precode")
 
 
 def pmrc_set_encode_kernel(code, which: int) -> None:
@@ -531,6 +552,26 @@ class Code:
 
     def decode(self, nodes, node_blocks, data_out, block_bytes, stream=None):
         pmrc_decode(self.handle, nodes, node_blocks, data_out, block_bytes, stream)
+
+    def specific_workspace_bytes(self, block_bytes) -> int:
+        return pmrc_specific_workspace_bytes(self.handle, block_bytes)
+
+    def decode_specific(self, nodes, node_blocks, data_out, block_bytes, workspace,
+                        workspace_bytes=None, stream=None):
+        """Data-collector reconstruction; `workspace` is a device tensor or
+        address of at least specific_workspace_bytes(block_bytes) bytes."""
+        if workspace_bytes is None:
+            workspace_bytes = int(workspace.numel() * workspace.element_size())
+        pmrc_decode_specific(self.handle, nodes, node_blocks, data_out, block_bytes, workspace,
+                             workspace_bytes, stream)
+
+    def encode_precode(self, data, parity, block_bytes, workspace, workspace_bytes=None,
+                       stream=None):
+        """Systematic encode by decoding then encoding (same parity as encode)."""
+        if workspace_bytes is None:
+            workspace_bytes = int(workspace.numel() * workspace.element_size())
+        pmrc_encode_precode(self.handle, data, parity, block_bytes, workspace, workspace_bytes,
+                            stream)
 
     def set_encode_kernel(self, which: int):
         pmrc_set_encode_kernel(self.handle, which)

@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "libpmrc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["region.cu", "bitslice.cu", "repair.cu", "batch.cu", "serve.cu", "plan.cpp",
-           "code.cpp", "api.cpp"]
+           "code.cpp", "specific.cpp", "api.cpp"]
 
 
 def nvcc() -> str:

@@ -390,4 +390,125 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
+size_t pmrc_specific_workspace_bytes(const pmrc_code *c, size_t block_bytes) {
+  if (!c) return 0;
+  return specific_workspace_blocks(c->m) * specific_pitch(block_bytes);
+}
+
+}  // extern "C"
+
+namespace {
+
+int specific_plan(const pmrc_code *c, const int *nodes, bool precode, const std::vector<char> &want,
+                  std::shared_ptr<SpecificPlan> &out, std::string &err) {
+  std::string key = precode ? "P:" : "D:";
+  for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
+  key += ":";
+  for (char w : want) key += w ? '1' : '0';
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->specific.find(key);
+    if (it != c->specific.end()) {
+      out = it->second;
+      return kOk;
+    }
+  }
+  auto sp = std::make_shared<SpecificPlan>();
+  int rc = build_specific(c->m, nodes, precode, want, *sp, err);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (c->specific.size() >= kPlanCacheCap) c->specific.erase(c->specific.begin());
+  c->specific[key] = sp;
+  out = sp;
+  return kOk;
+}
+
+// The stage launches, in stream order, over the workspace (see specific.h).
+int run_specific(const pmrc_code *c, SpecificPlan &sp, const uint8_t *const *in_blocks,
+                 uint8_t *const *final_out, size_t nbytes, uint8_t *ws, cudaStream_t s,
+                 std::string &err) {
+  const size_t pitch = specific_pitch(nbytes);
+  auto blocks = [&](uint8_t *base, int count) {
+    std::vector<uint8_t *> v(count);
+    for (int i = 0; i < count; i++) v[i] = base + (size_t)i * pitch;
+    return v;
+  };
+  std::vector<uint8_t *> w0 = blocks(ws, sp.w0);
+  std::vector<uint8_t *> w1 = blocks(ws + (size_t)sp.w0 * pitch, sp.w1);
+  std::vector<uint8_t *> w2 = blocks(ws + (size_t)(sp.w0 + sp.w1) * pitch, sp.w2);
+  auto cin = [](const std::vector<uint8_t *> &v) {
+    return std::vector<const uint8_t *>(v.begin(), v.end());
+  };
+  int rc = launch_region(*sp.A, in_blocks, w0.data(), nbytes, s, err);
+  if (!rc) rc = launch_region(*sp.PQ, cin(w0).data(), w1.data(), nbytes, s, err);
+  if (!rc) rc = launch_region(*sp.UV, cin(w1).data(), w0.data(), nbytes, s, err);
+  if (!rc) rc = launch_region(*sp.S, cin(w0).data(), sp.X || c->m.systematic ? w2.data() : final_out,
+                              nbytes, s, err);
+  if (!rc && sp.X) rc = launch_region(*sp.X, cin(w2).data(), final_out, nbytes, s, err);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmrc_decode_specific(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                         uint8_t *const *data_out, size_t nbytes, void *workspace,
+                         size_t workspace_bytes, pmrc_stream_t stream) {
+  if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
+  {
+    std::vector<char> seen(c->m.n, 0);
+    for (int i = 0; i < c->m.k; i++) {
+      if (nodes[i] < 0 || nodes[i] >= c->m.n || seen[nodes[i]])
+        return fail(PMRC_EINVAL, "nodes: out of range or repeated node id");
+      seen[nodes[i]] = 1;
+    }
+  }
+  if (nbytes == 0) return PMRC_OK;
+  if (!workspace || workspace_bytes < pmrc_specific_workspace_bytes(c, nbytes))
+    return fail(PMRC_EINVAL, "workspace is NULL or smaller than pmrc_specific_workspace_bytes");
+  std::vector<char> want;
+  decode_wanted(c, nodes, node_blocks, data_out, want);
+  std::shared_ptr<SpecificPlan> sp;
+  std::string err;
+  int rc = specific_plan(c, nodes, false, want, sp, err);
+  if (rc) return fail(rc, err);
+  const cudaStream_t s = (cudaStream_t)stream;
+  rc = run_specific(c, *sp, node_blocks, data_out, nbytes, (uint8_t *)workspace, s, err);
+  if (rc) return fail(rc, err);
+  const int a = c->m.alpha;
+  for (int r : sp->copy_rows) {  // data rows held by a listed node, not aliased
+    int pos = 0;
+    while (nodes[pos] != r / a) pos++;
+    const cudaError_t e = cudaMemcpyAsync(data_out[r], node_blocks[a * pos + r % a], nbytes,
+                                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(PMRC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+  }
+  return PMRC_OK;
+}
+
+int pmrc_encode_precode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *parity,
+                        size_t nbytes, void *workspace, size_t workspace_bytes,
+                        pmrc_stream_t stream) {
+  if (!c || !data || !parity) return fail(PMRC_EINVAL, "NULL argument");
+  if (!c->m.systematic)
+    return fail(PMRC_EINVAL, "precode encode produces a systematic code's parity");
+  const int K = c->m.k * c->m.alpha, NP = (c->m.n - c->m.k) * c->m.alpha;
+  for (int i = 0; i < K; i++)
+    if (!data[i]) return fail(PMRC_EINVAL, "data block is NULL");
+  for (int j = 0; j < NP; j++)
+    if (!parity[j]) return fail(PMRC_EINVAL, "parity block is NULL");
+  if (nbytes == 0) return PMRC_OK;
+  if (!workspace || workspace_bytes < pmrc_specific_workspace_bytes(c, nbytes))
+    return fail(PMRC_EINVAL, "workspace is NULL or smaller than pmrc_specific_workspace_bytes");
+  std::vector<int> nodes(c->m.k);
+  for (int i = 0; i < c->m.k; i++) nodes[i] = i;
+  std::shared_ptr<SpecificPlan> sp;
+  std::string err;
+  int rc = specific_plan(c, nodes.data(), true, std::vector<char>(K, 1), sp, err);
+  if (rc) return fail(rc, err);
+  rc = run_specific(c, *sp, data, parity, nbytes, (uint8_t *)workspace, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
 }  // extern "C"

@@ -11,6 +11,7 @@
 #include "code.h"
 #include "plan.h"
 #include "repair.h"
+#include "specific.h"
 
 struct pmrc_code {
   pmrc::CodeMatrices m;
@@ -20,6 +21,7 @@ struct pmrc_code {
   mutable std::mutex mu;               // guards cache
   mutable std::map<std::string, std::shared_ptr<pmrc::Plan>> cache;
   mutable std::map<std::string, std::shared_ptr<pmrc::FusedRepairPlan>> fused;
+  mutable std::map<std::string, std::shared_ptr<pmrc::SpecificPlan>> specific;
 };
 
 namespace pmrc {
