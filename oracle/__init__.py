@@ -27,6 +27,12 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                              subsets at n = 16 recover the data exactly
   encode_precode             pinned: data as nodes 0..k-1 re-decodes to itself
                              and every k-subset of the result recovers the data
+  mbr_*                      pinned: k Delta = k(2d-k+1)/2 and alpha = d
+                             (Sec. 2); G X equals Psi M(X); systematic nodes
+                             hold the symbols verbatim; any d rows of Psi and
+                             any k rows of Phi independent; repair of every
+                             node from every helper set and decode from every
+                             k-subset are exact (small n)
 """
 from __future__ import annotations
 
@@ -103,6 +109,15 @@ def lib():
                 "or_dc_decode": (i, [i, i, i, ip, u8p, u8p, sz]),
                 "or_decode_specific": (i, [i, i, i, i, ip, u8p, u8p, sz]),
                 "or_encode_precode": (i, [i, i, i, u8p, u8p, sz]),
+                "or_mbr_params": (i, [i, i, i, ip, ip]),
+                "or_mbr_psi": (i, [i, i, i, u8p]),
+                "or_mbr_index_matrix": (i, [i, i, ip]),
+                "or_mbr_generator": (i, [i, i, i, u8p]),
+                "or_mbr_encode": (i, [i, i, i, u8p, u8p, sz]),
+                "or_mbr_helper_coefficients": (i, [i, i, i, i, u8p]),
+                "or_mbr_newcomer_matrix": (i, [i, i, i, i, ip, u8p]),
+                "or_mbr_decode_matrix": (i, [i, i, i, ip, u8p]),
+                "or_mbr_decode": (i, [i, i, i, ip, u8p, u8p, sz]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -323,4 +338,80 @@ def encode_precode(n: int, k: int, construction: int, data: np.ndarray) -> np.nd
     B = data.shape[1]
     out = np.zeros(((n - k) * a, B), np.uint8)
     _check(lib().or_encode_precode(n, k, construction, _u8(data), _u8(out), B), "encode_precode")
+    return out
+
+
+# ------------------------------------------------------------------ PM-MBR
+def mbr_params(n: int, k: int, d: int):
+    a = ctypes.c_int()
+    B = ctypes.c_int()
+    _check(lib().or_mbr_params(n, k, d, ctypes.byref(a), ctypes.byref(B)), "mbr_params")
+    return a.value, B.value
+
+
+def mbr_psi(n: int, k: int, d: int) -> np.ndarray:
+    P = np.zeros((n, d), np.uint8)
+    _check(lib().or_mbr_psi(n, k, d, _u8(P)), "mbr_psi")
+    return P
+
+
+def mbr_index_matrix(k: int, d: int) -> np.ndarray:
+    L = np.zeros((d, d), np.int32)
+    _check(lib().or_mbr_index_matrix(k, d, _ip(L)), "mbr_index_matrix")
+    return L
+
+
+def mbr_generator(n: int, k: int, d: int) -> np.ndarray:
+    a, B = mbr_params(n, k, d)
+    G = np.zeros((n * a, B), np.uint8)
+    _check(lib().or_mbr_generator(n, k, d, _u8(G)), "mbr_generator")
+    return G
+
+
+def mbr_encode(n: int, k: int, d: int, data: np.ndarray) -> np.ndarray:
+    a, B = mbr_params(n, k, d)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    assert data.shape[0] == B
+    out = np.zeros((n * a, data.shape[1]), np.uint8)
+    _check(lib().or_mbr_encode(n, k, d, _u8(data), _u8(out), data.shape[1]), "mbr_encode")
+    return out
+
+
+def mbr_helper_coefficients(n: int, k: int, d: int, f: int) -> np.ndarray:
+    c = np.zeros(d, np.uint8)
+    _check(lib().or_mbr_helper_coefficients(n, k, d, f, _u8(c)), "mbr_helper_coefficients")
+    return c
+
+
+def mbr_repair_helper(n: int, k: int, d: int, f: int, blocks: np.ndarray) -> np.ndarray:
+    return region_apply(mbr_helper_coefficients(n, k, d, f)[None, :], blocks)[0]
+
+
+def mbr_newcomer_matrix(n: int, k: int, d: int, f: int, helpers) -> np.ndarray:
+    h = _ints(helpers)
+    D = np.zeros((d, d), np.uint8)
+    _check(lib().or_mbr_newcomer_matrix(n, k, d, f, _ip(h), _u8(D)), "mbr_newcomer_matrix")
+    return D
+
+
+def mbr_repair_newcomer(n: int, k: int, d: int, f: int, helpers, recv: np.ndarray) -> np.ndarray:
+    return region_apply(mbr_newcomer_matrix(n, k, d, f, helpers), recv)
+
+
+def mbr_decode_matrix(n: int, k: int, d: int, nodes) -> np.ndarray:
+    a, B = mbr_params(n, k, d)
+    s = _ints(nodes)
+    R = np.zeros((B, k * a), np.uint8)
+    _check(lib().or_mbr_decode_matrix(n, k, d, _ip(s), _u8(R)), "mbr_decode_matrix")
+    return R
+
+
+def mbr_decode(n: int, k: int, d: int, nodes, node_blocks: np.ndarray) -> np.ndarray:
+    a, B = mbr_params(n, k, d)
+    s = _ints(nodes)
+    node_blocks = np.ascontiguousarray(node_blocks, dtype=np.uint8)
+    assert node_blocks.shape[0] == k * a
+    out = np.zeros((B, node_blocks.shape[1]), np.uint8)
+    _check(lib().or_mbr_decode(n, k, d, _ip(s), _u8(node_blocks), _u8(out),
+                               node_blocks.shape[1]), "mbr_decode")
     return out

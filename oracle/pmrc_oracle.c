@@ -704,3 +704,242 @@ int or_encode_precode(int n, int k, int construction, const uint8_t *data, uint8
     free(G);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Product-matrix MBR codes (Sec. 2: alpha = d, Delta = (2d-k+1)/2; Sec. 3.2: */
+/* a systematic encoding matrix Psi = [I; Psi''] given directly; Sec. 4.3    */
+/* evaluates encode, repair and decode).  The message matrix of the seminal  */
+/* PM paper, restated:                                                       */
+/*     M = [ S    T ]    (d x d, symmetric)                                  */
+/*         [ T^t  0 ]                                                        */
+/* with S a symmetric k x k matrix and T a k x (d-k) matrix of message      */
+/* symbols, k(k+1)/2 + k(d-k) = k Delta in all.  Node i stores psi_i^t M     */
+/* (alpha = d blocks).  Psi must have every d rows independent and every k   */
+/* rows of its first k columns (Phi) independent.                            */
+/* ------------------------------------------------------------------------ */
+
+/* alpha = d, B = k Delta = k(2d-k+1)/2 message blocks; k <= d <= n-1. */
+int or_mbr_params(int n, int k, int d, int *alpha, int *B)
+{
+    if (k < 1 || d < k || d > n - 1 || n > 128)
+        return OR_EINVAL;
+    *alpha = d;
+    *B = k * (2 * d - k + 1) / 2;
+    return OR_OK;
+}
+
+/* Psi (n x d) = [I_k 0; C]: the first k rows are the unit rows e_i (the
+ * systematic nodes store message symbols verbatim), and the other n-k rows
+ * are the Cauchy matrix C_{i,j} = (g^{d+i} - g^j)^-1 (0-based i < n-k,
+ * j < d), every square sub-matrix of which is invertible.  Then any d rows
+ * of Psi, and any k rows of its first k columns, are independent. */
+int or_mbr_psi(int n, int k, int d, uint8_t *psi)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B))
+        return OR_EINVAL;
+    if (d + n - k > 255)
+        return OR_EINVAL;
+    memset(psi, 0, (size_t)n * d);
+    for (int i = 0; i < k; i++)
+        psi[(size_t)i * d + i] = 1;
+    for (int i = 0; i < n - k; i++)
+        for (int j = 0; j < d; j++)
+            psi[(size_t)(k + i) * d + j] = or_gf_inv(or_add(or_gf_pow_g(d + i), or_gf_pow_g(j)));
+    return OR_OK;
+}
+
+/* L (d x d): M_{l,j} = X_{L[l][j]}, or -1 where M is zero.  The upper
+ * triangle of S is numbered row by row (0 .. k(k+1)/2 - 1), then T row by
+ * row; the rest follows from the symmetry of M. */
+int or_mbr_index_matrix(int k, int d, int *L)
+{
+    if (k < 1 || d < k)
+        return OR_EINVAL;
+    for (int i = 0; i < d * d; i++)
+        L[i] = -1;
+    int s = 0;
+    for (int i = 0; i < k; i++)
+        for (int j = i; j < k; j++, s++) {
+            L[i * d + j] = s;
+            L[j * d + i] = s;
+        }
+    for (int i = 0; i < k; i++)
+        for (int m = 0; m < d - k; m++, s++) {
+            L[i * d + k + m] = s;
+            L[(k + m) * d + i] = s;
+        }
+    return OR_OK;
+}
+
+/* G (n*alpha x B): G[alpha i + j][L[l][j]] = Psi[i][l] (Sec. 3.1 applied to
+ * the MBR message matrix; zero entries of M contribute nothing). */
+int or_mbr_generator(int n, int k, int d, uint8_t *G)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B))
+        return OR_EINVAL;
+    uint8_t *psi = (uint8_t *)malloc((size_t)n * d);
+    int *L = (int *)malloc(sizeof(int) * d * d);
+    int rc = or_mbr_psi(n, k, d, psi);
+    if (rc == OR_OK) {
+        or_mbr_index_matrix(k, d, L);
+        memset(G, 0, (size_t)n * a * B);
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < a; j++)
+                for (int l = 0; l < d; l++)
+                    if (L[l * d + j] >= 0)
+                        G[(size_t)(a * i + j) * B + L[l * d + j]] = psi[i * d + l];
+    }
+    free(psi);
+    free(L);
+    return rc;
+}
+
+/* All n*alpha coded blocks (node-major). */
+int or_mbr_encode(int n, int k, int d, const uint8_t *data, uint8_t *out, size_t nbytes)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B))
+        return OR_EINVAL;
+    uint8_t *G = (uint8_t *)malloc((size_t)n * a * B);
+    int rc = or_mbr_generator(n, k, d, G);
+    if (rc == OR_OK)
+        or_region_apply(n * a, B, G, data, nbytes, out, nbytes, nbytes);
+    free(G);
+    return rc;
+}
+
+/* Repair of node f: helper h sends psi_h^t M psi_f, i.e. its alpha blocks
+ * projected on psi_f. */
+int or_mbr_helper_coefficients(int n, int k, int d, int f, uint8_t *coef)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B) || f < 0 || f >= n)
+        return OR_EINVAL;
+    uint8_t *psi = (uint8_t *)malloc((size_t)n * d);
+    int rc = or_mbr_psi(n, k, d, psi);
+    if (rc == OR_OK)
+        memcpy(coef, psi + (size_t)f * d, (size_t)d);
+    free(psi);
+    return rc;
+}
+
+/* The received vector is p = Psi_H M psi_f; Psi_H is invertible, so
+ * M psi_f = Psi_H^-1 p, and by symmetry of M the lost node psi_f^t M is its
+ * transpose: D = Psi_H^-1 (d x d). */
+int or_mbr_newcomer_matrix(int n, int k, int d, int f, const int *helpers, uint8_t *D)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B) || f < 0 || f >= n)
+        return OR_EINVAL;
+    for (int i = 0; i < d; i++) {
+        if (helpers[i] < 0 || helpers[i] >= n || helpers[i] == f)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (helpers[j] == helpers[i])
+                return OR_EINVAL;
+    }
+    uint8_t *psi = (uint8_t *)malloc((size_t)n * d);
+    uint8_t *PH = (uint8_t *)malloc((size_t)d * d);
+    int rc = or_mbr_psi(n, k, d, psi);
+    if (rc == OR_OK) {
+        for (int i = 0; i < d; i++)
+            memcpy(PH + (size_t)i * d, psi + (size_t)helpers[i] * d, (size_t)d);
+        rc = or_invert(d, PH, D);
+    }
+    free(psi);
+    free(PH);
+    return rc;
+}
+
+/* Reconstruction from k nodes (Sec. 2, X = G~^-1 Y~ with G~ made square):
+ * the k*alpha rows of G of the listed nodes have rank B; the first B of them
+ * (node-major) that are independent of the rows before them form G~, and
+ * R (B x k*alpha) applies G~^-1 to those rows and ignores the others. */
+int or_mbr_decode_matrix(int n, int k, int d, const int *nodes, uint8_t *R)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B))
+        return OR_EINVAL;
+    for (int i = 0; i < k; i++) {
+        if (nodes[i] < 0 || nodes[i] >= n)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (nodes[j] == nodes[i])
+                return OR_EINVAL;
+    }
+    int KA = k * a, N = n * a;
+    uint8_t *G = (uint8_t *)malloc((size_t)N * B);
+    uint8_t *E = (uint8_t *)malloc((size_t)B * B);   /* echelon copy of picked rows */
+    uint8_t *Gt = (uint8_t *)malloc((size_t)B * B);  /* picked rows, unreduced */
+    uint8_t *Gti = (uint8_t *)malloc((size_t)B * B);
+    uint8_t *v = (uint8_t *)malloc((size_t)B);
+    int *pick = (int *)malloc(sizeof(int) * B);
+    int *pivcol = (int *)malloc(sizeof(int) * B);
+    int rc = or_mbr_generator(n, k, d, G), got = 0;
+    for (int r = 0; r < KA && got < B && rc == OR_OK; r++) {
+        const uint8_t *row = G + (size_t)(a * nodes[r / a] + r % a) * B;
+        memcpy(v, row, (size_t)B);
+        /* reduce v by the echelon rows found so far */
+        for (int e = 0; e < got; e++) {
+            uint8_t f = v[pivcol[e]];
+            if (f)
+                for (int c = 0; c < B; c++)
+                    v[c] = or_add(v[c], or_gf_mul(f, E[(size_t)e * B + c]));
+        }
+        int pc = -1;
+        for (int c = 0; c < B && pc < 0; c++)
+            if (v[c])
+                pc = c;
+        if (pc < 0)
+            continue; /* dependent on the rows already picked */
+        uint8_t inv = or_gf_inv(v[pc]);
+        for (int c = 0; c < B; c++)
+            v[c] = or_gf_mul(v[c], inv);
+        /* keep the echelon rows reduced at the new pivot column */
+        for (int e = 0; e < got; e++) {
+            uint8_t f = E[(size_t)e * B + pc];
+            if (f)
+                for (int c = 0; c < B; c++)
+                    E[(size_t)e * B + c] = or_add(E[(size_t)e * B + c], or_gf_mul(f, v[c]));
+        }
+        memcpy(E + (size_t)got * B, v, (size_t)B);
+        memcpy(Gt + (size_t)got * B, row, (size_t)B);
+        pivcol[got] = pc;
+        pick[got] = r;
+        got++;
+    }
+    if (rc == OR_OK && got < B)
+        rc = OR_ESINGULAR;
+    if (rc == OR_OK)
+        rc = or_invert(B, Gt, Gti);
+    if (rc == OR_OK) {
+        memset(R, 0, (size_t)B * KA);
+        for (int x = 0; x < B; x++)
+            for (int t = 0; t < B; t++)
+                R[(size_t)x * KA + pick[t]] = Gti[(size_t)x * B + t];
+    }
+    free(G);
+    free(E);
+    free(Gt);
+    free(Gti);
+    free(v);
+    free(pick);
+    free(pivcol);
+    return rc;
+}
+
+int or_mbr_decode(int n, int k, int d, const int *nodes, const uint8_t *node_blocks,
+                  uint8_t *data, size_t nbytes)
+{
+    int a, B;
+    if (or_mbr_params(n, k, d, &a, &B))
+        return OR_EINVAL;
+    uint8_t *R = (uint8_t *)malloc((size_t)B * k * a);
+    int rc = or_mbr_decode_matrix(n, k, d, nodes, R);
+    if (rc == OR_OK)
+        or_region_apply(B, k * a, R, node_blocks, nbytes, data, nbytes, nbytes);
+    free(R);
+    return rc;
+}
