@@ -24,6 +24,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -83,6 +85,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch-stripes", type=int, default=4096)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-mbr", action="store_true")
     p.add_argument("--serve-requests", type=int, default=400,
                    help="requests per offered-load level")
     return p.parse_args()
@@ -335,6 +338,8 @@ def run_ours(args, rank, world, local_rank):
                         "linear_op": linear, "linear_over_specific": round(op_ms[linear] / ms, 3),
                         "launches": 5 if name == "encode_precode" else 4 + (W.decode_missing > 0)}
     del ws
+    if not args.no_mbr:
+        per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
@@ -366,6 +371,63 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def run_mbr(torch, P, inputs, args, flush, stream, dev, hbm):
+    """PM-MBR rows (n=16, k=8, d=14: alpha=14, K=84 data blocks of the
+    stripe's block size): systematic encode (112 parity blocks), fused repair
+    of a seeded node, lazy reconstruction from a seeded 8-node set."""
+    n, k, d, B = 16, 8, 14, args.block_bytes
+    c = P.Code(n, k, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=d)
+    a, K = c.alpha, c.data_blocks
+    st = int(torch.cuda.current_stream(dev).cuda_stream)
+    X = inputs.device_blocks(K, B, args.seed + 77, device=dev)
+    Y = torch.empty((n * a, B), dtype=torch.uint8, device=dev)
+    cn = P.Code(n, k, P.PMRC_MBR, P.PMRC_NONSYSTEMATIC, d=d)
+    cn.encode(P.ptr_array([X[i] for i in range(K)]), P.ptr_array([Y[r] for r in range(n * a)]), B)
+    f = inputs.failed_node(n, args.seed + 77)
+    H = c.default_helpers(f)
+    S = inputs.node_subset(n, k, args.seed + 77)
+    coef = P.pmrc_helper_coefficients(c.handle, f)
+    reads = int((coef != 0).sum())
+    node = torch.empty((a, B), dtype=torch.uint8, device=dev)
+    Xr = torch.empty((K, B), dtype=torch.uint8, device=dev)
+    dec_in = [Y[a * i + j] for i in S for j in range(a)]
+    dec_out = [Xr[r] for r in range(K)]
+    G = P.pmrc_code_generator(c.handle)
+    for pos, i in enumerate(S):          # data blocks held verbatim stay in place
+        for j in range(a):
+            col = np.flatnonzero(G[a * i + j])
+            if len(col) == 1 and G[a * i + j, col[0]] == 1:
+                dec_out[int(col[0])] = dec_in[a * pos + j]
+    missing = sum(1 for r in range(K) if dec_out[r] is not None and
+                  dec_out[r].data_ptr() == Xr[r].data_ptr())
+    R = P.pmrc_decode_matrix(c.handle, S)
+    dec_reads = int((R[[r for r in range(K) if dec_out[r].data_ptr() == Xr[r].data_ptr()]]
+                     != 0).any(axis=0).sum()) if missing else 0
+    x_arr = P.ptr_array([X[i] for i in range(K)])
+    par_arr = P.ptr_array([Y[k * a + r] for r in range(n * a - k * a)])
+    H_arr = P.int_array(H)
+    h_in = P.ptr_array([Y[a * h + j] for h in H for j in range(a)])
+    node_arr = P.ptr_array([node[j] for j in range(a)])
+    S_arr = P.int_array(S)
+    din, dout = P.ptr_array(dec_in), P.ptr_array(dec_out)
+    ops = {
+        "mbr_encode": (lambda: c.encode(x_arr, par_arr, B, st), K * B, (K + n * a - k * a) * B),
+        "mbr_repair": (lambda: c.repair(f, H_arr, h_in, node_arr, B, st), a * B,
+                       (d * reads + a) * B),
+        "mbr_decode": (lambda: c.decode(S_arr, din, dout, B, st), K * B,
+                       (dec_reads + missing) * B),
+    }
+    out = {}
+    for name, (fn, user, alg) in ops.items():
+        ms = time_op(torch, stream, flush, args, fn)
+        out[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
+                     "alg_bytes": alg, "frac_hbm": round(alg / (ms * 1e-3) / 1e9 / hbm, 4)}
+    out["mbr_repair"].update({"failed_node": f, "helper_reads": reads})
+    out["mbr_decode"].update({"nodes": S, "missing_rows": missing})
+    torch.cuda.synchronize()
+    return out
 
 
 def time_op(torch, stream, flush, args, fn):

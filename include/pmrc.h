@@ -1,6 +1,7 @@
 /*
- * pmrc.h -- C ABI of libpmrc: product-matrix minimum-storage regenerating
- * (PM-MSR) codes over GF(2^8) on one NVIDIA GB300 GPU (sm_103a).
+ * pmrc.h -- C ABI of libpmrc: product-matrix regenerating codes over GF(2^8)
+ * on one NVIDIA GB300 GPU (sm_103a): minimum-storage (PM-MSR) codes and,
+ * with construction PMRC_MBR, minimum-bandwidth (PM-MBR) codes.
  *
  * Follows N. Le Scouarnec, "Fast Product-Matrix Regenerating Codes":
  *   Sec. 2    the code as a linear map: k*alpha data blocks X, n*alpha coded
@@ -13,7 +14,9 @@
  *             sparse (identity + Cauchy) constructions; helpers of a failed
  *             node among the alpha first read one block, alpha otherwise.
  *
- * Parameters: d = 2k-2, alpha = k-1, 2k-1 <= n <= 254, field GF(2^8) with
+ * PM-MSR parameters: d = 2k-2, alpha = k-1, 2k-1 <= n <= 254 (PM-MBR: see
+ * pmrc_create; there "k*alpha data blocks" below reads "K = k Delta data
+ * blocks", and node blocks are still alpha per node).  Field GF(2^8) with
  * modulus x^8+x^4+x^3+x^2+1 (0x11D) and generator g = 2.  Node i stores the
  * alpha blocks Y[alpha*i .. alpha*i + alpha-1] ("node-major").  The message
  * matrix M = [S1; S2] numbers the upper triangle of S1 row by row, then that
@@ -60,26 +63,42 @@ enum {
   PMRC_EBUSY = -7        /* resource in use (batch/server state)              */
 };
 
-enum { PMRC_VANILLA = 0, PMRC_SPARSE = 1 };            /* Sec. 3.3            */
+enum { PMRC_VANILLA = 0, PMRC_SPARSE = 1 };            /* Sec. 3.3 (PM-MSR)   */
+enum { PMRC_MBR = 2 };                                 /* Sec. 2, 3.2, 4.3    */
 enum { PMRC_NONSYSTEMATIC = 0, PMRC_SYSTEMATIC = 1 };  /* Sec. 3.1 / Sec. 3.2 */
 
 /* Builds the code (Phi, Lambda, Psi, L, G and, for the systematic form,
  * G' = G G~^-1) on the host and its encode plan.  Host only: works without a
- * GPU.  d must equal 2k-2 (PMRC_EINVAL otherwise).  Returns
- * PMRC_EUNSUPPORTED when the construction is not an MSR code in GF(2^8) at
- * this size (e.g. vanilla with repeated lambda, k=16 n=32).  *out receives
- * a handle owned by the caller (free with pmrc_destroy). */
+ * GPU.  *out receives a handle owned by the caller (free with pmrc_destroy).
+ *
+ * PMRC_VANILLA / PMRC_SPARSE: PM-MSR codes (Sec. 3.3), alpha = k-1; d must
+ * equal 2k-2 (PMRC_EINVAL otherwise).  Returns PMRC_EUNSUPPORTED when the
+ * construction is not an MSR code in GF(2^8) at this size (e.g. vanilla
+ * with repeated lambda, k=16 n=32).  Data: K = k alpha blocks.
+ *
+ * PMRC_MBR: the PM-MBR code (Sec. 2: alpha = d, Delta = (2d-k+1)/2), any
+ * 1 <= k <= d <= n-1 with d + n - k <= 255.  Message matrix M = [S T; T^t 0]
+ * (S symmetric k x k, T k x (d-k); upper triangle of S then T, row by row,
+ * are the data blocks 0..K-1, K = k Delta).  Psi = [I_k 0; C] (the
+ * systematic Psi = [I; Psi''] of Sec. 3.2) with C_ij = (g^(d+i) + g^j)^-1,
+ * 0-based i < n-k, j < d; node i < k stores row i of M, i.e. data blocks
+ * verbatim.  The form only selects what pmrc_encode writes (every node, or
+ * the n-k parity nodes).  Repair: helper h sends its d blocks projected on
+ * psi_f (pmrc_helper_coefficients), the newcomer applies Psi_H^-1 (any d
+ * helpers work).  Decode reads k nodes (k d blocks) and writes the K data
+ * blocks.  The specific calls below are PM-MSR only. */
 int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out);
 
 /* Frees the handle and its device plans.  The caller makes sure no call on
  * it is still running on the GPU.  NULL is ignored. */
 void pmrc_destroy(pmrc_code *code);
 
-/* Encode (Sec. 3.1 / 3.2).  data: k*alpha device pointers (X).  out:
+/* Encode (Sec. 3.1 / 3.2).  data: K device pointers (X; K = k*alpha for
+ * PM-MSR, pmrc_code_blocks).  out:
  * non-systematic -> n*alpha pointers, all coded blocks Y = G X;
- * systematic     -> (n-k)*alpha pointers, the parity blocks G'' X (the first
- * k*alpha blocks of Y are the data itself).  NULL entries of out are
- * skipped. */
+ * systematic     -> (n-k)*alpha pointers, the parity nodes' blocks (G'' X
+ * for PM-MSR; the first k nodes hold the data itself).  NULL entries of out
+ * are skipped. */
 int pmrc_encode(const pmrc_code *code, const uint8_t *const *data, uint8_t *const *out,
                 size_t block_bytes, pmrc_stream_t stream);
 
@@ -332,8 +351,12 @@ const char *pmrc_last_error(void);
 /* params_out[6] = {n, k, d, alpha, construction, form}. */
 int pmrc_code_params(const pmrc_code *code, int *params_out);
 
-/* The code's generator, n*alpha x k*alpha, row-major: G (non-systematic) or
- * G' (systematic). */
+/* Data blocks K (k alpha for PM-MSR, k Delta for PM-MBR) and coded blocks
+ * n alpha: the pointer counts of encode (K in) and decode (K out). */
+int pmrc_code_blocks(const pmrc_code *code, int *data_blocks, int *coded_blocks);
+
+/* The code's generator, n*alpha x K, row-major: G (non-systematic) or
+ * G' (systematic); for PM-MBR always G (already systematic). */
 int pmrc_code_generator(const pmrc_code *code, uint8_t *g_out);
 
 /* phi_failed (alpha bytes): the helper coefficients of pmrc_repair_helper. */
@@ -342,7 +365,9 @@ int pmrc_helper_coefficients(const pmrc_code *code, int failed, uint8_t *coef_ou
 /* D (alpha x d, row-major) applied by pmrc_repair_newcomer. */
 int pmrc_newcomer_matrix(const pmrc_code *code, int failed, const int *helpers, uint8_t *d_out);
 
-/* (k*alpha x k*alpha, row-major) inverse applied by pmrc_decode. */
+/* (K x k*alpha, row-major) matrix applied by pmrc_decode: the inverse of
+ * the nodes' rows (PM-MSR; K = k*alpha), or of K independent ones of them
+ * with zero columns for the others (PM-MBR). */
 int pmrc_decode_matrix(const pmrc_code *code, const int *nodes, uint8_t *r_out);
 
 /* How the region kernel would cut the rows x cols matrix m (row-major, host)

@@ -39,6 +39,7 @@ PMRC_OP_DECODE = 2
 
 PMRC_VANILLA = 0
 PMRC_SPARSE = 1
+PMRC_MBR = 2
 PMRC_NONSYSTEMATIC = 0
 PMRC_SYSTEMATIC = 1
 
@@ -81,6 +82,7 @@ _SIGNATURES = {
     "pmrc_default_helpers": (_i, [_vp, _i, _ip]),
     "pmrc_last_error": (ctypes.c_char_p, []),
     "pmrc_code_params": (_i, [_vp, _ip]),
+    "pmrc_code_blocks": (_i, [_vp, _ip, _ip]),
     "pmrc_code_generator": (_i, [_vp, _u8p]),
     "pmrc_helper_coefficients": (_i, [_vp, _i, _u8p]),
     "pmrc_newcomer_matrix": (_i, [_vp, _i, _ip, _u8p]),
@@ -271,6 +273,13 @@ def pmrc_code_params(code) -> dict:
     return dict(zip(("n", "k", "d", "alpha", "construction", "form"), list(out)))
 
 
+def pmrc_code_blocks(code):
+    """(K data blocks, n*alpha coded blocks)."""
+    K, N = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pmrc_code_blocks(code, ctypes.byref(K), ctypes.byref(N)), "pmrc_code_blocks")
+    return K.value, N.value
+
+
 def _u8buf(size):
     return (ctypes.c_uint8 * size)()
 
@@ -281,8 +290,7 @@ def _mat(buf, rows, cols):
 
 
 def pmrc_code_generator(code):
-    p = pmrc_code_params(code)
-    N, K = p["n"] * p["alpha"], p["k"] * p["alpha"]
+    K, N = pmrc_code_blocks(code)
     buf = _u8buf(N * K)
     _check(lib().pmrc_code_generator(code, buf), "pmrc_code_generator")
     return _mat(buf, N, K)
@@ -304,10 +312,11 @@ def pmrc_newcomer_matrix(code, failed, helpers):
 
 def pmrc_decode_matrix(code, nodes):
     p = pmrc_code_params(code)
-    K = p["k"] * p["alpha"]
-    buf = _u8buf(K * K)
+    K, _ = pmrc_code_blocks(code)
+    KA = p["k"] * p["alpha"]
+    buf = _u8buf(K * KA)
     _check(lib().pmrc_decode_matrix(code, _ints(nodes), buf), "pmrc_decode_matrix")
-    return _mat(buf, K, K)
+    return _mat(buf, K, KA)
 
 
 def pmrc_plan_stats(m) -> dict:
@@ -513,11 +522,14 @@ class Code:
     """Owns a pmrc_code handle; methods are the C calls on it."""
 
     def __init__(self, n: int, k: int, construction: int = PMRC_SPARSE,
-                 form: int = PMRC_SYSTEMATIC):
-        self.handle = pmrc_create(n, k, 2 * k - 2, construction, form)
+                 form: int = PMRC_SYSTEMATIC, d: int = None):
+        """PM-MSR (PMRC_VANILLA / PMRC_SPARSE): d = 2k-2.  PM-MBR (PMRC_MBR):
+        any k <= d <= n-1 (default 2k-2)."""
+        self.handle = pmrc_create(n, k, 2 * k - 2 if d is None else d, construction, form)
         p = pmrc_code_params(self.handle)
         self.n, self.k, self.d, self.alpha = p["n"], p["k"], p["d"], p["alpha"]
         self.construction, self.form = construction, form
+        self.data_blocks, self.coded_blocks = pmrc_code_blocks(self.handle)
 
     def close(self):
         if self.handle:

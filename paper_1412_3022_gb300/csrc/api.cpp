@@ -91,7 +91,7 @@ int newcomer_plan(const pmrc_code *c, int f, const int *helpers, std::shared_ptr
 
 int decode_plan(const pmrc_code *c, const int *nodes, const std::vector<char> &want,
                 std::shared_ptr<Plan> &out, std::string &err) {
-  const int K = c->m.k * c->m.alpha;
+  const int K = c->m.K;
   std::string key = "d:";
   for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
   key += ":";
@@ -141,19 +141,18 @@ int fused_repair_plan(const pmrc_code *c, int f, const int *helpers,
 }
 
 // Which data rows a decode call must produce: non-NULL outputs, except a
-// systematic data block whose output pointer is the node block holding it.
+// data block whose output pointer is a listed node block that holds it
+// verbatim (a unit row of the code's generator: systematic MSR, MBR).
 int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                   uint8_t *const *data_out, std::vector<char> &want) {
-  const int a = c->m.alpha, K = c->m.k * a;
+  const int a = c->m.alpha, K = c->m.K;
   want.assign(K, 0);
   for (int r = 0; r < K; r++) want[r] = data_out[r] != nullptr;
-  if (c->m.systematic)
-    for (int i = 0; i < c->m.k; i++)
-      if (nodes[i] < c->m.k)
-        for (int j = 0; j < a; j++) {
-          const int r = a * nodes[i] + j;  // data row held by this node block
-          if (data_out[r] == node_blocks[a * i + j]) want[r] = 0;
-        }
+  for (int i = 0; i < c->m.k; i++)
+    for (int j = 0; j < a; j++) {
+      const int s = c->m.unit_col[a * nodes[i] + j];  // data block this node block copies
+      if (s >= 0 && data_out[s] == node_blocks[a * i + j]) want[s] = 0;
+    }
   return kOk;
 }
 
@@ -171,11 +170,12 @@ int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out
   std::string err;
   int rc = build_code(n, k, d, construction, form, c->m, err);
   if (rc) return fail(rc, err);
-  const int a = c->m.alpha, K = k * a, N = n * a;
-  if (K + (form ? N - K : N) > kMaxSlots)
+  const int K = c->m.K, N = c->m.N;
+  // encode plan: all rows (non-systematic) or the parity nodes' rows
+  // (systematic: the first k nodes hold the data)
+  const int first = form ? k * c->m.alpha : 0;
+  if (K + N - first > kMaxSlots)
     return fail(PMRC_EUNSUPPORTED, "code too large: more than 1024 block pointers per encode");
-  // encode plan: all rows (non-systematic) or the parity rows (systematic)
-  const int first = form ? K : 0;
   Mat M(N - first, K);
   std::copy(c->m.Gcode.v.begin() + (size_t)first * K, c->m.Gcode.v.end(), M.v.begin());
   std::vector<int> slot(N - first);
@@ -197,6 +197,13 @@ int pmrc_code_params(const pmrc_code *c, int *p) {
   p[3] = c->m.alpha;
   p[4] = c->m.construction;
   p[5] = c->m.systematic;
+  return PMRC_OK;
+}
+
+int pmrc_code_blocks(const pmrc_code *c, int *data_blocks, int *coded_blocks) {
+  if (!c || !data_blocks || !coded_blocks) return fail(PMRC_EINVAL, "NULL argument");
+  *data_blocks = c->m.K;
+  *coded_blocks = c->m.N;
   return PMRC_OK;
 }
 
@@ -391,7 +398,7 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
 }
 
 size_t pmrc_specific_workspace_bytes(const pmrc_code *c, size_t block_bytes) {
-  if (!c) return 0;
+  if (!c || c->m.construction == kConsMbr) return 0;
   return specific_workspace_blocks(c->m) * specific_pitch(block_bytes);
 }
 
@@ -456,6 +463,8 @@ int pmrc_decode_specific(const pmrc_code *c, const int *nodes, const uint8_t *co
                          uint8_t *const *data_out, size_t nbytes, void *workspace,
                          size_t workspace_bytes, pmrc_stream_t stream) {
   if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
+  if (c->m.construction == kConsMbr)
+    return fail(PMRC_EUNSUPPORTED, "the data collector of this library is the PM-MSR one");
   {
     std::vector<char> seen(c->m.n, 0);
     for (int i = 0; i < c->m.k; i++) {
@@ -491,6 +500,8 @@ int pmrc_encode_precode(const pmrc_code *c, const uint8_t *const *data, uint8_t 
                         size_t nbytes, void *workspace, size_t workspace_bytes,
                         pmrc_stream_t stream) {
   if (!c || !data || !parity) return fail(PMRC_EINVAL, "NULL argument");
+  if (c->m.construction == kConsMbr)
+    return fail(PMRC_EUNSUPPORTED, "PM-MBR is systematic by construction: use pmrc_encode");
   if (!c->m.systematic)
     return fail(PMRC_EINVAL, "precode encode produces a systematic code's parity");
   const int K = c->m.k * c->m.alpha, NP = (c->m.n - c->m.k) * c->m.alpha;

@@ -137,7 +137,7 @@ int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const
   }
   for (int j = 0; j < s.plan->nout; j++) s.ptrs.push_back(out[j]);
   s.nbytes = nbytes;
-  s.user_bytes = (int64_t)c->m.k * c->m.alpha * nbytes;
+  s.user_bytes = (int64_t)c->m.K * nbytes;
   s.work = s.plan->nnz;
   finish_stripe(s);
   return kOk;
@@ -197,8 +197,8 @@ int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *no
   s.type = 0;
   int rc = decode_plan(c, nodes, want, s.plan, err);
   if (rc) return rc;
-  const int K = c->m.k * c->m.alpha;
-  for (int i = 0; i < K; i++) s.ptrs.push_back(const_cast<uint8_t *>(node_blocks[i]));
+  const int KA = c->m.k * c->m.alpha, K = c->m.K;  // node blocks read, data blocks out
+  for (int i = 0; i < KA; i++) s.ptrs.push_back(const_cast<uint8_t *>(node_blocks[i]));
   for (int r = 0; r < K; r++) s.ptrs.push_back(want[r] ? data_out[r] : nullptr);
   for (const auto &blk : s.plan->blocks)
     for (uint16_t in : blk.inputs)

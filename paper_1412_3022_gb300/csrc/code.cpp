@@ -1,4 +1,5 @@
-// Host construction of PM-MSR codes (see code.h for the paper sections).
+// Host construction of PM-MSR and PM-MBR codes (see code.h for the paper
+// sections).
 #include "code.h"
 
 #include <algorithm>
@@ -52,8 +53,76 @@ bool mat_inverse(const Mat &A, Mat &out) {
 
 static uint8_t gpow(unsigned e) { return gf_pow(2, e % 255); }
 
+// Rows of Gcode that are unit vectors copy one data block verbatim.
+static void mark_unit_rows(CodeMatrices &c) {
+  c.unit_col.assign(c.N, -1);
+  for (int r = 0; r < c.N; r++) {
+    int col = -1, cnt = 0;
+    for (int q = 0; q < c.K && cnt < 2; q++)
+      if (c.Gcode.at(r, q)) {
+        cnt++;
+        col = c.Gcode.at(r, q) == 1 ? q : -2;
+      }
+    if (cnt == 1 && col >= 0) c.unit_col[r] = col;
+  }
+}
+
+// PM-MBR (Sec. 2: alpha = d, Delta = (2d-k+1)/2).  M = [S T; T^t 0] with S
+// symmetric k x k and T k x (d-k); the upper triangle of S is numbered row
+// by row, then T row by row.  Psi = [I_k 0; C] (the systematic form of
+// Sec. 3.2, Psi = [I; Psi'']) with C_ij = (g^(d+i) + g^j)^-1 a Cauchy matrix
+// (0-based i < n-k, j < d): every square sub-matrix of C is invertible, so
+// any d rows of Psi, and any k rows of its first k columns, are independent.
+static int build_mbr(int n, int k, int d, int systematic, CodeMatrices &c, std::string &err) {
+  if (k < 1 || d < k || d > n - 1) {
+    err = "PM-MBR needs 1 <= k <= d <= n-1";
+    return kEInval;
+  }
+  if (n > 254 || d + n - k > 255) {
+    err = "PM-MBR needs d + n - k <= 255 (distinct Cauchy points in GF(2^8))";
+    return kEInval;
+  }
+  c.n = n;
+  c.k = k;
+  c.d = d;
+  c.alpha = d;
+  c.K = k * (2 * d - k + 1) / 2;
+  c.N = n * d;
+  c.construction = kConsMbr;
+  c.systematic = systematic;
+  c.psi = Mat(n, d);
+  for (int i = 0; i < k; i++) c.psi.at(i, i) = 1;
+  for (int i = 0; i < n - k; i++)
+    for (int j = 0; j < d; j++)
+      c.psi.at(k + i, j) = gf_inv(gpow((unsigned)(d + i)) ^ gpow((unsigned)j));
+  c.phi = c.psi;  // helper h projects its d blocks on psi_f
+  c.lambda.assign(n, 0);
+  c.L.assign((size_t)d * d, -1);
+  int next = 0;
+  for (int i = 0; i < k; i++)
+    for (int j = i; j < k; j++, next++) c.L[(size_t)i * d + j] = c.L[(size_t)j * d + i] = next;
+  for (int i = 0; i < k; i++)
+    for (int m = 0; m < d - k; m++, next++)
+      c.L[(size_t)i * d + k + m] = c.L[(size_t)(k + m) * d + i] = next;
+  c.G = Mat(c.N, c.K);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < d; j++)
+      for (int l = 0; l < d; l++) {
+        const int s = c.L[(size_t)l * d + j];
+        if (s >= 0) c.G.at(d * i + j, s) = c.psi.at(i, l);
+      }
+  c.Gcode = c.G;  // already systematic: node i < k stores row i of M
+  mark_unit_rows(c);
+  return kOk;
+}
+
 int build_code(int n, int k, int d, int construction, int systematic, CodeMatrices &c,
                std::string &err) {
+  if (systematic != 0 && systematic != 1) {
+    err = "form must be PMRC_NONSYSTEMATIC or PMRC_SYSTEMATIC";
+    return kEInval;
+  }
+  if (construction == kConsMbr) return build_mbr(n, k, d, systematic, c, err);
   if (k < 2 || d != 2 * k - 2) {
     err = "PM-MSR needs k >= 2 and d = 2k-2";
     return kEInval;
@@ -63,11 +132,7 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
     return kEInval;
   }
   if (construction != 0 && construction != 1) {
-    err = "construction must be PMRC_VANILLA or PMRC_SPARSE";
-    return kEInval;
-  }
-  if (systematic != 0 && systematic != 1) {
-    err = "form must be PMRC_NONSYSTEMATIC or PMRC_SYSTEMATIC";
+    err = "construction must be PMRC_VANILLA, PMRC_SPARSE or PMRC_MBR";
     return kEInval;
   }
   const int a = k - 1;
@@ -127,6 +192,8 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
       }
   }
   const int K = k * a, N = n * a;
+  c.K = K;
+  c.N = N;
   c.G = Mat(N, K);
   for (int i = 0; i < n; i++)
     for (int j = 0; j < a; j++)
@@ -142,6 +209,7 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
     }
     c.Gcode = mat_mul(c.G, topinv);
   }
+  mark_unit_rows(c);
   return kOk;
 }
 
@@ -184,6 +252,12 @@ int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, st
     err = "the helpers' rows of Psi are singular for this failed node";
     return kESingular;
   }
+  if (c.construction == kConsMbr) {
+    // Psi_H M psi_f = p  =>  M psi_f = Psi_H^-1 p, and node f stores
+    // psi_f^t M = (M psi_f)^t (M symmetric): D = Psi_H^-1.
+    D = inv;
+    return kOk;
+  }
   // Psi_H M phi_f = p  =>  M phi_f = Psi_H^-1 p = [S1 phi_f; S2 phi_f];
   // node f stores phi_f^t S1 + lambda_f phi_f^t S2 (S1, S2 symmetric).
   const int a = c.alpha;
@@ -194,9 +268,66 @@ int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, st
   return kOk;
 }
 
+// MBR reconstruction: the k alpha rows of the listed nodes span the K data
+// blocks.  Rows are taken in order of preference -- rows copying a data
+// block first, then the others in node order -- and kept when independent
+// of those already kept (incremental elimination); the K kept rows are
+// inverted and every other row gets coefficient zero.
+static int decode_matrix_mbr(const CodeMatrices &c, const int *nodes, Mat &Rinv,
+                             std::string &err) {
+  const int a = c.alpha, K = c.K, KA = c.k * a;
+  const auto &T = mul_table().t;
+  std::vector<int> order;
+  for (int pass = 0; pass < 2; pass++)
+    for (int p = 0; p < KA; p++) {
+      const bool unit = c.unit_col[a * nodes[p / a] + p % a] >= 0;
+      if (unit == (pass == 0)) order.push_back(p);
+    }
+  Mat E(K, K), picked(K, K);      // reduced rows (pivot 1, pivots cleared) and originals
+  std::vector<int> pivot, kept;
+  std::vector<uint8_t> v(K);
+  for (int p : order) {
+    if ((int)kept.size() == K) break;
+    const int row = a * nodes[p / a] + p % a;
+    for (int q = 0; q < K; q++) v[q] = c.Gcode.at(row, q);
+    for (size_t e = 0; e < kept.size(); e++) {
+      const uint8_t f = v[pivot[e]];
+      if (!f) continue;
+      for (int q = 0; q < K; q++) v[q] ^= T[f][E.at((int)e, q)];
+    }
+    int pc = 0;
+    while (pc < K && !v[pc]) pc++;
+    if (pc == K) continue;
+    const uint8_t *s = T[gf_inv(v[pc])];
+    for (int q = 0; q < K; q++) v[q] = s[v[q]];
+    for (size_t e = 0; e < kept.size(); e++) {
+      const uint8_t f = E.at((int)e, pc);
+      if (!f) continue;
+      for (int q = 0; q < K; q++) E.at((int)e, q) ^= T[f][v[q]];
+    }
+    const int e = (int)kept.size();
+    for (int q = 0; q < K; q++) {
+      E.at(e, q) = v[q];
+      picked.at(e, q) = c.Gcode.at(row, q);
+    }
+    pivot.push_back(pc);
+    kept.push_back(p);
+  }
+  Mat inv;
+  if ((int)kept.size() < K || !mat_inverse(picked, inv)) {
+    err = "these k nodes do not determine the data";
+    return kESingular;
+  }
+  Rinv = Mat(K, KA);
+  for (int x = 0; x < K; x++)
+    for (int t = 0; t < K; t++) Rinv.at(x, kept[t]) = inv.at(x, t);
+  return kOk;
+}
+
 int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err) {
   int rc = check_distinct(nodes, c.k, c.n, -1, err, "nodes");
   if (rc) return rc;
+  if (c.construction == kConsMbr) return decode_matrix_mbr(c, nodes, Rinv, err);
   const int a = c.alpha, K = c.k * a;
   if (!c.systematic) {
     Mat GR(K, K);

@@ -7,6 +7,10 @@
 //   Sec. 3.3  Psi = [Phi  Lambda*Phi], vanilla (Vandermonde) and sparse
 //             (identity + Cauchy) constructions; helper read reduction
 //
+//   Sec. 2    MBR point alpha = d, Delta = (2d-k+1)/2 (construction 2):
+//             M = [S T; T^t 0] symmetric d x d, Psi = [I_k 0; Cauchy]
+//             (Sec. 3.2: a systematic Psi = [I; Psi''] given directly)
+//
 // All matrices are row-major uint8 over GF(2^8) (modulus 0x11D).
 #pragma once
 #include <cstdint>
@@ -39,16 +43,20 @@ Mat mat_mul(const Mat &A, const Mat &B);
 // Gauss-Jordan inverse; returns false if A is singular.
 bool mat_inverse(const Mat &A, Mat &out);
 
+constexpr int kConsMbr = 2;  // construction id of the PM-MBR code
+
 struct CodeMatrices {
   int n = 0, k = 0, d = 0, alpha = 0;
-  int construction = 0;  // 0 vanilla, 1 sparse
+  int K = 0, N = 0;      // data blocks (k alpha for MSR, k Delta for MBR), n alpha
+  int construction = 0;  // 0 vanilla MSR, 1 sparse MSR, 2 MBR
   int systematic = 0;
-  Mat phi;      // n x alpha
-  std::vector<uint8_t> lambda;  // n
+  Mat phi;      // n x alpha: the helper projection vectors (Phi for MSR, Psi for MBR)
+  std::vector<uint8_t> lambda;  // n (MSR)
   Mat psi;      // n x d
-  std::vector<int> L;           // d x alpha index matrix
-  Mat G;        // n*alpha x k*alpha, linearized generator (Sec. 3.1)
-  Mat Gcode;    // the code's generator: G, or G' = G G~^-1 when systematic
+  std::vector<int> L;           // d x alpha index matrix (-1: zero entry of M, MBR)
+  Mat G;        // N x K, linearized generator (Sec. 3.1)
+  Mat Gcode;    // the code's generator: G, or G' = G G~^-1 when systematic (MSR)
+  std::vector<int> unit_col;    // per row of Gcode: the data block it copies, or -1
 };
 
 // Builds every matrix of the code.  Returns kEInval for bad parameters,
@@ -62,8 +70,10 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
 void helper_coefficients(const CodeMatrices &c, int f, std::vector<uint8_t> &coef);
 int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, std::string &err);
 
-// Reconstruction from k nodes (Sec. 2): rows of (Gcode restricted to the
-// nodes' rows)^-1.  `wanted[r]` selects the data rows to produce.
+// Reconstruction from k nodes (Sec. 2): Rinv (K x k alpha) with
+// X = Rinv Y_nodes.  MSR: the inverse of the nodes' rows of Gcode.  MBR: the
+// nodes' k alpha rows have rank K; K independent ones (rows that copy a data
+// block first) are inverted and the others get zero coefficients.
 int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err);
 
 // Default helper set for node f: the d lowest-index survivors, or the first

@@ -430,7 +430,8 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   r->B = q->block_bytes;
   r->in = q->in;
   r->out = q->out;
-  const size_t a = c->m.alpha, K = c->m.k * a, N = c->m.n * a;
+  // K data blocks, KA = k alpha blocks on the first k (or any k) nodes, N coded
+  const size_t a = c->m.alpha, K = c->m.K, KA = (size_t)c->m.k * a, N = c->m.N;
   // Build (or find) the request's coefficient plan here, on the caller's
   // thread, and upload it to the server's device: the scheduler then only
   // assembles work items.  Plan time counts in the request's latency.
@@ -443,7 +444,7 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   switch (q->op) {
     case PMRC_OP_ENCODE:
       r->nin = K;
-      r->nout = c->m.systematic ? N - K : N;
+      r->nout = c->m.systematic ? N - KA : N;
       r->user_bytes = (int64_t)K * r->B;
       rc = c->encode->device_image(&image, err);
       break;
@@ -489,7 +490,7 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
         rc = decode_plan(c, q->nodes, std::vector<char>(K, 1), dp, err);
         if (!rc) rc = dp->device_image(&image, err);
       }
-      r->nin = K;
+      r->nin = KA;
       r->nout = K;
       r->user_bytes = (int64_t)K * r->B;
       break;

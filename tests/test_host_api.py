@@ -85,7 +85,7 @@ def test_error_statuses():
         P.pmrc_create(14, 8, 14, 1, 1)          # n < 2k-1
     assert e.value.rc == P.PMRC_EINVAL
     with pytest.raises(P.PMRCError) as e:
-        P.pmrc_create(16, 8, 14, 2, 1)          # construction
+        P.pmrc_create(16, 8, 14, 3, 1)          # construction
     assert e.value.rc == P.PMRC_EINVAL
     c = P.Code(8, 4, 1, 1)
     with pytest.raises(P.PMRCError) as e:
@@ -156,3 +156,52 @@ def test_k16_systematic_decode_matrix_matches_full_inverse(S):
     systematic form; the rows must equal the oracle's full inverse."""
     c = P.Code(32, 16, 1, 1)
     assert np.array_equal(c.decode_matrix(S), O.decode_matrix(32, 16, 1, True, S))
+
+
+# ------------------------------------------------------------------ PM-MBR
+MBR_CASES = [(6, 3, 4), (8, 4, 6), (8, 4, 7), (16, 8, 14), (16, 8, 15), (32, 16, 30)]
+
+
+@pytest.mark.parametrize("n,k,d", MBR_CASES)
+def test_mbr_matrices_match_oracle(n, k, d):
+    c = P.Code(n, k, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=d)
+    a, B = O.mbr_params(n, k, d)
+    assert (c.alpha, c.data_blocks, c.coded_blocks) == (a, B, n * a)
+    assert np.array_equal(P.pmrc_code_generator(c.handle), O.mbr_generator(n, k, d))
+    rng = np.random.default_rng(n + d)
+    for f in range(n):
+        H = c.default_helpers(f)
+        assert f not in H and len(set(H)) == d
+        assert np.array_equal(P.pmrc_helper_coefficients(c.handle, f),
+                              O.mbr_helper_coefficients(n, k, d, f))
+        H2 = rng.permutation([h for h in range(n) if h != f])[:d].tolist()
+        assert np.array_equal(P.pmrc_newcomer_matrix(c.handle, f, H2),
+                              O.mbr_newcomer_matrix(n, k, d, f, H2))
+    X = rng.integers(0, 256, (B, 3), dtype=np.uint8)
+    Y = O.mbr_encode(n, k, d, X)
+    for _ in range(6):   # the decode matrix may pick other rows than the oracle's
+        S = rng.permutation(rng.choice(n, k, replace=False)).tolist()
+        R = P.pmrc_decode_matrix(c.handle, S)
+        assert R.shape == (B, k * a)
+        assert np.array_equal(O.region_apply(R, Y[[a * i + j for i in S for j in range(a)]]), X)
+
+
+def test_mbr_create_rejects_bad_points():
+    for n, k, d in [(8, 4, 3), (8, 4, 8), (8, 0, 4)]:
+        with pytest.raises(P.PMRCError) as e:
+            P.Code(n, k, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=d)
+        assert e.value.rc == P.PMRC_EINVAL
+    c = P.Code(8, 4, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=6)
+    assert c.specific_workspace_bytes(4096) == 0
+    with pytest.raises(P.PMRCError) as e:   # PM-MSR data collector only
+        c.decode_specific([0, 1, 2, 3], [0] * 24, [0] * 18, 4096, 1 << 20, 1 << 20)
+    assert e.value.rc == P.PMRC_EUNSUPPORTED
+
+
+def test_mbr_encode_plan_is_sparse():
+    """Parity rows touch d or k data blocks (Sec. 4.3: naturally sparse)."""
+    c = P.Code(16, 8, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=14)
+    G = P.pmrc_code_generator(c.handle)
+    par = G[8 * 14:]
+    st = P.pmrc_plan_stats(par)
+    assert st["nnz"] == int((par != 0).sum()) == 8 * (8 * 14 + 6 * 8)
