@@ -33,9 +33,10 @@ struct Spec {
   int n, k, construction, form;
 };
 
-// the codes of the benchmarked workloads (n = 2k)
+// the codes of the benchmarked workloads (n = 2k, d = 2k-2; construction 2
+// is PM-MBR)
 const Spec kSpecs[] = {
-    {16, 8, 1, 1}, {16, 8, 0, 0}, {8, 4, 1, 1}, {6, 3, 1, 1}, {6, 3, 0, 0},
+    {16, 8, 1, 1}, {16, 8, 0, 0}, {8, 4, 1, 1}, {6, 3, 1, 1}, {6, 3, 0, 0}, {16, 8, 2, 1},
 };
 
 constexpr int kRows = 8;    // rows per block (8 x 8 bit-plane accumulators)
@@ -71,8 +72,10 @@ int main(int argc, char **argv) {
       fprintf(stderr, "gen_bitslice: %s\n", err.c_str());
       return 1;
     }
-    const int a = c.alpha, K = s.k * a, N = s.n * a;
-    const int first = s.form ? K : 0;
+    // K data blocks (k alpha for PM-MSR, k Delta for PM-MBR); the systematic
+    // form encodes the rows of the nodes after the first k
+    const int a = c.alpha, K = c.K, N = c.N;
+    const int first = s.form ? s.k * a : 0;
     const int rows = N - first;
     std::vector<uint8_t> M((size_t)rows * K);
     for (int r = 0; r < rows; r++)

@@ -216,3 +216,22 @@ def test_mbr_batched_and_served():
     assert np.array_equal(q_out[1].numpy(), Y[a * f:a * f + a])
     assert np.array_equal(q_out[2].numpy(), X)
     srv.close()
+
+
+def test_mbr_bitsliced_encode_matches_generic_and_oracle():
+    n, k, d = 16, 8, 14
+    c = mbr(n, k, d)
+    a, B = O.mbr_params(n, k, d)
+    nbytes = 64 * 1024 + 32 + 7          # bitsliced body plus a ragged tail
+    X = inputs.blocks(B, nbytes, seed=51)
+    xin = Blocks(B, nbytes, 0, X)
+    outs = {}
+    for which in (P.PMRC_KERNEL_BITSLICED, P.PMRC_KERNEL_GENERIC):
+        c.set_encode_kernel(which)
+        y = Blocks((n - k) * a, nbytes)
+        c.encode(xin.ptrs(), y.ptrs(), nbytes)
+        assert y.guards_intact()
+        outs[which] = y.get()
+    c.set_encode_kernel(P.PMRC_KERNEL_AUTO)
+    assert np.array_equal(outs[P.PMRC_KERNEL_BITSLICED], outs[P.PMRC_KERNEL_GENERIC])
+    assert np.array_equal(outs[P.PMRC_KERNEL_BITSLICED], O.mbr_encode(n, k, d, X)[k * a:])
