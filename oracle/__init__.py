@@ -27,6 +27,10 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                              subsets at n = 16 recover the data exactly
   encode_precode             pinned: data as nodes 0..k-1 re-decodes to itself
                              and every k-subset of the result recovers the data
+  rs_*                       pinned: V Z is polynomial evaluation (Horner,
+                             independent multiply); systematic identity top;
+                             every k-subset decodes and every node repairs
+                             from every k helpers (small n), sampled at n=16
   mbr_*                      pinned: k Delta = k(2d-k+1)/2 and alpha = d
                              (Sec. 2); G X equals Psi M(X); systematic nodes
                              hold the symbols verbatim; any d rows of Psi and
@@ -118,6 +122,10 @@ def lib():
                 "or_mbr_newcomer_matrix": (i, [i, i, i, i, ip, u8p]),
                 "or_mbr_decode_matrix": (i, [i, i, i, ip, u8p]),
                 "or_mbr_decode": (i, [i, i, i, ip, u8p, u8p, sz]),
+                "or_rs_generator": (i, [i, i, i, u8p]),
+                "or_rs_encode": (i, [i, i, i, u8p, u8p, sz]),
+                "or_rs_decode": (i, [i, i, i, ip, u8p, u8p, sz]),
+                "or_rs_repair": (i, [i, i, i, i, ip, u8p, u8p, sz]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -415,3 +423,37 @@ def mbr_decode(n: int, k: int, d: int, nodes, node_blocks: np.ndarray) -> np.nda
     _check(lib().or_mbr_decode(n, k, d, _ip(s), _u8(node_blocks), _u8(out),
                                node_blocks.shape[1]), "mbr_decode")
     return out
+
+
+# ------------------------------------------------------------ Reed-Solomon
+def rs_generator(n: int, k: int, systematic: bool = True) -> np.ndarray:
+    G = np.zeros((n, k), np.uint8)
+    _check(lib().or_rs_generator(n, k, int(systematic), _u8(G)), "rs_generator")
+    return G
+
+
+def rs_encode(n: int, k: int, systematic: bool, data: np.ndarray) -> np.ndarray:
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    assert data.shape[0] == k
+    out = np.zeros((n, data.shape[1]), np.uint8)
+    _check(lib().or_rs_encode(n, k, int(systematic), _u8(data), _u8(out), data.shape[1]),
+           "rs_encode")
+    return out
+
+
+def rs_decode(n: int, k: int, systematic: bool, nodes, node_blocks: np.ndarray) -> np.ndarray:
+    s = _ints(nodes)
+    node_blocks = np.ascontiguousarray(node_blocks, dtype=np.uint8)
+    out = np.zeros((k, node_blocks.shape[1]), np.uint8)
+    _check(lib().or_rs_decode(n, k, int(systematic), _ip(s), _u8(node_blocks), _u8(out),
+                              node_blocks.shape[1]), "rs_decode")
+    return out
+
+
+def rs_repair(n: int, k: int, systematic: bool, f: int, helpers, helper_blocks: np.ndarray) -> np.ndarray:
+    h = _ints(helpers)
+    helper_blocks = np.ascontiguousarray(helper_blocks, dtype=np.uint8)
+    out = np.zeros((1, helper_blocks.shape[1]), np.uint8)
+    _check(lib().or_rs_repair(n, k, int(systematic), f, _ip(h), _u8(helper_blocks), _u8(out),
+                              helper_blocks.shape[1]), "rs_repair")
+    return out[0]

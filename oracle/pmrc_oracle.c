@@ -943,3 +943,96 @@ int or_mbr_decode(int n, int k, int d, const int *nodes, const uint8_t *node_blo
     free(R);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reed-Solomon baseline (Sec. 4: the paper compares every PM code against   */
+/* Vandermonde-based Reed-Solomon codes).  Restated from the definitions:    */
+/* node i stores the evaluation at x_i = g^i of the polynomial whose k       */
+/* coefficients are the message Z, i.e. Y = V Z with V[i][j] = g^(i j)       */
+/* (n <= 255 distinct points: any k rows of V are invertible).  The          */
+/* systematic form is Sec. 3.2's G' = V V~^-1 with V~ the first k rows.      */
+/* One block per node (alpha = 1); repair of node f reads any k nodes.       */
+/* ------------------------------------------------------------------------ */
+
+int or_rs_generator(int n, int k, int systematic, uint8_t *G)
+{
+    if (k < 1 || n <= k || n > 255)
+        return OR_EINVAL;
+    uint8_t *V = (uint8_t *)malloc((size_t)n * k);
+    uint8_t *Vinv = (uint8_t *)malloc((size_t)k * k);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < k; j++)
+            V[i * k + j] = or_gf_pow_g(i * j);
+    int rc = OR_OK;
+    if (!systematic) {
+        memcpy(G, V, (size_t)n * k);
+    } else {
+        rc = or_invert(k, V, Vinv);
+        if (rc == OR_OK)
+            or_mat_mul(n, k, k, V, Vinv, G);
+    }
+    free(V);
+    free(Vinv);
+    return rc;
+}
+
+int or_rs_encode(int n, int k, int systematic, const uint8_t *data, uint8_t *out, size_t nbytes)
+{
+    uint8_t *G = (uint8_t *)malloc((size_t)n * k);
+    int rc = or_rs_generator(n, k, systematic, G);
+    if (rc == OR_OK)
+        or_region_apply(n, k, G, data, nbytes, out, nbytes, nbytes);
+    free(G);
+    return rc;
+}
+
+/* X = G_S^-1 Y_S from the blocks of any k distinct nodes. */
+int or_rs_decode(int n, int k, int systematic, const int *nodes, const uint8_t *node_blocks,
+                 uint8_t *data, size_t nbytes)
+{
+    if (k < 1 || n <= k || n > 255)
+        return OR_EINVAL;
+    for (int i = 0; i < k; i++) {
+        if (nodes[i] < 0 || nodes[i] >= n)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (nodes[j] == nodes[i])
+                return OR_EINVAL;
+    }
+    uint8_t *G = (uint8_t *)malloc((size_t)n * k);
+    uint8_t *GS = (uint8_t *)malloc((size_t)k * k);
+    uint8_t *R = (uint8_t *)malloc((size_t)k * k);
+    int rc = or_rs_generator(n, k, systematic, G);
+    if (rc == OR_OK) {
+        for (int i = 0; i < k; i++)
+            memcpy(GS + (size_t)i * k, G + (size_t)nodes[i] * k, (size_t)k);
+        rc = or_invert(k, GS, R);
+    }
+    if (rc == OR_OK)
+        or_region_apply(k, k, R, node_blocks, nbytes, data, nbytes, nbytes);
+    free(G);
+    free(GS);
+    free(R);
+    return rc;
+}
+
+/* Repair of node f from k helpers: decode, then re-encode row f. */
+int or_rs_repair(int n, int k, int systematic, int f, const int *helpers,
+                 const uint8_t *helper_blocks, uint8_t *out, size_t nbytes)
+{
+    if (f < 0 || f >= n)
+        return OR_EINVAL;
+    for (int i = 0; i < k; i++)
+        if (helpers[i] == f)
+            return OR_EINVAL;
+    uint8_t *X = (uint8_t *)malloc((size_t)k * (nbytes ? nbytes : 1));
+    uint8_t *G = (uint8_t *)malloc((size_t)n * k);
+    int rc = or_rs_decode(n, k, systematic, helpers, helper_blocks, X, nbytes);
+    if (rc == OR_OK)
+        rc = or_rs_generator(n, k, systematic, G);
+    if (rc == OR_OK)
+        or_region_apply(1, k, G + (size_t)f * k, X, nbytes, out, nbytes, nbytes);
+    free(X);
+    free(G);
+    return rc;
+}
