@@ -44,6 +44,7 @@ WORKLOAD = ("PM-MSR n=16 k=8 d=14 alpha=7 GF(2^8)/0x11D, 56 data blocks x 1 MiB 
             "repair of a seeded node (14 helper projections + newcomer) + "
             "reconstruction from a seeded 8-node subset")
 FLUSH_BYTES = 512 << 20
+SMS = 152   # GB300 streaming multiprocessors
 
 
 # ------------------------------------------------------------ multi-rank
@@ -154,6 +155,7 @@ def measured_peaks():
 class Workload:
     def __init__(self, torch, P, inputs, B, seed, device):
         self.t = torch
+        self.P = P
         self.B = B
         a, K = A_, K_ * A_
         self.sysc = P.Code(N_, K_, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
@@ -213,6 +215,11 @@ class Workload:
         self.user = {"gen_encode": K * B, "sys_encode": K * B, "repair": a * B, "decode": K * B}
         self.decode_missing = len(missing)
         self.helper_reads = reads_per_helper
+        # products per byte column the region kernel computes (planner blocks,
+        # zero products included) for the ops it runs
+        P = self.P
+        dec_st = P.pmrc_plan_stats(R[missing]) if missing else {"entries": 0}
+        self.entries = {"decode": int(dec_st["entries"])}
         del np
 
     def ops(self):
@@ -304,6 +311,18 @@ def run_ours(args, rank, world, local_rank):
                 "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(ach / hbm, 4), "peak_source": peak_src + " hbm_gbs (burst copy)",
                 "traffic": None}
+    # the same kernel against its integer-ALU ceiling: the region kernel
+    # spends 12 PRMT + 6 LOP3 (18 ALU lane-ops) per 16 GF(2^8) byte-products,
+    # and the ALU pipe issues 64 lanes/clk/SM on 152 SMs at the sampled clock
+    if dom in W.entries:
+        mhz = (ck or {}).get("sm_mhz") or 2070.0
+        peak_p = 64.0 / 18.0 * 16.0 * SMS * mhz * 1e6 / 1e9
+        ach_p = W.entries[dom] * B / (op_ms[dom] * 1e-3) / 1e9
+        roofline["alu"] = {"unit": "G byte-products/s", "achieved": round(ach_p, 1),
+                           "peak": round(peak_p, 1), "frac": round(ach_p / peak_p, 4),
+                           "products_per_launch": W.entries[dom] * B, "sm_mhz": mhz,
+                           "model": "18 ALU lane-ops per 16 byte-products; 64 ALU "
+                                    "lanes/clk/SM x 152 SMs x sampled SM clock"}
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
@@ -340,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
     del ws
     if not args.no_mbr:
         per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
+        per_op.update(run_rs(torch, P, inputs, args, flush, stream, dev, hbm))
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
@@ -426,6 +446,49 @@ def run_mbr(torch, P, inputs, args, flush, stream, dev, hbm):
                      "alg_bytes": alg, "frac_hbm": round(alg / (ms * 1e-3) / 1e9 / hbm, 4)}
     out["mbr_repair"].update({"failed_node": f, "helper_reads": reads})
     out["mbr_decode"].update({"nodes": S, "missing_rows": missing})
+    torch.cuda.synchronize()
+    return out
+
+
+def run_rs(torch, P, inputs, args, flush, stream, dev, hbm):
+    """Reed-Solomon baseline rows (the paper's comparison code, Sec. 4):
+    RS(16, 8) systematic over the same 56 MiB stripe (8 data blocks of
+    7 x the block size): encode, repair of a seeded node from 8 helpers,
+    lazy decode from a seeded 8-node set."""
+    n, k, B = 16, 8, 7 * args.block_bytes
+    c = P.Code(n, k, P.PMRC_RS, P.PMRC_SYSTEMATIC)
+    st = int(torch.cuda.current_stream(dev).cuda_stream)
+    Y = torch.empty((n, B), dtype=torch.uint8, device=dev)
+    Y[:k].copy_(inputs.device_blocks(k, B, args.seed + 88, device=dev))
+    c.encode(P.ptr_array([Y[i] for i in range(k)]), P.ptr_array([Y[k + i] for i in range(n - k)]), B)
+    f = inputs.failed_node(n, args.seed + 88)
+    H = c.default_helpers(f)
+    S = inputs.node_subset(n, k, args.seed + 88)
+    node = torch.empty((1, B), dtype=torch.uint8, device=dev)
+    Xr = torch.empty((k, B), dtype=torch.uint8, device=dev)
+    dec_in = [Y[i] for i in S]
+    dec_out = [Xr[r] for r in range(k)]
+    for pos, i in enumerate(S):       # present data blocks stay in place
+        if i < k:
+            dec_out[i] = dec_in[pos]
+    missing = [r for r in range(k) if r not in S]
+    x_arr, par_arr = P.ptr_array([Y[i] for i in range(k)]), P.ptr_array([Y[k + i] for i in range(n - k)])
+    H_arr, h_in, n_out = P.int_array(H), P.ptr_array([Y[h] for h in H]), P.ptr_array([node[0]])
+    S_arr, din, dout = P.int_array(S), P.ptr_array(dec_in), P.ptr_array(dec_out)
+    ops = {
+        "rs_encode": (lambda: c.encode(x_arr, par_arr, B, st), k * B, (k + n - k) * B),
+        "rs_repair": (lambda: c.repair(f, H_arr, h_in, n_out, B, st), B, (k + 1) * B),
+        "rs_decode": (lambda: c.decode(S_arr, din, dout, B, st), k * B,
+                      ((k if missing else 0) + len(missing)) * B),
+    }
+    out = {}
+    for name, (fn, user, alg) in ops.items():
+        ms = time_op(torch, stream, flush, args, fn)
+        out[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
+                     "alg_bytes": alg, "frac_hbm": round(alg / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "block_bytes": B}
+    out["rs_repair"]["failed_node"] = f
+    out["rs_decode"].update({"nodes": S, "missing_rows": len(missing)})
     torch.cuda.synchronize()
     return out
 

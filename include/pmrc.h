@@ -65,6 +65,7 @@ enum {
 
 enum { PMRC_VANILLA = 0, PMRC_SPARSE = 1 };            /* Sec. 3.3 (PM-MSR)   */
 enum { PMRC_MBR = 2 };                                 /* Sec. 2, 3.2, 4.3    */
+enum { PMRC_RS = 3 };                                  /* Sec. 4 baseline     */
 enum { PMRC_NONSYSTEMATIC = 0, PMRC_SYSTEMATIC = 1 };  /* Sec. 3.1 / Sec. 3.2 */
 
 /* Builds the code (Phi, Lambda, Psi, L, G and, for the systematic form,
@@ -86,7 +87,13 @@ enum { PMRC_NONSYSTEMATIC = 0, PMRC_SYSTEMATIC = 1 };  /* Sec. 3.1 / Sec. 3.2 */
  * the n-k parity nodes).  Repair: helper h sends its d blocks projected on
  * psi_f (pmrc_helper_coefficients), the newcomer applies Psi_H^-1 (any d
  * helpers work).  Decode reads k nodes (k d blocks) and writes the K data
- * blocks.  The specific calls below are PM-MSR only. */
+ * blocks.  The specific calls below are PM-MSR only.
+ *
+ * PMRC_RS: the Reed-Solomon baseline the paper compares against (Sec. 4):
+ * node i stores the message polynomial evaluated at g^i (Y = V Z,
+ * V[i][j] = g^(ij)), systematic form V V~^-1 (Sec. 3.2); 1 <= k < n <= 255,
+ * d must equal k, alpha = 1.  Repair of node f reads one block from each of
+ * k helpers (helper coefficient 1) and applies G'[f] G'_H^-1. */
 int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out);
 
 /* Frees the handle and its device plans.  The caller makes sure no call on
@@ -135,7 +142,9 @@ int pmrc_repair_newcomer(const pmrc_code *code, int failed, const int *helpers,
  * Sec. 3.3) the newcomer reads the helpers' blocks directly.
  * helper_blocks: d*alpha pointers (helper i's alpha blocks at
  * [i*alpha, i*alpha + alpha)), entries with a zero helper coefficient may be
- * NULL.  out: alpha pointers.  Requires alpha <= 16. */
+ * NULL.  out: alpha pointers.  Requires alpha <= 16.  For PMRC_RS (one
+ * block per node, helper coefficient 1) the projections are the helper
+ * blocks themselves and the call runs the newcomer row over them. */
 int pmrc_repair(const pmrc_code *code, int failed, const int *helpers,
                 const uint8_t *const *helper_blocks, uint8_t *const *out, size_t block_bytes,
                 pmrc_stream_t stream);

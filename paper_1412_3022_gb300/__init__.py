@@ -40,6 +40,7 @@ PMRC_OP_DECODE = 2
 PMRC_VANILLA = 0
 PMRC_SPARSE = 1
 PMRC_MBR = 2
+PMRC_RS = 3
 PMRC_NONSYSTEMATIC = 0
 PMRC_SYSTEMATIC = 1
 
@@ -524,8 +525,10 @@ class Code:
     def __init__(self, n: int, k: int, construction: int = PMRC_SPARSE,
                  form: int = PMRC_SYSTEMATIC, d: int = None):
         """PM-MSR (PMRC_VANILLA / PMRC_SPARSE): d = 2k-2.  PM-MBR (PMRC_MBR):
-        any k <= d <= n-1 (default 2k-2)."""
-        self.handle = pmrc_create(n, k, 2 * k - 2 if d is None else d, construction, form)
+        any k <= d <= n-1 (default 2k-2).  Reed-Solomon (PMRC_RS): d = k."""
+        if d is None:
+            d = k if construction == PMRC_RS else 2 * k - 2
+        self.handle = pmrc_create(n, k, d, construction, form)
         p = pmrc_code_params(self.handle)
         self.n, self.k, self.d, self.alpha = p["n"], p["k"], p["d"], p["alpha"]
         self.construction, self.form = construction, form

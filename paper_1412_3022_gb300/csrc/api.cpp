@@ -355,8 +355,18 @@ int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *co
                 uint8_t *const *out, size_t nbytes, pmrc_stream_t stream) {
   if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
   if (c->m.alpha > 16) return fail(PMRC_EUNSUPPORTED, "pmrc_repair needs alpha <= 16");
-  std::shared_ptr<FusedRepairPlan> p;
   std::string err;
+  if (c->m.construction == kConsRs) {
+    // one block per node and helper coefficient 1: the projections are the
+    // helpers' blocks themselves, so the repair is the newcomer's 1 x k row
+    // applied to them
+    if (!out[0]) return fail(PMRC_EINVAL, "output block is NULL");
+    std::shared_ptr<Plan> np;
+    int rc = newcomer_plan(c, f, helpers, np, err);
+    if (!rc) rc = launch_region(*np, blocks, out, nbytes, (cudaStream_t)stream, err);
+    return rc ? fail(rc, err) : PMRC_OK;
+  }
+  std::shared_ptr<FusedRepairPlan> p;
   int rc = fused_repair_plan(c, f, helpers, p, err);
   if (rc) return fail(rc, err);
   rc = launch_fused_repair(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
@@ -398,7 +408,7 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
 }
 
 size_t pmrc_specific_workspace_bytes(const pmrc_code *c, size_t block_bytes) {
-  if (!c || c->m.construction == kConsMbr) return 0;
+  if (!c || c->m.construction > 1) return 0;  // PM-MSR only
   return specific_workspace_blocks(c->m) * specific_pitch(block_bytes);
 }
 
@@ -463,7 +473,7 @@ int pmrc_decode_specific(const pmrc_code *c, const int *nodes, const uint8_t *co
                          uint8_t *const *data_out, size_t nbytes, void *workspace,
                          size_t workspace_bytes, pmrc_stream_t stream) {
   if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
-  if (c->m.construction == kConsMbr)
+  if (c->m.construction > 1)
     return fail(PMRC_EUNSUPPORTED, "the data collector of this library is the PM-MSR one");
   {
     std::vector<char> seen(c->m.n, 0);
@@ -500,8 +510,8 @@ int pmrc_encode_precode(const pmrc_code *c, const uint8_t *const *data, uint8_t 
                         size_t nbytes, void *workspace, size_t workspace_bytes,
                         pmrc_stream_t stream) {
   if (!c || !data || !parity) return fail(PMRC_EINVAL, "NULL argument");
-  if (c->m.construction == kConsMbr)
-    return fail(PMRC_EUNSUPPORTED, "PM-MBR is systematic by construction: use pmrc_encode");
+  if (c->m.construction > 1)
+    return fail(PMRC_EUNSUPPORTED, "precode encode is the PM-MSR systematic construction");
   if (!c->m.systematic)
     return fail(PMRC_EINVAL, "precode encode produces a systematic code's parity");
   const int K = c->m.k * c->m.alpha, NP = (c->m.n - c->m.k) * c->m.alpha;

@@ -116,6 +116,52 @@ static int build_mbr(int n, int k, int d, int systematic, CodeMatrices &c, std::
   return kOk;
 }
 
+// Reed-Solomon (the comparison code of Sec. 4): node i stores the message
+// polynomial evaluated at g^i, Y = V Z with V[i][j] = g^(ij); any k of the
+// n <= 255 distinct points determine Z.  Systematic form G' = V V~^-1
+// (Sec. 3.2).  One block per node; node f is repaired from k helpers by
+// decoding and re-encoding its row, so Psi := G' (the rows the newcomer
+// inverts) and every helper sends its block (phi = 1).
+static int build_rs(int n, int k, int d, int systematic, CodeMatrices &c, std::string &err) {
+  if (k < 1 || n <= k || n > 255) {
+    err = "Reed-Solomon needs 1 <= k < n <= 255";
+    return kEInval;
+  }
+  if (d != k) {
+    err = "Reed-Solomon repair reads d = k helpers";
+    return kEInval;
+  }
+  c.n = n;
+  c.k = k;
+  c.d = k;
+  c.alpha = 1;
+  c.K = k;
+  c.N = n;
+  c.construction = kConsRs;
+  c.systematic = systematic;
+  c.G = Mat(n, k);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < k; j++) c.G.at(i, j) = gpow((unsigned)(i * j));
+  if (!systematic) {
+    c.Gcode = c.G;
+  } else {
+    Mat top(k, k), topinv;
+    std::copy(c.G.v.begin(), c.G.v.begin() + (size_t)k * k, top.v.begin());
+    if (!mat_inverse(top, topinv)) {
+      err = "the first k points do not determine the message";
+      return kEUnsupported;
+    }
+    c.Gcode = mat_mul(c.G, topinv);
+  }
+  c.psi = c.Gcode;
+  c.phi = Mat(n, 1);
+  for (int i = 0; i < n; i++) c.phi.at(i, 0) = 1;
+  c.lambda.assign(n, 0);
+  c.L.clear();
+  mark_unit_rows(c);
+  return kOk;
+}
+
 int build_code(int n, int k, int d, int construction, int systematic, CodeMatrices &c,
                std::string &err) {
   if (systematic != 0 && systematic != 1) {
@@ -123,6 +169,7 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
     return kEInval;
   }
   if (construction == kConsMbr) return build_mbr(n, k, d, systematic, c, err);
+  if (construction == kConsRs) return build_rs(n, k, d, systematic, c, err);
   if (k < 2 || d != 2 * k - 2) {
     err = "PM-MSR needs k >= 2 and d = 2k-2";
     return kEInval;
@@ -132,7 +179,7 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
     return kEInval;
   }
   if (construction != 0 && construction != 1) {
-    err = "construction must be PMRC_VANILLA, PMRC_SPARSE or PMRC_MBR";
+    err = "construction must be PMRC_VANILLA, PMRC_SPARSE, PMRC_MBR or PMRC_RS";
     return kEInval;
   }
   const int a = k - 1;
@@ -251,6 +298,17 @@ int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, st
   if (!mat_inverse(PH, inv)) {
     err = "the helpers' rows of Psi are singular for this failed node";
     return kESingular;
+  }
+  if (c.construction == kConsRs) {
+    // X = G'_H^-1 y_H, so node f's block is G'[f] G'_H^-1 y_H
+    D = Mat(1, c.d);
+    const auto &T = mul_table().t;
+    for (int q = 0; q < c.d; q++) {
+      uint8_t s = 0;
+      for (int l = 0; l < c.d; l++) s ^= T[c.psi.at(f, l)][inv.at(l, q)];
+      D.at(0, q) = s;
+    }
+    return kOk;
   }
   if (c.construction == kConsMbr) {
     // Psi_H M psi_f = p  =>  M psi_f = Psi_H^-1 p, and node f stores

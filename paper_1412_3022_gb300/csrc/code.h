@@ -7,6 +7,8 @@
 //   Sec. 3.3  Psi = [Phi  Lambda*Phi], vanilla (Vandermonde) and sparse
 //             (identity + Cauchy) constructions; helper read reduction
 //
+//   Sec. 4    Vandermonde Reed-Solomon baseline (construction 3): Y = V Z,
+//             V[i][j] = g^(ij), systematic G' = V V~^-1; one block per node
 //   Sec. 2    MBR point alpha = d, Delta = (2d-k+1)/2 (construction 2):
 //             M = [S T; T^t 0] symmetric d x d, Psi = [I_k 0; Cauchy]
 //             (Sec. 3.2: a systematic Psi = [I; Psi''] given directly)
@@ -44,11 +46,12 @@ Mat mat_mul(const Mat &A, const Mat &B);
 bool mat_inverse(const Mat &A, Mat &out);
 
 constexpr int kConsMbr = 2;  // construction id of the PM-MBR code
+constexpr int kConsRs = 3;   // Reed-Solomon baseline (Sec. 4), alpha = 1, d = k
 
 struct CodeMatrices {
   int n = 0, k = 0, d = 0, alpha = 0;
   int K = 0, N = 0;      // data blocks (k alpha for MSR, k Delta for MBR), n alpha
-  int construction = 0;  // 0 vanilla MSR, 1 sparse MSR, 2 MBR
+  int construction = 0;  // 0 vanilla MSR, 1 sparse MSR, 2 MBR, 3 Reed-Solomon
   int systematic = 0;
   Mat phi;      // n x alpha: the helper projection vectors (Phi for MSR, Psi for MBR)
   std::vector<uint8_t> lambda;  // n (MSR)

@@ -30,13 +30,14 @@ using namespace pmrc;
 namespace {
 
 struct Spec {
-  int n, k, construction, form;
+  int n, k, construction, form, d;
 };
 
-// the codes of the benchmarked workloads (n = 2k, d = 2k-2; construction 2
-// is PM-MBR)
+// the codes of the benchmarked workloads (n = 2k, d = 2k-2 for the PM codes;
+// construction 2 is PM-MBR, 3 the Reed-Solomon baseline with d = k)
 const Spec kSpecs[] = {
-    {16, 8, 1, 1}, {16, 8, 0, 0}, {8, 4, 1, 1}, {6, 3, 1, 1}, {6, 3, 0, 0}, {16, 8, 2, 1},
+    {16, 8, 1, 1, 14}, {16, 8, 0, 0, 14}, {8, 4, 1, 1, 6}, {6, 3, 1, 1, 4},
+    {6, 3, 0, 0, 4},   {16, 8, 2, 1, 14}, {16, 8, 3, 1, 8},
 };
 
 constexpr int kRows = 8;    // rows per block (8 x 8 bit-plane accumulators)
@@ -68,7 +69,7 @@ int main(int argc, char **argv) {
   for (const Spec &s : kSpecs) {
     CodeMatrices c;
     std::string err;
-    if (build_code(s.n, s.k, 2 * s.k - 2, s.construction, s.form, c, err)) {
+    if (build_code(s.n, s.k, s.d, s.construction, s.form, c, err)) {
       fprintf(stderr, "gen_bitslice: %s\n", err.c_str());
       return 1;
     }

@@ -37,8 +37,8 @@ size_t specific_workspace_blocks(const CodeMatrices &c) {
 int build_specific(const CodeMatrices &c, const int *nodes, bool precode,
                    const std::vector<char> &want, SpecificPlan &out, std::string &err) {
   const int k = c.k, a = c.alpha, K = k * a, N = c.n * a;
-  if (k - 1 != a) {
-    err = "the data collector needs alpha = k - 1";
+  if ((c.construction != 0 && c.construction != 1) || k - 1 != a) {
+    err = "the data collector is the PM-MSR one (alpha = k - 1)";
     return kEUnsupported;
   }
   const int nA = k * (k - 1), np = nA / 2, nUV = 2 * a * a;

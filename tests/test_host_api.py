@@ -205,3 +205,31 @@ def test_mbr_encode_plan_is_sparse():
     par = G[8 * 14:]
     st = P.pmrc_plan_stats(par)
     assert st["nnz"] == int((par != 0).sum()) == 8 * (8 * 14 + 6 * 8)
+
+
+# ------------------------------------------------------------ Reed-Solomon
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("n,k", [(6, 3), (9, 6), (16, 8), (32, 16)])
+def test_rs_matrices_match_oracle(n, k, form):
+    c = P.Code(n, k, P.PMRC_RS, form)
+    assert (c.alpha, c.d, c.data_blocks, c.coded_blocks) == (1, k, k, n)
+    assert np.array_equal(P.pmrc_code_generator(c.handle), O.rs_generator(n, k, bool(form)))
+    X = np.random.default_rng(n).integers(0, 256, (k, 3), dtype=np.uint8)
+    Y = O.rs_encode(n, k, bool(form), X)
+    rng = np.random.default_rng(k)
+    for f in range(n):
+        H = rng.permutation([h for h in range(n) if h != f])[:k].tolist()
+        assert list(P.pmrc_helper_coefficients(c.handle, f)) == [1]
+        D = P.pmrc_newcomer_matrix(c.handle, f, H)
+        assert np.array_equal(O.region_apply(D, Y[H])[0], O.rs_repair(n, k, bool(form), f, H, Y[H]))
+    for _ in range(5):
+        S = rng.permutation(rng.choice(n, k, replace=False)).tolist()
+        R = P.pmrc_decode_matrix(c.handle, S)
+        assert np.array_equal(O.region_apply(R, Y[S]), X)
+
+
+def test_rs_rejects_bad_parameters():
+    for n, k, d in [(8, 4, 6), (4, 4, 4), (300, 8, 8)]:
+        with pytest.raises(P.PMRCError) as e:
+            P.pmrc_create(n, k, d, P.PMRC_RS, 1)
+        assert e.value.rc == P.PMRC_EINVAL
