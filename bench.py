@@ -87,6 +87,9 @@ def parse():
     p.add_argument("--batch-stripes", type=int, default=4096)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-mbr", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the rows outside the step (fused repair, specific algorithms, "
+                        "PM-MBR, Reed-Solomon), e.g. for a launch list of the step alone")
     p.add_argument("--serve-requests", type=int, default=400,
                    help="requests per offered-load level")
     return p.parse_args()
@@ -156,6 +159,7 @@ class Workload:
     def __init__(self, torch, P, inputs, B, seed, device):
         self.t = torch
         self.P = P
+        self.seed = seed
         self.B = B
         a, K = A_, K_ * A_
         self.sysc = P.Code(N_, K_, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
@@ -222,8 +226,9 @@ class Workload:
         self.entries = {"decode": int(dec_st["entries"])}
         del np
 
-    def ops(self):
-        s, B, a, st = self, self.B, self.c_args, self.stream
+    def ops(self, stream=None):
+        s, B, a = self, self.B, self.c_args
+        st = self.stream if stream is None else stream
         return [
             ("gen_encode", lambda: s.genc.encode(a["x_ptrs"], a["gen_ptrs"], B, st)),
             ("sys_encode", lambda: s.sysc.encode(a["x_ptrs"], a["par_ptrs"], B, st)),
@@ -331,36 +336,37 @@ def run_ours(args, rank, world, local_rank):
         except (OSError, ValueError):
             pass
 
-    # the fused single-GPU repair (helper projections kept in scratch)
-    fused_ms = time_op(torch, stream, flush, args, lambda: W.sysc.repair(
-        W.f, W.c_H, W.c_args["helper_in"], W.c_args["node_ptrs"], B, W.stream))
-    per_op["repair_fused"] = {"ms": round(fused_ms, 4),
-                              "user_GBps": round(W.user["repair"] / (fused_ms * 1e-3) / 1e9, 2),
-                              "alg_bytes": W.alg["repair_fused"],
-                              "frac_hbm": round(W.alg["repair_fused"] / (fused_ms * 1e-3) / 1e9
-                                                / hbm, 4)}
-    # the paper's "specific" algorithms (Sec. 4) beside the linearized ones:
-    # data-collector decode of the same node set, precode systematic encode
-    ws_bytes = W.sysc.specific_workspace_bytes(B)
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    spec = {
-        "decode_specific": (lambda: W.sysc.decode_specific(
-            W.c_S, W.c_args["dec_in"], W.c_args["dec_out"], B, ws.data_ptr(), ws_bytes, W.stream),
-            "decode", W.user["decode"]),
-        "encode_precode": (lambda: W.sysc.encode_precode(
-            W.c_args["x_ptrs"], W.c_args["par_ptrs"], B, ws.data_ptr(), ws_bytes, W.stream),
-            "sys_encode", W.user["sys_encode"]),
-    }
-    for name, (fn, linear, user) in spec.items():
-        ms = time_op(torch, stream, flush, args, fn)
-        per_op[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
-                        "linear_op": linear, "linear_over_specific": round(op_ms[linear] / ms, 3),
-                        "launches": 5 if name == "encode_precode" else 4 + (W.decode_missing > 0)}
-    del ws
-    if not args.no_mbr:
-        per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
-        per_op.update(run_rs(torch, P, inputs, args, flush, stream, dev, hbm))
-    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world)
+    if not args.no_extra:
+        # the fused single-GPU repair (helper projections kept in scratch)
+        fused_ms = time_op(torch, stream, flush, args, lambda: W.sysc.repair(
+            W.f, W.c_H, W.c_args["helper_in"], W.c_args["node_ptrs"], B, W.stream))
+        per_op["repair_fused"] = {"ms": round(fused_ms, 4),
+                                  "user_GBps": round(W.user["repair"] / (fused_ms * 1e-3) / 1e9, 2),
+                                  "alg_bytes": W.alg["repair_fused"],
+                                  "frac_hbm": round(W.alg["repair_fused"] / (fused_ms * 1e-3) / 1e9
+                                                    / hbm, 4)}
+        # the paper's "specific" algorithms (Sec. 4) beside the linearized ones:
+        # data-collector decode of the same node set, precode systematic encode
+        ws_bytes = W.sysc.specific_workspace_bytes(B)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        spec = {
+            "decode_specific": (lambda: W.sysc.decode_specific(
+                W.c_S, W.c_args["dec_in"], W.c_args["dec_out"], B, ws.data_ptr(), ws_bytes, W.stream),
+                "decode", W.user["decode"]),
+            "encode_precode": (lambda: W.sysc.encode_precode(
+                W.c_args["x_ptrs"], W.c_args["par_ptrs"], B, ws.data_ptr(), ws_bytes, W.stream),
+                "sys_encode", W.user["sys_encode"]),
+        }
+        for name, (fn, linear, user) in spec.items():
+            ms = time_op(torch, stream, flush, args, fn)
+            per_op[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
+                            "linear_op": linear, "linear_over_specific": round(op_ms[linear] / ms, 3),
+                            "launches": 5 if name == "encode_precode" else 4 + (W.decode_missing > 0)}
+        del ws
+        if not args.no_mbr:
+            per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
+            per_op.update(run_rs(torch, P, inputs, args, flush, stream, dev, hbm))
+    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
     result = {
@@ -707,9 +713,13 @@ def run_serving(torch, P, inputs, args):
     return out
 
 
-def run_e2e(torch, W, args, dev, stream, dist=None, world=1):
+def run_e2e(torch, W, args, dev, stream, dist=None, world=1, inputs=None):
     """Same step through the public API with host buffers: pinned H2D of the
-    stripe, every operation, D2H of every block the step produced."""
+    stripe, every operation, D2H of every block the step produced.  Steps
+    are pipelined the way a streaming caller runs them: two device buffer
+    sets on three streams (copy in, compute, copy out), so the copies of one
+    step overlap the compute and copies of its neighbours; every step still
+    moves its own inputs in and all its results out."""
     B, K, a = W.B, K_ * A_, A_
     hx = torch.empty((K, B), dtype=torch.uint8).pin_memory()
     hx.copy_(W.X.cpu())
@@ -717,34 +727,51 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1):
     hout = torch.empty((out_rows, B), dtype=torch.uint8).pin_memory()
     present = {a * i + j for i in W.S if i < K_ for j in range(a)}
     missing = [r for r in range(K) if r not in present]
-    ops = W.ops()
+    sets = [W, Workload(torch, W.P, inputs, B, W.seed, dev)]   # same stripe, own buffers
+    s_in, s_comp, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+    opsets = [S.ops(int(s_comp.cuda_stream)) for S in sets]
+    ev_in = [torch.cuda.Event() for _ in sets]
+    ev_comp = [torch.cuda.Event() for _ in sets]
+    ev_out = [torch.cuda.Event() for _ in sets]
+    for e in ev_out:
+        e.record(s_out)
 
-    def step():
-        W.X.copy_(hx, non_blocking=True)
-        for _, fn in ops:
+    def step(i):
+        b = i % 2
+        S = sets[b]
+        s_in.wait_event(ev_out[b])           # buffers of step i-2 are free
+        with torch.cuda.stream(s_in):
+            S.X.copy_(hx, non_blocking=True)
+        ev_in[b].record(s_in)
+        s_comp.wait_event(ev_in[b])
+        for _, fn in opsets[b]:
             fn()
-        o = 0
-        hout[o:o + N_ * a].copy_(W.gen_out, non_blocking=True)
-        o += N_ * a
-        hout[o:o + K].copy_(W.Y[K:], non_blocking=True)
-        o += K
-        hout[o:o + a].copy_(W.node, non_blocking=True)
-        o += a
-        for r in missing:
-            hout[o].copy_(W.data_out[r], non_blocking=True)
-            o += 1
+        ev_comp[b].record(s_comp)
+        s_out.wait_event(ev_comp[b])
+        with torch.cuda.stream(s_out):
+            o = 0
+            hout[o:o + N_ * a].copy_(S.gen_out, non_blocking=True)
+            o += N_ * a
+            hout[o:o + K].copy_(S.Y[K:], non_blocking=True)
+            o += K
+            hout[o:o + a].copy_(S.node, non_blocking=True)
+            o += a
+            for r in missing:
+                hout[o].copy_(S.data_out[r], non_blocking=True)
+                o += 1
+        ev_out[b].record(s_out)
 
-    for _ in range(max(1, args.warmup)):
-        step()
+    for i in range(max(2, args.warmup)):
+        step(i)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
+    e0.record(s_in)
+    for i in range(args.steps):
+        step(i)
+    e1.record(s_out)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -752,7 +779,8 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1):
     user = sum(W.user.values())
     return {"value": round(whole_job_gbps(user, world, ms), 2), "unit": "GB/s",
             "ms_per_step": round(ms, 4), "h2d_bytes_per_step": K * B,
-            "d2h_bytes_per_step": out_rows * B}
+            "d2h_bytes_per_step": out_rows * B,
+            "pipeline": "2 buffer sets, 3 streams (H2D / compute / D2H)"}
 
 
 # ------------------------------------------------------------------ oracle
