@@ -19,7 +19,10 @@
 //     before the 16-byte store;
 //   * the split tables of every (input, row) coefficient of the block are
 //     precomputed in the plan and staged in shared memory; a zero
-//     coefficient has all-zero tables, so no coefficient needs a branch.
+//     coefficient has all-zero tables, so no coefficient needs a branch;
+//   * for blocks of one or two rows a CTA loops over several byte tiles (the
+//     tables are staged once per CTA), and blocks of few inputs load all of a
+//     tile's inputs before using the first.
 #include "gf256.h"
 #include "region.h"
 
@@ -70,8 +73,11 @@ __global__ void __launch_bounds__(kThreads)
     const uint64_t off = ((uint64_t)tile * kThreads + threadIdx.x) * kVec;
     if (off >= a.nbytes) continue;
     uint32_t acc[R][4];
-    mac_block<R>(acc, nin, nrows, R, s_tab4, s_tab1, k,
-                 [&](int i) { return load16(a.ptr[s_slot[i]], off, a.nbytes, vec); });
+    auto fetch = [&](int i) { return load16(a.ptr[s_slot[i]], off, a.nbytes, vec); };
+    if (R <= 2 && nin <= 8)
+      mac_block_preload<R>(acc, nin, nrows, R, s_tab4, s_tab1, k, fetch);
+    else
+      mac_block<R>(acc, nin, nrows, R, s_tab4, s_tab1, k, fetch);
 #pragma unroll
     for (int r = 0; r < R; r++) {
       if (r < nrows) {
@@ -98,7 +104,26 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   for (int i = 0; i < plan.nin; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
   for (int j = 0; j < plan.nout; j++) a.ptr[plan.nin + j] = out[j];
   for (int j = plan.nin + plan.nout; j < MAXP; j++) a.ptr[j] = nullptr;
-  const dim3 grid((unsigned)plan.blocks.size(), a.ntiles < 65535u ? a.ntiles : 65535u);
+  // blocks of one or two rows do little work per tile: their CTAs loop over
+  // several tiles (about two waves of CTAs in all) so the block's tables are
+  // staged once per CTA; bigger blocks keep one tile per CTA, which balances
+  // the tail better
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  }
+  const uint64_t nb = plan.blocks.size();
+  uint64_t gy = a.ntiles;
+  if (R <= 2) {
+    const uint64_t target = (uint64_t)sms * 8;  // 4 resident CTAs per SM, two waves
+    gy = (target + nb - 1) / nb;
+    if (gy > a.ntiles) gy = a.ntiles;
+  }
+  if (gy > 65535u) gy = 65535u;
+  if (gy < 1) gy = 1;
+  const dim3 grid((unsigned)nb, (unsigned)gy);
   const size_t smem = (size_t)plan.max_entries * 20 + (size_t)(plan.max_inputs + R) * 2 + 16;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(region_kernel<R, MAXP>,
