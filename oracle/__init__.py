@@ -27,6 +27,11 @@ Parity status per function (what pins it is in ``tests/test_oracle_pins.py``):
                              subsets at n = 16 recover the data exactly
   encode_precode             pinned: data as nodes 0..k-1 re-decodes to itself
                              and every k-subset of the result recovers the data
+  gf16_* (GF(2^16) variant)  pinned: the tower multiply against an
+                             independent GF(2^8) shift-and-reduce, w has
+                             trace 1 (no root), g has order 65535, inverses;
+                             linearization vs Psi M(X); repair from every
+                             helper set and decode from every k-subset (n <= 8)
   rs_*                       pinned: V Z is polynomial evaluation (Horner,
                              independent multiply); systematic identity top;
                              every k-subset decodes and every node repairs
@@ -86,6 +91,7 @@ def lib():
             path = build()
             L = ctypes.CDLL(path)
             u8p = ctypes.POINTER(ctypes.c_uint8)
+            u16p = ctypes.POINTER(ctypes.c_uint16)
             ip = ctypes.POINTER(ctypes.c_int)
             i, sz = ctypes.c_int, ctypes.c_size_t
             sig = {
@@ -126,6 +132,19 @@ def lib():
                 "or_rs_encode": (i, [i, i, i, u8p, u8p, sz]),
                 "or_rs_decode": (i, [i, i, i, ip, u8p, u8p, sz]),
                 "or_rs_repair": (i, [i, i, i, i, ip, u8p, u8p, sz]),
+                "or16_omega": (ctypes.c_uint8, []),
+                "or16_primitive": (ctypes.c_uint16, []),
+                "or16_gf_mul": (ctypes.c_uint16, [ctypes.c_uint16, ctypes.c_uint16]),
+                "or16_gf_inv": (ctypes.c_uint16, [ctypes.c_uint16]),
+                "or16_gf_pow_g": (ctypes.c_uint16, [i]),
+                "or16_phi_lambda": (i, [i, i, i, u16p, u16p]),
+                "or16_psi": (i, [i, i, i, u16p]),
+                "or16_code_generator": (i, [i, i, i, i, u16p]),
+                "or16_region_apply": (None, [i, i, u16p, u8p, u8p, sz]),
+                "or16_encode": (i, [i, i, i, i, u8p, u8p, sz]),
+                "or16_newcomer_matrix": (i, [i, i, i, i, ip, u16p]),
+                "or16_helper_coefficients": (i, [i, i, i, i, u16p]),
+                "or16_decode_matrix": (i, [i, i, i, i, ip, u16p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -457,3 +476,93 @@ def rs_repair(n: int, k: int, systematic: bool, f: int, helpers, helper_blocks: 
     _check(lib().or_rs_repair(n, k, int(systematic), f, _ip(h), _u8(helper_blocks), _u8(out),
                               helper_blocks.shape[1]), "rs_repair")
     return out[0]
+
+
+# ------------------------------------------------------------ GF(2^16)
+def _u16(a: np.ndarray):
+    assert a.dtype == np.uint16 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))
+
+
+def gf16_omega() -> int:
+    return int(lib().or16_omega())
+
+
+def gf16_primitive() -> int:
+    return int(lib().or16_primitive())
+
+
+def gf16_mul(a: int, b: int) -> int:
+    return int(lib().or16_gf_mul(a, b))
+
+
+def gf16_inv(a: int) -> int:
+    return int(lib().or16_gf_inv(a))
+
+
+def gf16_phi_lambda(n: int, k: int, construction: int):
+    d, a = params(n, k)
+    phi = np.zeros((n, a), np.uint16)
+    lam = np.zeros(n, np.uint16)
+    _check(lib().or16_phi_lambda(n, k, construction, _u16(phi), _u16(lam)), "gf16_phi_lambda")
+    return phi, lam
+
+
+def gf16_psi(n: int, k: int, construction: int) -> np.ndarray:
+    d, a = params(n, k)
+    P = np.zeros((n, d), np.uint16)
+    _check(lib().or16_psi(n, k, construction, _u16(P)), "gf16_psi")
+    return P
+
+
+def gf16_generator(n: int, k: int, construction: int, systematic: bool) -> np.ndarray:
+    d, a = params(n, k)
+    G = np.zeros((n * a, k * a), np.uint16)
+    _check(lib().or16_code_generator(n, k, construction, int(systematic), _u16(G)),
+           "gf16_generator")
+    return G
+
+
+def gf16_region_apply(M: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Y = M X over planar GF(2^16) blocks (rows of X: B bytes, B even)."""
+    M = np.ascontiguousarray(M, dtype=np.uint16)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    rows, cols = M.shape
+    assert X.shape[0] == cols and X.shape[1] % 2 == 0
+    Y = np.zeros((rows, X.shape[1]), np.uint8)
+    if X.shape[1]:
+        lib().or16_region_apply(rows, cols, _u16(M), _u8(X), _u8(Y), X.shape[1])
+    return Y
+
+
+def gf16_encode(n: int, k: int, construction: int, systematic: bool, data: np.ndarray) -> np.ndarray:
+    d, a = params(n, k)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    out = np.zeros((n * a, data.shape[1]), np.uint8)
+    _check(lib().or16_encode(n, k, construction, int(systematic), _u8(data), _u8(out),
+                             data.shape[1]), "gf16_encode")
+    return out
+
+
+def gf16_helper_coefficients(n: int, k: int, construction: int, f: int) -> np.ndarray:
+    d, a = params(n, k)
+    c = np.zeros(a, np.uint16)
+    _check(lib().or16_helper_coefficients(n, k, construction, f, _u16(c)), "gf16_helper_coefficients")
+    return c
+
+
+def gf16_newcomer_matrix(n: int, k: int, construction: int, f: int, helpers) -> np.ndarray:
+    d, a = params(n, k)
+    h = _ints(helpers)
+    D = np.zeros((a, d), np.uint16)
+    _check(lib().or16_newcomer_matrix(n, k, construction, f, _ip(h), _u16(D)), "gf16_newcomer_matrix")
+    return D
+
+
+def gf16_decode_matrix(n: int, k: int, construction: int, systematic: bool, nodes) -> np.ndarray:
+    d, a = params(n, k)
+    s = _ints(nodes)
+    R = np.zeros((k * a, k * a), np.uint16)
+    _check(lib().or16_decode_matrix(n, k, construction, int(systematic), _ip(s), _u16(R)),
+           "gf16_decode_matrix")
+    return R

@@ -1036,3 +1036,343 @@ int or_rs_repair(int n, int k, int systematic, int f, const int *helpers,
     free(G);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* GF(2^16) variant (Sec. 3.3: the validity of the sparse construction is    */
+/* also checked in GF(2^16), for k up to 64).  Reading: GF(2^16) is built as */
+/* the quadratic extension GF(2^8)[y]/(y^2 + y + w), w the smallest element  */
+/* of GF(2^8) of absolute trace 1 (so the polynomial has no root); an        */
+/* element a + b y is the 16-bit value a | b << 8, and g is the smallest      */
+/* value of multiplicative order 65535.  A block of B bytes holds B/2        */
+/* symbols in two byte planes: the low bytes a at [0, B/2), the high bytes b */
+/* at [B/2, B).  Constructions and operations are those above with g and the */
+/* arithmetic of this field.                                                 */
+/* ------------------------------------------------------------------------ */
+
+static uint8_t or16_w;
+static uint16_t or16_g;
+static uint16_t or16_exp[2 * 65535];
+static int or16_log[65536];
+static int or16_ready;
+
+static uint8_t or_trace(uint8_t a)
+{
+    uint8_t t = a, s = a;
+    for (int i = 1; i < 8; i++) {
+        t = or_gf_mul(t, t);
+        s ^= t;
+    }
+    return s;
+}
+
+/* (a0 + a1 y)(b0 + b1 y) with y^2 = y + w */
+static uint16_t or16_mul_direct(uint16_t x, uint16_t z)
+{
+    uint8_t a0 = (uint8_t)x, a1 = (uint8_t)(x >> 8), b0 = (uint8_t)z, b1 = (uint8_t)(z >> 8);
+    uint8_t hh = or_gf_mul(a1, b1);
+    uint8_t lo = or_add(or_gf_mul(a0, b0), or_gf_mul(or16_w, hh));
+    uint8_t hi = or_add(or_add(or_gf_mul(a1, b0), or_gf_mul(a0, b1)), hh);
+    return (uint16_t)(lo | (hi << 8));
+}
+
+static void or16_init(void)
+{
+    if (or16_ready)
+        return;
+    or_init();
+    or16_w = 0;
+    for (int a = 1; a < 256 && !or16_w; a++)
+        if (or_trace((uint8_t)a) == 1)
+            or16_w = (uint8_t)a;
+    for (int v = 2; v < 65536; v++) {
+        uint16_t p = 1;
+        int ord = 0;
+        for (int i = 1; i <= 65535; i++) {
+            p = or16_mul_direct(p, (uint16_t)v);
+            if (p == 1) {
+                ord = i;
+                break;
+            }
+        }
+        if (ord == 65535) {
+            or16_g = (uint16_t)v;
+            break;
+        }
+    }
+    uint16_t p = 1;
+    for (int i = 0; i < 65535; i++) {
+        or16_exp[i] = or16_exp[i + 65535] = p;
+        or16_log[p] = i;
+        p = or16_mul_direct(p, or16_g);
+    }
+    or16_log[0] = -1;
+    or16_ready = 1;
+}
+
+uint8_t or16_omega(void) { or16_init(); return or16_w; }
+uint16_t or16_primitive(void) { or16_init(); return or16_g; }
+
+uint16_t or16_gf_mul(uint16_t a, uint16_t b)
+{
+    or16_init();
+    if (!a || !b)
+        return 0;
+    return or16_exp[or16_log[a] + or16_log[b]];
+}
+
+uint16_t or16_gf_inv(uint16_t a)
+{
+    or16_init();
+    return a ? or16_exp[(65535 - or16_log[a]) % 65535] : 0;
+}
+
+uint16_t or16_gf_pow_g(int e)
+{
+    or16_init();
+    return or16_exp[e % 65535];
+}
+
+static int or16_invert(int m, const uint16_t *A, uint16_t *Ainv)
+{
+    uint16_t *W = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)m * 2 * m);
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < 2 * m; j++)
+            W[(size_t)i * 2 * m + j] = j < m ? A[(size_t)i * m + j] : (uint16_t)(j - m == i);
+    int rc = OR_OK;
+    for (int c = 0; c < m && rc == OR_OK; c++) {
+        int p = c;
+        while (p < m && W[(size_t)p * 2 * m + c] == 0)
+            p++;
+        if (p == m) {
+            rc = OR_ESINGULAR;
+            break;
+        }
+        for (int j = 0; j < 2 * m; j++) {
+            uint16_t t = W[(size_t)p * 2 * m + j];
+            W[(size_t)p * 2 * m + j] = W[(size_t)c * 2 * m + j];
+            W[(size_t)c * 2 * m + j] = t;
+        }
+        uint16_t inv = or16_gf_inv(W[(size_t)c * 2 * m + c]);
+        for (int j = 0; j < 2 * m; j++)
+            W[(size_t)c * 2 * m + j] = or16_gf_mul(W[(size_t)c * 2 * m + j], inv);
+        for (int r = 0; r < m; r++) {
+            uint16_t f = W[(size_t)r * 2 * m + c];
+            if (r == c || !f)
+                continue;
+            for (int j = 0; j < 2 * m; j++)
+                W[(size_t)r * 2 * m + j] ^= or16_gf_mul(f, W[(size_t)c * 2 * m + j]);
+        }
+    }
+    if (rc == OR_OK)
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++)
+                Ainv[(size_t)i * m + j] = W[(size_t)i * 2 * m + m + j];
+    free(W);
+    return rc;
+}
+
+/* Phi (n x alpha) and lambda (n) over GF(2^16), the same formulas as
+ * or_phi_lambda with this field's g. */
+int or16_phi_lambda(int n, int k, int construction, uint16_t *phi, uint16_t *lambda)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a) || n > 60000)
+        return OR_EINVAL;
+    or16_init();
+    if (construction == OR_VANILLA) {
+        for (int i = 0; i < n; i++) {
+            for (int j = 0; j < a; j++)
+                phi[i * a + j] = or16_gf_pow_g(i * j);
+            lambda[i] = or16_gf_pow_g(i * a);
+        }
+    } else {
+        for (int i = 1; i <= n; i++) {
+            uint16_t x = or16_gf_pow_g(i + a);
+            for (int j = 1; j <= a; j++)
+                phi[(i - 1) * a + (j - 1)] =
+                    i <= a ? (uint16_t)(i == j) : or16_gf_inv((uint16_t)(x ^ or16_gf_pow_g(j - 1)));
+            lambda[i - 1] = or16_gf_mul((uint16_t)(x ^ 1), or16_gf_inv((uint16_t)(x ^ or16_gf_pow_g(a))));
+        }
+    }
+    return OR_OK;
+}
+
+int or16_psi(int n, int k, int construction, uint16_t *psi)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    uint16_t *phi = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * a);
+    uint16_t *lam = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+    int rc = or16_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < a; j++) {
+                psi[i * d + j] = phi[i * a + j];
+                psi[i * d + a + j] = or16_gf_mul(lam[i], phi[i * a + j]);
+            }
+    free(phi);
+    free(lam);
+    return rc;
+}
+
+/* G (non-systematic) or G' = G G~^-1 (systematic) over GF(2^16). */
+int or16_code_generator(int n, int k, int construction, int systematic, uint16_t *Gout)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    int K = k * a, N = n * a;
+    uint16_t *psi = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * d);
+    int *L = (int *)malloc(sizeof(int) * d * a);
+    uint16_t *G = (uint16_t *)calloc((size_t)N * K, sizeof(uint16_t));
+    int rc = or16_psi(n, k, construction, psi);
+    if (rc == OR_OK) {
+        or_index_matrix(k, L);
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < a; j++)
+                for (int l = 0; l < d; l++)
+                    G[(size_t)(a * i + j) * K + L[l * a + j]] = psi[i * d + l];
+    }
+    if (rc == OR_OK && !systematic)
+        memcpy(Gout, G, sizeof(uint16_t) * (size_t)N * K);
+    if (rc == OR_OK && systematic) {
+        uint16_t *Ti = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)K * K);
+        rc = or16_invert(K, G, Ti);
+        if (rc == OR_OK)
+            for (int r = 0; r < N; r++)
+                for (int c = 0; c < K; c++) {
+                    uint16_t s = 0;
+                    for (int q = 0; q < K; q++)
+                        s ^= or16_gf_mul(G[(size_t)r * K + q], Ti[(size_t)q * K + c]);
+                    Gout[(size_t)r * K + c] = s;
+                }
+        free(Ti);
+    }
+    free(psi);
+    free(L);
+    free(G);
+    return rc;
+}
+
+/* Y = M X over planar GF(2^16) blocks of nbytes (even) bytes. */
+void or16_region_apply(int rows, int cols, const uint16_t *M, const uint8_t *in, uint8_t *out,
+                       size_t nbytes)
+{
+    size_t h = nbytes / 2;
+    for (int r = 0; r < rows; r++) {
+        uint8_t *y = out + (size_t)r * nbytes;
+        for (size_t t = 0; t < h; t++) {
+            uint16_t s = 0;
+            for (int c = 0; c < cols; c++) {
+                uint16_t m = M[(size_t)r * cols + c];
+                if (!m)
+                    continue;
+                const uint8_t *x = in + (size_t)c * nbytes;
+                s ^= or16_gf_mul(m, (uint16_t)(x[t] | (x[h + t] << 8)));
+            }
+            y[t] = (uint8_t)s;
+            y[h + t] = (uint8_t)(s >> 8);
+        }
+    }
+}
+
+int or16_encode(int n, int k, int construction, int systematic, const uint8_t *data, uint8_t *out,
+                size_t nbytes)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a) || nbytes % 2)
+        return OR_EINVAL;
+    int K = k * a, N = n * a;
+    uint16_t *G = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)N * K);
+    int rc = or16_code_generator(n, k, construction, systematic, G);
+    if (rc == OR_OK)
+        or16_region_apply(N, K, G, data, out, nbytes);
+    free(G);
+    return rc;
+}
+
+/* Repair (the PM repair of the section above, over GF(2^16)): helper h
+ * sends its alpha blocks projected on phi_f; D = [I | lambda_f I] Psi_H^-1. */
+int or16_newcomer_matrix(int n, int k, int construction, int f, const int *helpers, uint16_t *D)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a) || f < 0 || f >= n)
+        return OR_EINVAL;
+    for (int i = 0; i < d; i++) {
+        if (helpers[i] < 0 || helpers[i] >= n || helpers[i] == f)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (helpers[j] == helpers[i])
+                return OR_EINVAL;
+    }
+    uint16_t *psi = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * d);
+    uint16_t *PH = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)d * d);
+    uint16_t *PHi = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)d * d);
+    uint16_t *phi = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * a);
+    uint16_t *lam = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+    int rc = or16_psi(n, k, construction, psi);
+    if (rc == OR_OK)
+        rc = or16_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK) {
+        for (int i = 0; i < d; i++)
+            memcpy(PH + (size_t)i * d, psi + (size_t)helpers[i] * d, sizeof(uint16_t) * d);
+        rc = or16_invert(d, PH, PHi);
+    }
+    if (rc == OR_OK)
+        for (int j = 0; j < a; j++)
+            for (int c = 0; c < d; c++)
+                D[j * d + c] = PHi[j * d + c] ^ or16_gf_mul(lam[f], PHi[(a + j) * d + c]);
+    free(psi);
+    free(PH);
+    free(PHi);
+    free(phi);
+    free(lam);
+    return rc;
+}
+
+int or16_helper_coefficients(int n, int k, int construction, int f, uint16_t *coef)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a) || f < 0 || f >= n)
+        return OR_EINVAL;
+    uint16_t *phi = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * a);
+    uint16_t *lam = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+    int rc = or16_phi_lambda(n, k, construction, phi, lam);
+    if (rc == OR_OK)
+        memcpy(coef, phi + (size_t)f * a, sizeof(uint16_t) * a);
+    free(phi);
+    free(lam);
+    return rc;
+}
+
+/* Reconstruction: the inverse of the listed nodes' rows of the code's
+ * generator. */
+int or16_decode_matrix(int n, int k, int construction, int systematic, const int *nodes,
+                       uint16_t *Rinv)
+{
+    int d, a;
+    if (or_params(n, k, &d, &a))
+        return OR_EINVAL;
+    for (int i = 0; i < k; i++) {
+        if (nodes[i] < 0 || nodes[i] >= n)
+            return OR_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (nodes[j] == nodes[i])
+                return OR_EINVAL;
+    }
+    int K = k * a, N = n * a;
+    uint16_t *G = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)N * K);
+    uint16_t *GR = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)K * K);
+    int rc = or16_code_generator(n, k, construction, systematic, G);
+    if (rc == OR_OK) {
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < a; j++)
+                memcpy(GR + (size_t)(a * i + j) * K, G + (size_t)(a * nodes[i] + j) * K,
+                       sizeof(uint16_t) * K);
+        rc = or16_invert(K, GR, Rinv);
+    }
+    free(G);
+    free(GR);
+    return rc;
+}
