@@ -366,6 +366,7 @@ def run_ours(args, rank, world, local_rank):
         if not args.no_mbr:
             per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
             per_op.update(run_rs(torch, P, inputs, args, flush, stream, dev, hbm))
+            per_op.update(run_gf16(torch, P, inputs, args, flush, stream, dev, hbm))
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
@@ -495,6 +496,56 @@ def run_rs(torch, P, inputs, args, flush, stream, dev, hbm):
                      "block_bytes": B}
     out["rs_repair"]["failed_node"] = f
     out["rs_decode"].update({"nodes": S, "missing_rows": len(missing)})
+    torch.cuda.synchronize()
+    return out
+
+
+def run_gf16(torch, P, inputs, args, flush, stream, dev, hbm):
+    """GF(2^16) rows: the n=16 k=8 sparse systematic code over GF(2^16) on
+    the same 56 MiB stripe (blocks of two byte planes): encode, two-step
+    repair of a seeded node, lazy decode from a seeded 8-node set."""
+    n, k, B = 16, 8, args.block_bytes
+    a, K = k - 1, k * (k - 1)
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC, field_bits=16)
+    st = int(torch.cuda.current_stream(dev).cuda_stream)
+    Y = torch.empty((n * a, B), dtype=torch.uint8, device=dev)
+    Y[:K].copy_(inputs.device_blocks(K, B, args.seed + 99, device=dev))
+    x_arr = P.ptr_array([Y[i] for i in range(K)])
+    par_arr = P.ptr_array([Y[K + i] for i in range(K)])
+    c.encode(x_arr, par_arr, B)
+    f = inputs.failed_node(n, args.seed + 99)
+    H = c.default_helpers(f)
+    S = inputs.node_subset(n, k, args.seed + 99)
+    recv = torch.empty((2 * k - 2, B), dtype=torch.uint8, device=dev)
+    node = torch.empty((a, B), dtype=torch.uint8, device=dev)
+    Xr = torch.empty((K, B), dtype=torch.uint8, device=dev)
+    dec_in = [Y[a * i + j] for i in S for j in range(a)]
+    dec_out = [Xr[r] for r in range(K)]
+    for pos, i in enumerate(S):
+        if i < k:
+            for j in range(a):
+                dec_out[a * i + j] = dec_in[a * pos + j]
+    missing = sum(1 for i in range(k) if i not in S) * a
+    H_arr, S_arr = P.int_array(H), P.int_array(S)
+    h_in = P.ptr_array([Y[a * h + j] for h in H for j in range(a)])
+    r_arr, n_arr = P.ptr_array([recv[i] for i in range(2 * k - 2)]), P.ptr_array([node[j] for j in range(a)])
+    din, dout = P.ptr_array(dec_in), P.ptr_array(dec_out)
+
+    def repair():
+        c.repair_helpers(f, H_arr, h_in, r_arr, B, st)
+        c.repair_newcomer(f, H_arr, r_arr, n_arr, B, st)
+    ops = {
+        "gf16_sys_encode": (lambda: c.encode(x_arr, par_arr, B, st), K * B, 2 * K * B),
+        "gf16_repair": (repair, a * B, ((2 * k - 2) * a + 2 * (2 * k - 2) + a) * B),
+        "gf16_decode": (lambda: c.decode(S_arr, din, dout, B, st), K * B, (K + missing) * B),
+    }
+    out = {}
+    for name, (fn, user, alg) in ops.items():
+        ms = time_op(torch, stream, flush, args, fn)
+        out[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
+                     "alg_bytes": alg, "frac_hbm": round(alg / (ms * 1e-3) / 1e9 / hbm, 4)}
+    out["gf16_repair"]["failed_node"] = f
+    out["gf16_decode"].update({"nodes": S, "missing_rows": missing})
     torch.cuda.synchronize()
     return out
 

@@ -96,6 +96,21 @@ enum { PMRC_NONSYSTEMATIC = 0, PMRC_SYSTEMATIC = 1 };  /* Sec. 3.1 / Sec. 3.2 */
  * k helpers (helper coefficient 1) and applies G'[f] G'_H^-1. */
 int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out);
 
+/* pmrc_create over GF(2^8) (field_bits = 8, the same as pmrc_create) or
+ * GF(2^16) (field_bits = 16; PMRC_VANILLA / PMRC_SPARSE only).  GF(2^16) is
+ * the quadratic extension GF(2^8)[y]/(y^2 + y + w), w the smallest element
+ * of GF(2^8) of absolute trace 1; a + b y is the value a | b << 8 and g the
+ * smallest value of order 65535 (Sec. 3.3 checks the sparse construction in
+ * GF(2^16) for k up to 64; the vanilla code at k=16, n=32 is valid there).
+ * A block of B bytes (B even) holds B/2 symbols as two byte planes: the low
+ * bytes at [0, B/2), the high bytes at [B/2, B).  pmrc_encode,
+ * pmrc_repair_helper(s), pmrc_repair_newcomer and pmrc_decode take the same
+ * arguments as for GF(2^8) codes (B must be even); the other calls return
+ * PMRC_EUNSUPPORTED for GF(2^16) codes.  PMRC_EINVAL for another
+ * field_bits. */
+int pmrc_create_field(int n, int k, int d, int construction, int form, int field_bits,
+                      pmrc_code **out);
+
 /* Frees the handle and its device plans.  The caller makes sure no call on
  * it is still running on the GPU.  NULL is ignored. */
 void pmrc_destroy(pmrc_code *code);
@@ -363,6 +378,13 @@ int pmrc_code_params(const pmrc_code *code, int *params_out);
 /* Data blocks K (k alpha for PM-MSR, k Delta for PM-MBR) and coded blocks
  * n alpha: the pointer counts of encode (K in) and decode (K out). */
 int pmrc_code_blocks(const pmrc_code *code, int *data_blocks, int *coded_blocks);
+
+/* 8 or 16: the field of the code's symbols (0 if code is NULL). */
+int pmrc_code_field_bits(const pmrc_code *code);
+
+/* The generator of a GF(2^16) code (n*alpha x k*alpha, row-major, 16-bit
+ * values a | b << 8).  PMRC_EINVAL for a GF(2^8) code. */
+int pmrc_code_generator16(const pmrc_code *code, uint16_t *g_out);
 
 /* The code's generator, n*alpha x K, row-major: G (non-systematic) or
  * G' (systematic); for PM-MBR always G (already systematic). */

@@ -84,6 +84,9 @@ _SIGNATURES = {
     "pmrc_last_error": (ctypes.c_char_p, []),
     "pmrc_code_params": (_i, [_vp, _ip]),
     "pmrc_code_blocks": (_i, [_vp, _ip, _ip]),
+    "pmrc_create_field": (_i, [_i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "pmrc_code_field_bits": (_i, [_vp]),
+    "pmrc_code_generator16": (_i, [_vp, ctypes.POINTER(ctypes.c_uint16)]),
     "pmrc_code_generator": (_i, [_vp, _u8p]),
     "pmrc_helper_coefficients": (_i, [_vp, _i, _u8p]),
     "pmrc_newcomer_matrix": (_i, [_vp, _i, _ip, _u8p]),
@@ -272,6 +275,26 @@ def pmrc_code_params(code) -> dict:
     out = (ctypes.c_int * 6)()
     _check(lib().pmrc_code_params(code, out), "pmrc_code_params")
     return dict(zip(("n", "k", "d", "alpha", "construction", "form"), list(out)))
+
+
+def pmrc_create_field(n: int, k: int, d: int, construction: int, form: int,
+                      field_bits: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pmrc_create_field(n, k, d, construction, form, field_bits, ctypes.byref(h)),
+           "pmrc_create_field")
+    return int(h.value)
+
+
+def pmrc_code_field_bits(code) -> int:
+    return int(lib().pmrc_code_field_bits(code))
+
+
+def pmrc_code_generator16(code):
+    import numpy as np
+    K, N = pmrc_code_blocks(code)
+    buf = (ctypes.c_uint16 * (K * N))()
+    _check(lib().pmrc_code_generator16(code, buf), "pmrc_code_generator16")
+    return np.frombuffer(bytes(buf), dtype=np.uint16).reshape(N, K).copy()
 
 
 def pmrc_code_blocks(code):
@@ -523,12 +546,14 @@ class Code:
     """Owns a pmrc_code handle; methods are the C calls on it."""
 
     def __init__(self, n: int, k: int, construction: int = PMRC_SPARSE,
-                 form: int = PMRC_SYSTEMATIC, d: int = None):
-        """PM-MSR (PMRC_VANILLA / PMRC_SPARSE): d = 2k-2.  PM-MBR (PMRC_MBR):
-        any k <= d <= n-1 (default 2k-2).  Reed-Solomon (PMRC_RS): d = k."""
+                 form: int = PMRC_SYSTEMATIC, d: int = None, field_bits: int = 8):
+        """PM-MSR (PMRC_VANILLA / PMRC_SPARSE): d = 2k-2, over GF(2^8) or
+        (field_bits=16) GF(2^16).  PM-MBR (PMRC_MBR): any k <= d <= n-1
+        (default 2k-2).  Reed-Solomon (PMRC_RS): d = k."""
         if d is None:
             d = k if construction == PMRC_RS else 2 * k - 2
-        self.handle = pmrc_create(n, k, d, construction, form)
+        self.handle = pmrc_create_field(n, k, d, construction, form, field_bits)
+        self.field_bits = field_bits
         p = pmrc_code_params(self.handle)
         self.n, self.k, self.d, self.alpha = p["n"], p["k"], p["d"], p["alpha"]
         self.construction, self.form = construction, form

@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "libpmrc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["region.cu", "bitslice.cu", "repair.cu", "batch.cu", "serve.cu", "plan.cpp",
-           "code.cpp", "specific.cpp", "api.cpp"]
+           "code.cpp", "code16.cpp", "specific.cpp", "api.cpp"]
 
 
 def nvcc() -> str:
@@ -51,7 +51,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     gen = os.path.join(BUILD, "gen_bitslice")
     cxx = shutil.which("g++") or "g++"
     r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", gen,
-                        os.path.join(CSRC, "gen_bitslice.cpp"), os.path.join(CSRC, "code.cpp")],
+                        os.path.join(CSRC, "gen_bitslice.cpp"), os.path.join(CSRC, "code.cpp"),
+                        os.path.join(CSRC, "code16.cpp")],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"g++ failed on gen_bitslice:\n{r.stdout}\n{r.stderr}")

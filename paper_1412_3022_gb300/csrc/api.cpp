@@ -52,16 +52,17 @@ int helper_plan(const pmrc_code *c, int f, int nh, std::shared_ptr<Plan> &out,
   }
   const std::string key = "h:" + std::to_string(f) + ":" + std::to_string(nh);
   out = cached_plan(c, key, [&]() {
-    std::vector<uint8_t> coef;
-    helper_coefficients(c->m, f, coef);
-    const int a = c->m.alpha;
-    Mat M(nh, nh * a);  // block diagonal: helper h reads its own alpha blocks
-    std::vector<int> slot(nh);
-    for (int h = 0; h < nh; h++) {
-      for (int j = 0; j < a; j++) M.at(h, h * a + j) = coef[j];
-      slot[h] = h;
-    }
-    return make_plan(M, slot, nh);
+    Mat P;  // beta x alpha: the projection one helper applies to its blocks
+    helper_matrix(c->m, f, P);
+    const int a = c->m.alpha, b = c->m.beta;
+    Mat M(nh * b, nh * a);  // block diagonal: helper h reads its own alpha blocks
+    std::vector<int> slot(nh * b);
+    for (int h = 0; h < nh; h++)
+      for (int t = 0; t < b; t++) {
+        for (int j = 0; j < a; j++) M.at(h * b + t, h * a + j) = P.at(t, j);
+        slot[h * b + t] = h * b + t;
+      }
+    return make_plan(M, slot, nh * b);
   });
   return kOk;
 }
@@ -158,17 +159,65 @@ int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *no
 
 }  // namespace pmrc
 
+namespace {
+
+// GF(2^16) codes: user block i (B bytes, two byte planes) is the pair of
+// GF(2^8) sub-blocks 2i (low plane) and 2i + 1 (high plane) of B/2 bytes.
+std::vector<const uint8_t *> split_in(const uint8_t *const *p, int n, size_t half) {
+  std::vector<const uint8_t *> v(2 * (size_t)n);
+  for (int i = 0; i < n; i++) {
+    v[2 * i] = p[i];
+    v[2 * i + 1] = p[i] ? p[i] + half : nullptr;
+  }
+  return v;
+}
+
+std::vector<uint8_t *> split_out(uint8_t *const *p, int n, size_t half) {
+  std::vector<uint8_t *> v(2 * (size_t)n);
+  for (int i = 0; i < n; i++) {
+    v[2 * i] = p[i];
+    v[2 * i + 1] = p[i] ? p[i] + half : nullptr;
+  }
+  return v;
+}
+
+bool is16(const pmrc_code *c) { return c && c->m.w == 16; }
+
+int not_for16(const char *what) {
+  return fail(PMRC_EUNSUPPORTED, std::string(what) + " is not available for GF(2^16) codes");
+}
+
+int encode_body(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                size_t nbytes, pmrc_stream_t stream);
+int repair_helpers_body(const pmrc_code *c, int f, int nh, const int *helpers,
+                        const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
+                        pmrc_stream_t stream);
+int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
+                         const uint8_t *const *received, uint8_t *const *out, size_t nbytes,
+                         pmrc_stream_t stream);
+int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream);
+
+}  // namespace
+
 extern "C" {
 
 const char *pmrc_last_error(void) { return g_last_error.c_str(); }
 
 int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out) {
+  return pmrc_create_field(n, k, d, construction, form, 8, out);
+}
+
+int pmrc_create_field(int n, int k, int d, int construction, int form, int field_bits,
+                      pmrc_code **out) {
   if (!out) return fail(PMRC_EINVAL, "out is NULL");
   *out = nullptr;
+  if (field_bits != 8 && field_bits != 16) return fail(PMRC_EINVAL, "field_bits must be 8 or 16");
   std::unique_ptr<pmrc_code> c(new (std::nothrow) pmrc_code());
   if (!c) return fail(PMRC_ENOMEM, "out of host memory");
   std::string err;
-  int rc = build_code(n, k, d, construction, form, c->m, err);
+  int rc = field_bits == 16 ? build_code16(n, k, d, construction, form, c->m, err)
+                            : build_code(n, k, d, construction, form, c->m, err);
   if (rc) return fail(rc, err);
   const int K = c->m.K, N = c->m.N;
   // encode plan: all rows (non-systematic) or the parity nodes' rows
@@ -194,7 +243,7 @@ int pmrc_code_params(const pmrc_code *c, int *p) {
   p[0] = c->m.n;
   p[1] = c->m.k;
   p[2] = c->m.d;
-  p[3] = c->m.alpha;
+  p[3] = is16(c) ? c->m.f16.alpha : c->m.alpha;
   p[4] = c->m.construction;
   p[5] = c->m.systematic;
   return PMRC_OK;
@@ -202,19 +251,30 @@ int pmrc_code_params(const pmrc_code *c, int *p) {
 
 int pmrc_code_blocks(const pmrc_code *c, int *data_blocks, int *coded_blocks) {
   if (!c || !data_blocks || !coded_blocks) return fail(PMRC_EINVAL, "NULL argument");
-  *data_blocks = c->m.K;
-  *coded_blocks = c->m.N;
+  *data_blocks = is16(c) ? c->m.f16.K : c->m.K;
+  *coded_blocks = is16(c) ? c->m.f16.N : c->m.N;
+  return PMRC_OK;
+}
+
+int pmrc_code_field_bits(const pmrc_code *c) { return c ? c->m.w : 0; }
+
+int pmrc_code_generator16(const pmrc_code *c, uint16_t *g) {
+  if (!c || !g) return fail(PMRC_EINVAL, "NULL argument");
+  if (!is16(c)) return fail(PMRC_EINVAL, "not a GF(2^16) code");
+  memcpy(g, c->m.f16.Gcode.data(), c->m.f16.Gcode.size() * sizeof(uint16_t));
   return PMRC_OK;
 }
 
 int pmrc_code_generator(const pmrc_code *c, uint8_t *g) {
   if (!c || !g) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) return not_for16("pmrc_code_generator (use pmrc_code_generator16)");
   memcpy(g, c->m.Gcode.v.data(), c->m.Gcode.v.size());
   return PMRC_OK;
 }
 
 int pmrc_helper_coefficients(const pmrc_code *c, int f, uint8_t *coef) {
   if (!c || !coef) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) return not_for16("pmrc_helper_coefficients");
   if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
   std::vector<uint8_t> v;
   helper_coefficients(c->m, f, v);
@@ -224,6 +284,7 @@ int pmrc_helper_coefficients(const pmrc_code *c, int f, uint8_t *coef) {
 
 int pmrc_newcomer_matrix(const pmrc_code *c, int f, const int *helpers, uint8_t *d_out) {
   if (!c || !helpers || !d_out) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) return not_for16("pmrc_newcomer_matrix");
   Mat D;
   std::string err;
   int rc = newcomer_matrix(c->m, f, helpers, D, err);
@@ -234,6 +295,7 @@ int pmrc_newcomer_matrix(const pmrc_code *c, int f, const int *helpers, uint8_t 
 
 int pmrc_decode_matrix(const pmrc_code *c, const int *nodes, uint8_t *r_out) {
   if (!c || !nodes || !r_out) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) return not_for16("pmrc_decode_matrix");
   Mat R;
   std::string err;
   int rc = decode_matrix(c->m, nodes, R, err);
@@ -281,6 +343,23 @@ int pmrc_set_encode_kernel(pmrc_code *c, int which) {
 int pmrc_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
                 size_t nbytes, pmrc_stream_t stream) {
   if (!c || !data || !out) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) {
+    if (nbytes % 2) return fail(PMRC_EINVAL, "GF(2^16) blocks hold whole 2-byte symbols");
+    const auto &f = c->m.f16;
+    const int nout = c->m.systematic ? f.N - c->m.k * f.alpha : f.N;
+    auto in8 = split_in(data, f.K, nbytes / 2);
+    auto out8 = split_out(out, nout, nbytes / 2);
+    return encode_body(c, in8.data(), out8.data(), nbytes / 2, stream);
+  }
+  return encode_body(c, data, out, nbytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int encode_body(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                size_t nbytes, pmrc_stream_t stream) {
   std::string err;
   const Plan &P = *c->encode;
   size_t done = 0;
@@ -310,18 +389,16 @@ int pmrc_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
-int pmrc_repair_helpers(const pmrc_code *c, int f, int nh, const int *helpers,
+int repair_helpers_body(const pmrc_code *c, int f, int nh, const int *helpers,
                         const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
                         pmrc_stream_t stream) {
-  if (!c || !blocks || !out || nh <= 0 || (nh > 1 && !helpers))
-    return fail(PMRC_EINVAL, "NULL argument or nhelpers <= 0");
-  if (nh * (c->m.alpha + 1) > kMaxSlots) return fail(PMRC_EUNSUPPORTED, "too many helpers");
+  if (nh * (c->m.alpha + c->m.beta) > kMaxSlots) return fail(PMRC_EUNSUPPORTED, "too many helpers");
   if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
   if (helpers)
     for (int h = 0; h < nh; h++)
       if (helpers[h] < 0 || helpers[h] >= c->m.n || helpers[h] == f)
         return fail(PMRC_EINVAL, "helper id out of range or equal to the failed node");
-  for (int h = 0; h < nh; h++)
+  for (int h = 0; h < nh * c->m.beta; h++)
     if (!out[h]) return fail(PMRC_EINVAL, "output block is NULL");
   std::shared_ptr<Plan> p;
   std::string err;
@@ -329,6 +406,44 @@ int pmrc_repair_helpers(const pmrc_code *c, int f, int nh, const int *helpers,
   if (rc) return fail(rc, err);
   rc = launch_region(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
   return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
+                         const uint8_t *const *received, uint8_t *const *out, size_t nbytes,
+                         pmrc_stream_t stream) {
+  for (int j = 0; j < c->m.alpha; j++)
+    if (!out[j]) return fail(PMRC_EINVAL, "output block is NULL");
+  std::shared_ptr<Plan> p;
+  std::string err;
+  int rc = newcomer_plan(c, f, helpers, p, err);
+  if (rc) return fail(rc, err);
+  rc = launch_region(*p, received, out, nbytes, (cudaStream_t)stream, err);
+  return rc ? fail(rc, err) : PMRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmrc_repair_helpers(const pmrc_code *c, int f, int nh, const int *helpers,
+                        const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
+                        pmrc_stream_t stream) {
+  if (!c || !blocks || !out || nh <= 0 || (nh > 1 && !helpers))
+    return fail(PMRC_EINVAL, "NULL argument or nhelpers <= 0");
+  if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
+  if (helpers)
+    for (int h = 0; h < nh; h++)
+      if (helpers[h] < 0 || helpers[h] >= c->m.n || helpers[h] == f)
+        return fail(PMRC_EINVAL, "helper id out of range or equal to the failed node");
+  for (int h = 0; h < nh; h++)
+    if (!out[h]) return fail(PMRC_EINVAL, "output block is NULL");
+  if (is16(c)) {
+    if (nbytes % 2) return fail(PMRC_EINVAL, "GF(2^16) blocks hold whole 2-byte symbols");
+    auto in8 = split_in(blocks, nh * c->m.f16.alpha, nbytes / 2);
+    auto out8 = split_out(out, nh, nbytes / 2);
+    return repair_helpers_body(c, f, nh, helpers, in8.data(), out8.data(), nbytes / 2, stream);
+  }
+  return repair_helpers_body(c, f, nh, helpers, blocks, out, nbytes, stream);
 }
 
 int pmrc_repair_helper(const pmrc_code *c, int f, int helper, const uint8_t *const *blocks,
@@ -341,19 +456,21 @@ int pmrc_repair_newcomer(const pmrc_code *c, int f, const int *helpers,
                          const uint8_t *const *received, uint8_t *const *out, size_t nbytes,
                          pmrc_stream_t stream) {
   if (!c || !helpers || !received || !out) return fail(PMRC_EINVAL, "NULL argument");
-  for (int j = 0; j < c->m.alpha; j++)
-    if (!out[j]) return fail(PMRC_EINVAL, "output block is NULL");
-  std::shared_ptr<Plan> p;
-  std::string err;
-  int rc = newcomer_plan(c, f, helpers, p, err);
-  if (rc) return fail(rc, err);
-  rc = launch_region(*p, received, out, nbytes, (cudaStream_t)stream, err);
-  return rc ? fail(rc, err) : PMRC_OK;
+  if (is16(c)) {
+    if (nbytes % 2) return fail(PMRC_EINVAL, "GF(2^16) blocks hold whole 2-byte symbols");
+    for (int j = 0; j < c->m.f16.alpha; j++)
+      if (!out[j]) return fail(PMRC_EINVAL, "output block is NULL");
+    auto in8 = split_in(received, c->m.d, nbytes / 2);
+    auto out8 = split_out(out, c->m.f16.alpha, nbytes / 2);
+    return repair_newcomer_body(c, f, helpers, in8.data(), out8.data(), nbytes / 2, stream);
+  }
+  return repair_newcomer_body(c, f, helpers, received, out, nbytes, stream);
 }
 
 int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
                 uint8_t *const *out, size_t nbytes, pmrc_stream_t stream) {
   if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) return not_for16("pmrc_repair (fused)");
   if (c->m.alpha > 16) return fail(PMRC_EUNSUPPORTED, "pmrc_repair needs alpha <= 16");
   std::string err;
   if (c->m.construction == kConsRs) {
@@ -377,6 +494,7 @@ int pmrc_repair_noalloc(const pmrc_code *c, int f, const int *helpers,
                         const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
                         pmrc_stream_t stream) {
   if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
+  if (is16(c)) return not_for16("pmrc_repair_noalloc");
   if (c->m.alpha > 16) return fail(PMRC_EUNSUPPORTED, "pmrc_repair_noalloc needs alpha <= 16");
   std::shared_ptr<FusedRepairPlan> p;
   std::string err;
@@ -397,6 +515,21 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
       seen[nodes[i]] = 1;
     }
   }
+  if (is16(c)) {
+    if (nbytes % 2) return fail(PMRC_EINVAL, "GF(2^16) blocks hold whole 2-byte symbols");
+    auto in8 = split_in(node_blocks, c->m.k * c->m.f16.alpha, nbytes / 2);
+    auto out8 = split_out(data_out, c->m.f16.K, nbytes / 2);
+    return decode_body(c, nodes, in8.data(), out8.data(), nbytes / 2, stream);
+  }
+  return decode_body(c, nodes, node_blocks, data_out, nbytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
+                uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream) {
   std::vector<char> want;
   decode_wanted(c, nodes, node_blocks, data_out, want);
   std::shared_ptr<Plan> p;
@@ -407,8 +540,12 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 size_t pmrc_specific_workspace_bytes(const pmrc_code *c, size_t block_bytes) {
-  if (!c || c->m.construction > 1) return 0;  // PM-MSR only
+  if (!c || c->m.construction > 1 || is16(c)) return 0;  // PM-MSR over GF(2^8) only
   return specific_workspace_blocks(c->m) * specific_pitch(block_bytes);
 }
 
@@ -475,6 +612,7 @@ int pmrc_decode_specific(const pmrc_code *c, const int *nodes, const uint8_t *co
   if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
   if (c->m.construction > 1)
     return fail(PMRC_EUNSUPPORTED, "the data collector of this library is the PM-MSR one");
+  if (is16(c)) return not_for16("pmrc_decode_specific");
   {
     std::vector<char> seen(c->m.n, 0);
     for (int i = 0; i < c->m.k; i++) {
@@ -512,6 +650,7 @@ int pmrc_encode_precode(const pmrc_code *c, const uint8_t *const *data, uint8_t 
   if (!c || !data || !parity) return fail(PMRC_EINVAL, "NULL argument");
   if (c->m.construction > 1)
     return fail(PMRC_EUNSUPPORTED, "precode encode is the PM-MSR systematic construction");
+  if (is16(c)) return not_for16("pmrc_encode_precode");
   if (!c->m.systematic)
     return fail(PMRC_EINVAL, "precode encode produces a systematic code's parity");
   const int K = c->m.k * c->m.alpha, NP = (c->m.n - c->m.k) * c->m.alpha;

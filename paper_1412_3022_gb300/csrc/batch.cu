@@ -126,6 +126,10 @@ void finish_stripe(WorkStripe &s) {
 int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
                   size_t nbytes, WorkStripe &s, std::string &err) {
   s = WorkStripe();
+  if (c->m.w != 8) {
+    err = "batched and served operations take GF(2^8) codes";
+    return kEUnsupported;
+  }
   s.type = 0;
   s.plan = c->encode;
   for (int i = 0; i < s.plan->nin; i++) {
@@ -146,6 +150,10 @@ int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const
 int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
                   uint8_t *const *out, size_t nbytes, WorkStripe &s, std::string &err) {
   s = WorkStripe();
+  if (c->m.w != 8) {
+    err = "batched and served operations take GF(2^8) codes";
+    return kEUnsupported;
+  }
   if (c->m.alpha > 16) {
     err = "batched repair needs alpha <= 16";
     return kEUnsupported;
@@ -182,6 +190,10 @@ int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *
 int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                   uint8_t *const *data_out, size_t nbytes, WorkStripe &s, std::string &err) {
   s = WorkStripe();
+  if (c->m.w != 8) {
+    err = "batched and served operations take GF(2^8) codes";
+    return kEUnsupported;
+  }
   {
     std::vector<char> seen(c->m.n, 0);
     for (int i = 0; i < c->m.k; i++) {

@@ -54,7 +54,7 @@ bool mat_inverse(const Mat &A, Mat &out) {
 static uint8_t gpow(unsigned e) { return gf_pow(2, e % 255); }
 
 // Rows of Gcode that are unit vectors copy one data block verbatim.
-static void mark_unit_rows(CodeMatrices &c) {
+void mark_unit_rows(CodeMatrices &c) {
   c.unit_col.assign(c.N, -1);
   for (int r = 0; r < c.N; r++) {
     int col = -1, cnt = 0;
@@ -260,6 +260,15 @@ int build_code(int n, int k, int d, int construction, int systematic, CodeMatric
   return kOk;
 }
 
+void helper_matrix(const CodeMatrices &c, int f, Mat &P) {
+  if (c.w == 16) {
+    helper_matrix16(c, f, P);
+    return;
+  }
+  P = Mat(1, c.alpha);
+  for (int j = 0; j < c.alpha; j++) P.at(0, j) = c.phi.at(f, j);
+}
+
 void helper_coefficients(const CodeMatrices &c, int f, std::vector<uint8_t> &coef) {
   coef.assign(c.phi.v.begin() + (size_t)f * c.alpha, c.phi.v.begin() + (size_t)(f + 1) * c.alpha);
 }
@@ -292,6 +301,7 @@ int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, st
   }
   int rc = check_distinct(helpers, c.d, c.n, f, err, "helpers");
   if (rc) return rc;
+  if (c.w == 16) return newcomer_matrix16(c, f, helpers, D, err);
   Mat PH(c.d, c.d), inv;
   for (int i = 0; i < c.d; i++)
     for (int l = 0; l < c.d; l++) PH.at(i, l) = c.psi.at(helpers[i], l);
@@ -386,6 +396,7 @@ int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::strin
   int rc = check_distinct(nodes, c.k, c.n, -1, err, "nodes");
   if (rc) return rc;
   if (c.construction == kConsMbr) return decode_matrix_mbr(c, nodes, Rinv, err);
+  if (c.w == 16) return decode_matrix16(c, nodes, Rinv, err);
   const int a = c.alpha, K = c.k * a;
   if (!c.systematic) {
     Mat GR(K, K);
@@ -453,10 +464,18 @@ int default_helpers(const CodeMatrices &c, int f, int *out, std::string &err) {
   std::vector<int> idx(d);
   for (int i = 0; i < d; i++) idx[i] = i;
   for (int tries = 0; tries < 100000; tries++) {
-    Mat PH(d, d), inv;
-    for (int i = 0; i < d; i++)
-      for (int l = 0; l < d; l++) PH.at(i, l) = c.psi.at(surv[idx[i]], l);
-    if (mat_inverse(PH, inv)) {
+    bool ok;
+    if (c.w == 16) {
+      std::vector<int> h(d);
+      for (int i = 0; i < d; i++) h[i] = surv[idx[i]];
+      ok = helpers_invertible16(c, h.data());
+    } else {
+      Mat PH(d, d), inv;
+      for (int i = 0; i < d; i++)
+        for (int l = 0; l < d; l++) PH.at(i, l) = c.psi.at(surv[idx[i]], l);
+      ok = mat_inverse(PH, inv);
+    }
+    if (ok) {
       for (int i = 0; i < d; i++) out[i] = surv[idx[i]];
       return kOk;
     }

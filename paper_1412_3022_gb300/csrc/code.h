@@ -60,7 +60,31 @@ struct CodeMatrices {
   Mat G;        // N x K, linearized generator (Sec. 3.1)
   Mat Gcode;    // the code's generator: G, or G' = G G~^-1 when systematic (MSR)
   std::vector<int> unit_col;    // per row of Gcode: the data block it copies, or -1
+  // GF(2^16) codes (code16.cpp): the matrices above are the GF(2^8)
+  // expansion (two byte planes per user block, alpha/K/N doubled); the
+  // GF(2^16) originals are kept here.  beta = sub-blocks per helper projection.
+  int w = 8, beta = 1;
+  struct {
+    int alpha = 0, K = 0, N = 0;
+    std::vector<uint16_t> phi, lambda, psi, Gcode;
+  } f16;
 };
+
+void mark_unit_rows(CodeMatrices &c);
+
+// GF(2^16) (code16.cpp): construction and its expansion to GF(2^8) region
+// matrices; the repair and decode matrices of such a code, expanded.
+int build_code16(int n, int k, int d, int construction, int systematic, CodeMatrices &c,
+                 std::string &err);
+void expand16(const std::vector<uint16_t> &M, int rows, int cols, Mat &out);
+void helper_matrix16(const CodeMatrices &c, int f, Mat &P);
+bool helpers_invertible16(const CodeMatrices &c, const int *helpers);
+int newcomer_matrix16(const CodeMatrices &c, int f, const int *helpers, Mat &D, std::string &err);
+int decode_matrix16(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err);
+
+// The helper projection of node f as a beta x alpha matrix (1 x alpha
+// phi_f for GF(2^8) codes, its 2 x 2 expansion for GF(2^16)).
+void helper_matrix(const CodeMatrices &c, int f, Mat &P);
 
 // Builds every matrix of the code.  Returns kEInval for bad parameters,
 // kEUnsupported when the construction is not an MSR code in GF(2^8) at this

@@ -423,6 +423,7 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   if (!s || !q || !q->code || !q->in || !q->out || q->block_bytes == 0)
     return sfail(PMRC_EINVAL, "NULL argument or empty block");
   const pmrc_code *c = q->code;
+  if (c->m.w != 8) return sfail(PMRC_EUNSUPPORTED, "the server takes GF(2^8) codes");
   std::unique_ptr<Req> r(new (std::nothrow) Req());
   if (!r) return sfail(PMRC_ENOMEM, "out of host memory");
   r->op = q->op;

@@ -233,3 +233,37 @@ def test_rs_rejects_bad_parameters():
         with pytest.raises(P.PMRCError) as e:
             P.pmrc_create(n, k, d, P.PMRC_RS, 1)
         assert e.value.rc == P.PMRC_EINVAL
+
+
+# ------------------------------------------------------------ GF(2^16)
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("cons", [0, 1])
+@pytest.mark.parametrize("n,k", [(5, 3), (8, 4), (16, 8)])
+def test_gf16_generator_matches_oracle(n, k, cons, form):
+    c = P.Code(n, k, cons, form, field_bits=16)
+    assert P.pmrc_code_field_bits(c.handle) == 16
+    assert (c.alpha, c.data_blocks, c.coded_blocks) == (k - 1, k * (k - 1), n * (k - 1))
+    assert np.array_equal(P.pmrc_code_generator16(c.handle),
+                          O.gf16_generator(n, k, cons, bool(form)))
+
+
+def test_gf16_vanilla_k16_valid_and_errors():
+    c = P.Code(32, 16, P.PMRC_VANILLA, P.PMRC_SYSTEMATIC, field_bits=16)   # invalid in GF(2^8)
+    assert np.array_equal(P.pmrc_code_generator16(c.handle),
+                          O.gf16_generator(32, 16, O.VANILLA, True))
+    with pytest.raises(P.PMRCError) as e:
+        P.pmrc_create_field(8, 4, 6, P.PMRC_SPARSE, 1, 12)
+    assert e.value.rc == P.PMRC_EINVAL
+    with pytest.raises(P.PMRCError) as e:
+        P.pmrc_create_field(16, 8, 14, P.PMRC_MBR, 1, 16)
+    assert e.value.rc == P.PMRC_EINVAL
+    c = P.Code(8, 4, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC, field_bits=16)
+    with pytest.raises(P.PMRCError) as e:   # fused repair is GF(2^8) only
+        c.repair(5, c.default_helpers(5), [1] * 18, [1] * 3, 64)
+    assert e.value.rc == P.PMRC_EUNSUPPORTED
+    with pytest.raises(P.PMRCError) as e:   # whole 2-byte symbols
+        c.encode([1] * 12, [1] * 12, 63)
+    assert e.value.rc == P.PMRC_EINVAL
+    for f in range(8):
+        H = c.default_helpers(f)
+        O.gf16_newcomer_matrix(8, 4, O.SPARSE, f, H)   # the oracle agrees it is invertible
