@@ -39,7 +39,7 @@ struct RegionArgs {
   uint32_t idx_base;     // byte offset of the uint16 slot array in image
   uint32_t tab4_base;    // byte offset of the TabEntry array
   uint32_t tab1_base;    // byte offset of the T2 word array
-  uint32_t ntiles;       // ceil(nbytes / (kThreads * kVec))
+  uint32_t ntiles;       // ceil(nbytes / (blockDim.x * kVec))
   int aligned;           // every pointer is 16-byte aligned
   MulConsts k;
   uint8_t *ptr[MAXP];    // input slots, then output slots
@@ -58,19 +58,19 @@ __global__ void __launch_bounds__(kThreads)
     const uint4 *g4 = reinterpret_cast<const uint4 *>(a.image + a.tab4_base) + d.tab_off;
     const uint32_t *g1 = reinterpret_cast<const uint32_t *>(a.image + a.tab1_base) + d.tab_off;
     const uint16_t *idx = reinterpret_cast<const uint16_t *>(a.image + a.idx_base);
-    for (int i = threadIdx.x; i < nent; i += kThreads) {
+    for (int i = threadIdx.x; i < nent; i += blockDim.x) {
       s_tab4[i] = g4[i];
       s_tab1[i] = g1[i];
     }
-    for (int i = threadIdx.x; i < nin; i += kThreads) s_slot[i] = idx[d.in_off + i];
-    for (int i = threadIdx.x; i < nrows; i += kThreads) s_slot[nin + i] = idx[d.out_off + i];
+    for (int i = threadIdx.x; i < nin; i += blockDim.x) s_slot[i] = idx[d.in_off + i];
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) s_slot[nin + i] = idx[d.out_off + i];
   }
   __syncthreads();
 
   const MulConsts k = a.k;
   const bool vec = a.aligned != 0;
   for (uint32_t tile = blockIdx.y; tile < a.ntiles; tile += gridDim.y) {
-    const uint64_t off = ((uint64_t)tile * kThreads + threadIdx.x) * kVec;
+    const uint64_t off = ((uint64_t)tile * blockDim.x + threadIdx.x) * kVec;
     if (off >= a.nbytes) continue;
     uint32_t acc[R][4];
     auto fetch = [&](int i) { return load16(a.ptr[s_slot[i]], off, a.nbytes, vec); };
@@ -97,7 +97,21 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   a.idx_base = (uint32_t)plan.idx_base;
   a.tab4_base = (uint32_t)plan.tab4_base;
   a.tab1_base = (uint32_t)plan.tab1_base;
-  const uint64_t tile = (uint64_t)kThreads * kVec;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  }
+  const uint64_t nb = plan.blocks.size();
+  // launches of few blocks on short columns (a newcomer apply, say) would
+  // leave most SMs idle with 4 KiB tiles: they run 128-thread CTAs on 2 KiB
+  // tiles instead, twice as many
+  unsigned threads = kThreads;
+  if (nb * ((nbytes + (uint64_t)kThreads * kVec - 1) / ((uint64_t)kThreads * kVec)) <
+      (uint64_t)sms * 4)
+    threads = kThreads / 2;
+  const uint64_t tile = (uint64_t)threads * kVec;
   a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
   a.aligned = aligned ? 1 : 0;
   a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
@@ -108,13 +122,6 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   // several tiles (about two waves of CTAs in all) so the block's tables are
   // staged once per CTA; bigger blocks keep one tile per CTA, which balances
   // the tail better
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-  }
-  const uint64_t nb = plan.blocks.size();
   uint64_t gy = a.ntiles;
   if (R <= 2) {
     const uint64_t target = (uint64_t)sms * 8;  // 4 resident CTAs per SM, two waves
@@ -130,7 +137,7 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  region_kernel<R, MAXP><<<grid, kThreads, smem, st>>>(a);
+  region_kernel<R, MAXP><<<grid, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
