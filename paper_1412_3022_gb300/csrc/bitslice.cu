@@ -35,6 +35,7 @@
 #include <cstring>
 
 #include "bitslice.h"
+#include "device_info.h"
 
 namespace pmrc {
 namespace {
@@ -217,18 +218,12 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
   for (int j = 0; j < b.noutputs; j++) a.ptr[b.ninputs + j] = out[j];
   // one CTA per SM; each block gets CTAs in proportion to its cost, at
   // least one, and no more than it has warp tiles to hand out
-  static int sms = 0;
-  static bool smem_set[64] = {};
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-  }
+  static std::atomic<uint64_t> smem_set[kMaxDevices];
+  const int sms = current_sm_count();
   const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes;  // 80 KiB
-  if (!smem_set[id]) {
+  if (first_on_device(smem_set, id)) {
     cudaError_t e = cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    smem_set[id] = true;
   }
   const uint64_t units = (nbytes + kBsUnit - 1) / kBsUnit;
   const uint64_t cap = std::max<uint64_t>(1, (units + kBsThreads / 32 - 1) / (kBsThreads / 32));

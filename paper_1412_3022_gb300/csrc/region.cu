@@ -23,6 +23,7 @@
 //   * for blocks of one or two rows a CTA loops over several byte tiles (the
 //     tables are staged once per CTA), and blocks of few inputs load all of a
 //     tile's inputs before using the first.
+#include "device_info.h"
 #include "gf256.h"
 #include "region.h"
 
@@ -97,12 +98,7 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   a.idx_base = (uint32_t)plan.idx_base;
   a.tab4_base = (uint32_t)plan.tab4_base;
   a.tab1_base = (uint32_t)plan.tab1_base;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-  }
+  const int sms = current_sm_count();
   const uint64_t nb = plan.blocks.size();
   // launches of few blocks on short columns (a newcomer apply, say) would
   // leave most SMs idle with 4 KiB tiles: they run 128-thread CTAs on 2 KiB

@@ -15,6 +15,7 @@
 
 #include <cstring>
 
+#include "device_info.h"
 #include "gf256.h"
 #include "plan.h"
 #include "repair.h"
@@ -240,13 +241,7 @@ int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *cons
 }
 
 unsigned fused_repair_grid(uint32_t ntiles) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
-  }
-  const uint32_t cap = (uint32_t)sms * 2;
+  const uint32_t cap = (uint32_t)current_sm_count() * 2;
   return ntiles < cap ? (ntiles ? ntiles : 1) : cap;
 }
 
