@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--block-bytes", type=int, default=1 << 20)
     p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--ref-seconds", type=float, default=6.0,
+                   help="--impl reference: CPU seconds per step, at most")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -899,7 +901,7 @@ def run_reference(args, rank):
         return None
     # size each step so that warmup+steps stay within a few minutes
     budget = 150.0 / max(1, args.steps + args.warmup)
-    cols = calibrate_cols(min(budget, 6.0), args.seed)
+    cols = calibrate_cols(min(budget, args.ref_seconds), args.seed)
     O, X, Y, f, H, S = oracle_sample(cols, args.seed)
     for _ in range(args.warmup):
         oracle_step(O, X, Y, f, H, S)
