@@ -255,6 +255,19 @@ int pmrc_encode_precode(const pmrc_code *code, const uint8_t *const *data,
 enum { PMRC_KERNEL_AUTO = 0, PMRC_KERNEL_GENERIC = 1, PMRC_KERNEL_BITSLICED = 2 };
 int pmrc_set_encode_kernel(pmrc_code *code, int which);
 
+/* Reconstruction kernel of a handle (GF(2^8) codes).  PMRC_KERNEL_AUTO
+ * (default): for blocks of at least 256 KiB, a bitsliced kernel generated
+ * for the call's decode rows and compiled at run time (NVRTC, loaded on
+ * demand) on the first reconstruction of each (node set, wanted rows) --
+ * about a second, part of the per-failure-pattern initialization that
+ * Sec. 4 reports apart from throughput -- then cached in the handle; the
+ * split-table kernel otherwise, and whenever the run-time kernel cannot be
+ * built (NVRTC missing, blocks not 16-byte aligned, or more than 64 inputs
+ * per 8-row block).  PMRC_KERNEL_GENERIC: always the split-table kernel.
+ * PMRC_KERNEL_BITSLICED: the run-time kernel at any size, PMRC_EUNSUPPORTED
+ * from pmrc_decode when it cannot be built.  Results are identical. */
+int pmrc_set_decode_kernel(pmrc_code *code, int which);
+
 /* ---- batched execution ---------------------------------------------------
  * Many stripes (any mix of codes, block sizes and operations) run by one
  * persistent kernel replayed from a CUDA graph.  The same per-stripe results

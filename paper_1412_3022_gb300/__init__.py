@@ -84,6 +84,7 @@ _SIGNATURES = {
     "pmrc_last_error": (ctypes.c_char_p, []),
     "pmrc_code_params": (_i, [_vp, _ip]),
     "pmrc_code_blocks": (_i, [_vp, _ip, _ip]),
+    "pmrc_set_decode_kernel": (_i, [_vp, _i]),
     "pmrc_create_field": (_i, [_i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
     "pmrc_code_field_bits": (_i, [_vp]),
     "pmrc_code_generator16": (_i, [_vp, ctypes.POINTER(ctypes.c_uint16)]),
@@ -254,6 +255,10 @@ def pmrc_encode_precode(code, data, parity, block_bytes, workspace, workspace_by
     _check(lib().pmrc_encode_precode(code, _ptrs(data), _ptrs(parity), block_bytes,
                                      _addr(workspace), workspace_bytes, _stream(stream)),
            "pmrc_encode_precode")
+
+
+def pmrc_set_decode_kernel(code, which: int) -> None:
+    _check(lib().pmrc_set_decode_kernel(code, which), "pmrc_set_decode_kernel")
 
 
 def pmrc_set_encode_kernel(code, which: int) -> None:
@@ -612,6 +617,9 @@ class Code:
             workspace_bytes = int(workspace.numel() * workspace.element_size())
         pmrc_encode_precode(self.handle, data, parity, block_bytes, workspace, workspace_bytes,
                             stream)
+
+    def set_decode_kernel(self, which: int):
+        pmrc_set_decode_kernel(self.handle, which)
 
     def set_encode_kernel(self, which: int):
         pmrc_set_encode_kernel(self.handle, which)

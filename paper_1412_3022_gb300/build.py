@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "libpmrc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["region.cu", "bitslice.cu", "repair.cu", "batch.cu", "serve.cu", "plan.cpp",
-           "code.cpp", "code16.cpp", "specific.cpp", "api.cpp"]
+           "code.cpp", "code16.cpp", "specific.cpp", "bs_emit.cpp", "jit.cpp", "api.cpp"]
 
 
 def nvcc() -> str:
@@ -51,14 +51,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     gen = os.path.join(BUILD, "gen_bitslice")
     cxx = shutil.which("g++") or "g++"
     r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", gen,
-                        os.path.join(CSRC, "gen_bitslice.cpp"), os.path.join(CSRC, "code.cpp"),
-                        os.path.join(CSRC, "code16.cpp")],
+                        os.path.join(CSRC, "gen_bitslice.cpp"), os.path.join(CSRC, "bs_emit.cpp"),
+                        os.path.join(CSRC, "code.cpp"), os.path.join(CSRC, "code16.cpp")],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"g++ failed on gen_bitslice:\n{r.stdout}\n{r.stderr}")
     r = subprocess.run([gen, os.path.join(BUILD, "bitslice_gen.cuh")], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"gen_bitslice failed:\n{r.stdout}\n{r.stderr}")
+    # 2. the bitsliced device code as a string, for run-time compilation
+    with open(os.path.join(CSRC, "bitslice_dev.cuh")) as f:
+        dev_src = f.read()
+    if ")BSDEV\"" in dev_src:
+        raise RuntimeError("bitslice_dev.cuh contains the raw-string delimiter")
+    with open(os.path.join(BUILD, "bitslice_dev_src.inc"), "w") as f:
+        f.write('static const char kBsDevSrc[] = R"BSDEV(' + dev_src + ')BSDEV";\n')
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + BUILD]
 
@@ -77,7 +84,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = OUT + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -161,6 +161,13 @@ int decode_wanted(const pmrc_code *c, const int *nodes, const uint8_t *const *no
 
 namespace {
 
+// reconstruction through run-time bitsliced kernels: AUTO uses them for
+// blocks of at least this many bytes (the compilation, about a second per
+// node set, is paid once per handle), and for reconstructions whose blocks
+// read at most this many inputs
+constexpr size_t kRuntimeMinBytes = 256 << 10;
+constexpr int kRuntimeMaxInputs = 64;
+
 // GF(2^16) codes: user block i (B bytes, two byte planes) is the pair of
 // GF(2^8) sub-blocks 2i (low plane) and 2i + 1 (high plane) of B/2 bytes.
 std::vector<const uint8_t *> split_in(const uint8_t *const *p, int n, size_t half) {
@@ -329,6 +336,14 @@ int pmrc_default_helpers(const pmrc_code *c, int f, int *helpers_out) {
   std::string err;
   int rc = default_helpers(c->m, f, helpers_out, err);
   return rc ? fail(rc, err) : PMRC_OK;
+}
+
+int pmrc_set_decode_kernel(pmrc_code *c, int which) {
+  if (!c) return fail(PMRC_EINVAL, "NULL argument");
+  if (which != PMRC_KERNEL_AUTO && which != PMRC_KERNEL_GENERIC && which != PMRC_KERNEL_BITSLICED)
+    return fail(PMRC_EINVAL, "unknown kernel choice");
+  c->decode_kernel = which;
+  return PMRC_OK;
 }
 
 int pmrc_set_encode_kernel(pmrc_code *c, int which) {
@@ -528,6 +543,44 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
 
 namespace {
 
+// Bitsliced reconstruction compiled at run time for this (nodes, wanted
+// rows), cached in the handle; null when the pattern is not eligible or the
+// build failed (the reason in err).
+std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *nodes,
+                                                const std::vector<char> &want,
+                                                std::string &err) {
+  std::string key;
+  for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
+  key += ":";
+  for (char w : want) key += w ? '1' : '0';
+  std::lock_guard<std::mutex> g(c->jit_mu);
+  {
+    std::lock_guard<std::mutex> g2(c->mu);
+    auto it = c->rt.find(key);
+    if (it != c->rt.end()) {
+      if (!it->second) err = c->rt_err[key];
+      return it->second;
+    }
+  }
+  std::shared_ptr<BsRuntimeKernel> k;
+  Mat R;
+  int rc = decode_matrix(c->m, nodes, R, err);
+  if (!rc) {
+    std::vector<int> rows;
+    for (int r = 0; r < c->m.K; r++)
+      if (want[r]) rows.push_back(r);
+    Mat M((int)rows.size(), R.cols);
+    for (size_t q = 0; q < rows.size(); q++)
+      for (int col = 0; col < R.cols; col++) M.at((int)q, col) = R.at(rows[q], col);
+    if (!rows.empty()) rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, k, err);
+  }
+  std::lock_guard<std::mutex> g2(c->mu);
+  if (c->rt.size() >= kPlanCacheCap) c->rt.erase(c->rt.begin());
+  c->rt[key] = k;
+  if (!k) c->rt_err[key] = err;
+  return k;
+}
+
 int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream) {
   std::vector<char> want;
@@ -536,7 +589,50 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
   std::string err;
   int rc = decode_plan(c, nodes, want, p, err);
   if (rc) return fail(rc, err);
-  rc = launch_region(*p, node_blocks, data_out, nbytes, (cudaStream_t)stream, err);
+  for (const auto &blk : p->blocks)
+    for (uint16_t in : blk.inputs)
+      if (!node_blocks[in]) return fail(PMRC_EINVAL, "a node block the reconstruction reads is NULL");
+  const cudaStream_t st = (cudaStream_t)stream;
+  size_t done = 0;
+  // bitsliced path: reconstruction rows compiled at run time (GF(2^8)
+  // codes; AUTO for blocks of at least kRuntimeMinBytes)
+  const bool forced = c->decode_kernel == PMRC_KERNEL_BITSLICED;
+  const bool want_rt = c->m.w == 8 && nbytes >= 32 &&
+                       (forced || (c->decode_kernel == PMRC_KERNEL_AUTO && nbytes >= kRuntimeMinBytes));
+  if (want_rt) {
+    std::vector<int> rows;
+    for (int r = 0; r < c->m.K; r++)
+      if (want[r]) rows.push_back(r);
+    const int KA = c->m.k * c->m.alpha;
+    bool aligned = !rows.empty();
+    for (int i = 0; i < KA && aligned; i++)
+      aligned = !node_blocks[i] || (uintptr_t)node_blocks[i] % 16 == 0;
+    for (int r : rows) aligned = aligned && (uintptr_t)data_out[r] % 16 == 0;
+    std::string rerr;
+    std::shared_ptr<BsRuntimeKernel> k = aligned ? decode_runtime(c, nodes, want, rerr) : nullptr;
+    if (!k && forced)
+      return fail(PMRC_EUNSUPPORTED, aligned ? "bitsliced reconstruction: " + rerr
+                                             : "bitsliced reconstruction needs 16-byte aligned blocks");
+    if (k) {
+      std::vector<uint8_t *> outs;
+      for (int r : rows) outs.push_back(data_out[r]);
+      done = nbytes & ~(size_t)31;
+      const cudaError_t e = bitslice_launch_runtime(*k, node_blocks, outs.data(), done, st);
+      if (e != cudaSuccess)
+        return fail(PMRC_ECUDA, std::string("bitsliced reconstruction launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (done == nbytes) return PMRC_OK;
+  if (done == 0) {
+    rc = launch_region(*p, node_blocks, data_out, nbytes, st, err);
+  } else {  // ragged tail of the blocks
+    const int KA = c->m.k * c->m.alpha;
+    std::vector<const uint8_t *> in2(KA);
+    std::vector<uint8_t *> out2(c->m.K);
+    for (int i = 0; i < KA; i++) in2[i] = node_blocks[i] ? node_blocks[i] + done : nullptr;
+    for (int r = 0; r < c->m.K; r++) out2[r] = data_out[r] ? data_out[r] + done : nullptr;
+    rc = launch_region(*p, in2.data(), out2.data(), nbytes - done, st, err);
+  }
   return rc ? fail(rc, err) : PMRC_OK;
 }
 

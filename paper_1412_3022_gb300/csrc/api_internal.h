@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "bitslice.h"
 #include "code.h"
 #include "plan.h"
 #include "repair.h"
@@ -22,6 +23,12 @@ struct pmrc_code {
   mutable std::map<std::string, std::shared_ptr<pmrc::Plan>> cache;
   mutable std::map<std::string, std::shared_ptr<pmrc::FusedRepairPlan>> fused;
   mutable std::map<std::string, std::shared_ptr<pmrc::SpecificPlan>> specific;
+  // reconstruction kernels compiled at run time, per (nodes, wanted rows);
+  // a null kernel records a pattern that could not be built
+  int decode_kernel = 0;                    // PMRC_KERNEL_*
+  mutable std::mutex jit_mu;                // one compilation at a time per handle
+  mutable std::map<std::string, std::shared_ptr<pmrc::BsRuntimeKernel>> rt;
+  mutable std::map<std::string, std::string> rt_err;
 };
 
 namespace pmrc {

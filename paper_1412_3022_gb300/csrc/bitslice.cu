@@ -32,142 +32,20 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <vector>
 
 #include "bitslice.h"
+#include "bs_emit.h"
+#include "code.h"
 #include "device_info.h"
+#include "jit.h"
 
 namespace pmrc {
 namespace {
 
-constexpr int kBsThreads = 512;       // one CTA per SM (128 registers a thread)
-constexpr int kBsBytes = 32;          // bytes per thread per tile
-constexpr int kBsMaxPtr = 256;
-constexpr int kBsAhead = 4;           // inputs prefetched ahead of the one in use
-constexpr int kBsSlots = kBsAhead + 1;  // shared-memory ring (never the slot being read)
-constexpr uint32_t kBsUnit = 32 * kBsBytes;  // bytes of column per warp tile
-constexpr int kBsMaxBlocks = 32;
-
-struct BsArgs {
-  uint64_t nbytes;  // bytes covered by this launch (multiple of kBsBytes)
-  uint32_t hi28, hi30, hi31;  // 2^28, 2^30, 2^31: right shifts as multiply-high
-  uint32_t x16, x4, x2;       // left shifts as multiplies
-  uint16_t cta_start[kBsMaxBlocks + 1];  // CTAs [cta_start[b], cta_start[b+1]) run block b
-  uint8_t *ptr[kBsMaxPtr];    // K input blocks, then the output blocks
-};
-
-struct BsCtx {
-  const BsArgs *a;
-  uint64_t off;
-};
-
-__device__ __forceinline__ bool bs_ctx(const BsArgs &a, BsCtx &x, uint32_t unit) {
-  x.a = &a;
-  x.off = (uint64_t)unit * kBsUnit + (threadIdx.x % 32) * kBsBytes;
-  return x.off < a.nbytes;
-}
-
-__device__ __forceinline__ void bs_zero(uint32_t (&acc)[8][8]) {
-#pragma unroll
-  for (int r = 0; r < 8; r++)
-#pragma unroll
-    for (int i = 0; i < 8; i++) acc[r][i] = 0;
-}
-
-// 8x8 bit transpose inside each byte lane of 8 words: afterwards word i
-// holds bit i of the 32 bytes (bit 8m+j = bit i of byte m of word j).  The
-// transform is an involution.  Each stage exchanges the bit fields `mask` of
-// the lower word with the fields `mask << s` of the upper one: both words are
-// rebuilt as a select between the word and a shifted copy of its partner (one
-// 3-input logic op each); the shifts run as multiplies on the FMA pipe.
-__device__ __forceinline__ void bs_transpose(uint32_t (&w)[8], const BsArgs &a) {
-#pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const uint32_t sl = __umulhi(w[j], a.hi28), sh = w[j + 4] * a.x16;
-    w[j + 4] = (sl & 0x0F0F0F0Fu) | (w[j + 4] & ~0x0F0F0F0Fu);
-    w[j] = (sh & 0xF0F0F0F0u) | (w[j] & ~0xF0F0F0F0u);
-  }
-#pragma unroll
-  for (int j = 0; j < 8; j += 4)
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-      const uint32_t sl = __umulhi(w[j + q], a.hi30), sh = w[j + q + 2] * a.x4;
-      w[j + q + 2] = (sl & 0x33333333u) | (w[j + q + 2] & ~0x33333333u);
-      w[j + q] = (sh & 0xCCCCCCCCu) | (w[j + q] & ~0xCCCCCCCCu);
-    }
-#pragma unroll
-  for (int j = 0; j < 8; j += 2) {
-    const uint32_t sl = __umulhi(w[j], a.hi31), sh = w[j + 1] * a.x2;
-    w[j + 1] = (sl & 0x55555555u) | (w[j + 1] & ~0x55555555u);
-    w[j] = (sh & 0xAAAAAAAAu) | (w[j] & ~0xAAAAAAAAu);
-  }
-}
-
-// Asynchronous copy of this thread's 32 bytes of input `col` into ring slot
-// `slot` of the shared-memory staging area (cp.async, one commit group per
-// input).  Each thread reads back only what it copied, so no barrier is
-// needed; cp.async.wait_group orders the read after the copy.
-__device__ __forceinline__ void bs_prefetch(const BsCtx &x, int col, int slot) {
-  extern __shared__ __align__(16) uint8_t bs_smem[];
-  const uint8_t *src = x.a->ptr[col] + x.off;
-  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(
-      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16), "l"(src + 16)
-               : "memory");
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// An empty commit group: keeps the number of groups in flight the same for
-// every input of a block shorter than the prefetch distance.
-__device__ __forceinline__ void bs_commit_empty() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void bs_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void bs_planes(const BsCtx &x, int slot, uint32_t (&Q)[16],
-                                          uint32_t (&R)[16]) {
-  extern __shared__ __align__(16) uint8_t bs_smem[];
-  const uint4 *p = reinterpret_cast<const uint4 *>(
-      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
-  const uint4 u = p[0], v = p[1];
-  uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
-  bs_transpose(w, *x.a);
-  Q[0] = 0;
-  Q[1] = w[0];
-  Q[2] = w[1];
-  Q[3] = w[0] ^ w[1];
-  Q[4] = w[2];
-  Q[5] = w[2] ^ w[0];
-  Q[6] = w[2] ^ w[1];
-  Q[7] = w[2] ^ Q[3];
-  Q[8] = w[3];
-#pragma unroll
-  for (int s = 9; s < 16; s++) Q[s] = w[3] ^ Q[s - 8];
-  R[0] = 0;
-  R[1] = w[4];
-  R[2] = w[5];
-  R[3] = w[4] ^ w[5];
-  R[4] = w[6];
-  R[5] = w[6] ^ w[4];
-  R[6] = w[6] ^ w[5];
-  R[7] = w[6] ^ R[3];
-  R[8] = w[7];
-#pragma unroll
-  for (int s = 9; s < 16; s++) R[s] = w[7] ^ R[s - 8];
-}
-
-__device__ __forceinline__ void bs_store(const BsCtx &x, int slot, uint32_t (&planes)[8]) {
-  uint32_t w[8];
-#pragma unroll
-  for (int i = 0; i < 8; i++) w[i] = planes[i];
-  bs_transpose(w, *x.a);
-  uint4 *p = reinterpret_cast<uint4 *>(x.a->ptr[slot] + x.off);
-  __stcs(p, make_uint4(w[0], w[1], w[2], w[3]));
-  __stcs(p + 1, make_uint4(w[4], w[5], w[6], w[7]));
-}
+#include "bitslice_dev.cuh"
 
 struct BsKernel {
   int n, k, construction, form;
@@ -202,9 +80,14 @@ int bitslice_find(int n, int k, int construction, int form, uint64_t checksum) {
 
 long long bitslice_xors(int id) { return id >= 0 && id < kBsNumKernels ? kBsKernels[id].xors : 0; }
 
-cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
-                            cudaStream_t stream) {
-  const BsKernel &b = kBsKernels[id];
+namespace {
+
+// One CTA per SM; each block of the schedule gets CTAs in proportion to its
+// cost, at least one, and no more than it has warp tiles to hand out.
+cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs, int noutputs,
+                      const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
+                      cudaStream_t stream, std::atomic<uint64_t> (&smem_set)[kMaxDevices],
+                      int slot) {
   BsArgs a;
   a.nbytes = nbytes;
   a.hi28 = 1u << 28;
@@ -214,43 +97,108 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
   a.x4 = 4;
   a.x2 = 2;
   memset(a.ptr, 0, sizeof a.ptr);
-  for (int i = 0; i < b.ninputs; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
-  for (int j = 0; j < b.noutputs; j++) a.ptr[b.ninputs + j] = out[j];
-  // one CTA per SM; each block gets CTAs in proportion to its cost, at
-  // least one, and no more than it has warp tiles to hand out
-  static std::atomic<uint64_t> smem_set[kMaxDevices];
+  for (int i = 0; i < ninputs; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
+  for (int j = 0; j < noutputs; j++) a.ptr[ninputs + j] = out[j];
   const int sms = current_sm_count();
   const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes;  // 80 KiB
-  if (first_on_device(smem_set, id)) {
-    cudaError_t e = cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (first_on_device(smem_set, slot)) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const uint64_t units = (nbytes + kBsUnit - 1) / kBsUnit;
   const uint64_t cap = std::max<uint64_t>(1, (units + kBsThreads / 32 - 1) / (kBsThreads / 32));
   double total = 0;
-  for (int i = 0; i < b.nblocks; i++) total += b.cost[i];
+  for (int i = 0; i < nblocks; i++) total += cost[i];
   int cnt[kBsMaxBlocks];
   int used = 0;
-  for (int i = 0; i < b.nblocks; i++) {
-    cnt[i] = std::max(1, (int)(sms * b.cost[i] / total));
+  for (int i = 0; i < nblocks; i++) {
+    cnt[i] = std::max(1, (int)(sms * cost[i] / total));
     cnt[i] = (int)std::min<uint64_t>(cnt[i], cap);
     used += cnt[i];
   }
   for (; used < sms; used++) {  // hand out the rest to the slowest block
     int best = -1;
     double worst = 0;
-    for (int i = 0; i < b.nblocks; i++) {
-      const double t = (double)b.cost[i] / cnt[i];
+    for (int i = 0; i < nblocks; i++) {
+      const double t = (double)cost[i] / cnt[i];
       if ((uint64_t)cnt[i] < cap && t > worst) worst = t, best = i;
     }
     if (best < 0) break;
     cnt[best]++;
   }
   a.cta_start[0] = 0;
-  for (int i = 0; i < b.nblocks; i++) a.cta_start[i + 1] = (uint16_t)(a.cta_start[i] + cnt[i]);
-  for (int i = b.nblocks + 1; i <= kBsMaxBlocks; i++) a.cta_start[i] = a.cta_start[b.nblocks];
-  b.fn<<<a.cta_start[b.nblocks], kBsThreads, smem, stream>>>(a);
-  return cudaGetLastError();
+  for (int i = 0; i < nblocks; i++) a.cta_start[i + 1] = (uint16_t)(a.cta_start[i] + cnt[i]);
+  for (int i = nblocks + 1; i <= kBsMaxBlocks; i++) a.cta_start[i] = a.cta_start[nblocks];
+  void *args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(a.cta_start[nblocks]), dim3(kBsThreads), args, smem, stream);
+}
+
+std::atomic<uint64_t> g_static_smem_set[kMaxDevices];
+
+// the device code, as text, for run-time compilation (generated from
+// bitslice_dev.cuh at build time)
+#include "bitslice_dev_src.inc"
+
+}  // namespace
+
+cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
+                            cudaStream_t stream) {
+  const BsKernel &b = kBsKernels[id];
+  return bs_launch(reinterpret_cast<const void *>(b.fn), b.nblocks, b.cost, b.ninputs, b.noutputs,
+                   in, out, nbytes, stream, g_static_smem_set, id);
+}
+
+struct BsRuntimeKernel {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t fn = nullptr;
+  int nblocks = 0, ninputs = 0, noutputs = 0;
+  std::vector<int> cost;
+  std::atomic<uint64_t> smem_set[kMaxDevices] = {};
+  ~BsRuntimeKernel() {
+    if (lib) cudaLibraryUnload(lib);
+  }
+};
+
+int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs,
+                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
+  if (rows <= 0 || cols <= 0 || rows + cols > kBsMaxPtr) {
+    err = "matrix too large for one bitsliced launch";
+    return kEUnsupported;
+  }
+  const std::vector<BsBlock> blks = bs_blocks_chunked(M, rows, cols);
+  if ((int)blks.size() > kBsMaxBlocks) {
+    err = "too many blocks for one bitsliced launch";
+    return kEUnsupported;
+  }
+  for (const BsBlock &b : blks)
+    if ((int)b.inputs.size() > max_inputs) {
+      err = "a block reads more inputs than the run-time kernels take";
+      return kEUnsupported;
+    }
+  const char *kname = "bs_runtime_kernel";
+  const BsEmitted em = bs_emit_kernel(M, rows, cols, blks, kname, true);
+  const std::string src =
+      "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\n"
+      "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n" +
+      std::string(kBsDevSrc) + "\n" + em.code;
+  std::vector<char> cubin;
+  int rc = jit_compile(src, kname, cubin, err);
+  if (rc) return rc;
+  auto k = std::make_shared<BsRuntimeKernel>();
+  rc = jit_load(cubin, kname, &k->lib, &k->fn, err);
+  if (rc) return rc;
+  k->nblocks = (int)blks.size();
+  k->ninputs = cols;
+  k->noutputs = rows;
+  k->cost = em.cost;
+  out = k;
+  return kOk;
+}
+
+cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,
+                                    uint8_t *const *out, size_t nbytes, cudaStream_t stream) {
+  return bs_launch(reinterpret_cast<const void *>(k.fn), k.nblocks, k.cost.data(), k.ninputs,
+                   k.noutputs, in, out, nbytes, stream, k.smem_set, 0);
 }
 
 int bitslice_max_pointers() { return kBsMaxPtr; }

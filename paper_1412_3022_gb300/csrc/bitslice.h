@@ -4,6 +4,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <string>
 
 namespace pmrc {
 
@@ -24,5 +26,23 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
                             cudaStream_t stream);
 
 int bitslice_max_pointers();
+
+// A bitsliced kernel compiled at run time (NVRTC) for a matrix known only
+// then, e.g. the rows of a reconstruction: rows in blocks of at most 8 over
+// the union of their inputs, the same device code as the built-in kernels.
+struct BsRuntimeKernel;
+
+// Builds the kernel for M (rows x cols, row-major).  kEUnsupported when the
+// matrix is too large for one launch (cols + rows > 256 pointers, more than
+// 32 blocks or more than `max_inputs` inputs in a block) or NVRTC is missing
+// or fails (message in err).
+int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs,
+                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
+
+// out[r] = sum_c M[r][c] in[c] over bytes [0, nbytes); nbytes a multiple of
+// 32, every pointer 16-byte aligned; in[c] may be NULL for columns no row
+// reads, out[r] may not be NULL.
+cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,
+                                    uint8_t *const *out, size_t nbytes, cudaStream_t stream);
 
 }  // namespace pmrc

@@ -1,0 +1,135 @@
+// Device side of the bitsliced kernels (bitslice.cu): constants, the launch
+// arguments and the per-thread building blocks the generated block functions
+// call.  Self-contained (no includes): the library compiles it with nvcc,
+// and its text is also compiled at run time (jit.cpp) together with
+// schedules generated for matrices known only then.  Expects uint8_t,
+// uint16_t, uint32_t and uint64_t to be defined.
+constexpr int kBsThreads = 512;       // one CTA per SM (128 registers a thread)
+constexpr int kBsBytes = 32;          // bytes per thread per tile
+constexpr int kBsMaxPtr = 256;
+constexpr int kBsAhead = 4;           // inputs prefetched ahead of the one in use
+constexpr int kBsSlots = kBsAhead + 1;  // shared-memory ring (never the slot being read)
+constexpr uint32_t kBsUnit = 32 * kBsBytes;  // bytes of column per warp tile
+constexpr int kBsMaxBlocks = 32;
+
+struct BsArgs {
+  uint64_t nbytes;  // bytes covered by this launch (multiple of kBsBytes)
+  uint32_t hi28, hi30, hi31;  // 2^28, 2^30, 2^31: right shifts as multiply-high
+  uint32_t x16, x4, x2;       // left shifts as multiplies
+  uint16_t cta_start[kBsMaxBlocks + 1];  // CTAs [cta_start[b], cta_start[b+1]) run block b
+  uint8_t *ptr[kBsMaxPtr];    // K input blocks, then the output blocks
+};
+
+struct BsCtx {
+  const BsArgs *a;
+  uint64_t off;
+};
+
+__device__ __forceinline__ bool bs_ctx(const BsArgs &a, BsCtx &x, uint32_t unit) {
+  x.a = &a;
+  x.off = (uint64_t)unit * kBsUnit + (threadIdx.x % 32) * kBsBytes;
+  return x.off < a.nbytes;
+}
+
+__device__ __forceinline__ void bs_zero(uint32_t (&acc)[8][8]) {
+#pragma unroll
+  for (int r = 0; r < 8; r++)
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc[r][i] = 0;
+}
+
+// 8x8 bit transpose inside each byte lane of 8 words: afterwards word i
+// holds bit i of the 32 bytes (bit 8m+j = bit i of byte m of word j).  The
+// transform is an involution.  Each stage exchanges the bit fields `mask` of
+// the lower word with the fields `mask << s` of the upper one: both words are
+// rebuilt as a select between the word and a shifted copy of its partner (one
+// 3-input logic op each); the shifts run as multiplies on the FMA pipe.
+__device__ __forceinline__ void bs_transpose(uint32_t (&w)[8], const BsArgs &a) {
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const uint32_t sl = __umulhi(w[j], a.hi28), sh = w[j + 4] * a.x16;
+    w[j + 4] = (sl & 0x0F0F0F0Fu) | (w[j + 4] & ~0x0F0F0F0Fu);
+    w[j] = (sh & 0xF0F0F0F0u) | (w[j] & ~0xF0F0F0F0u);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j += 4)
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const uint32_t sl = __umulhi(w[j + q], a.hi30), sh = w[j + q + 2] * a.x4;
+      w[j + q + 2] = (sl & 0x33333333u) | (w[j + q + 2] & ~0x33333333u);
+      w[j + q] = (sh & 0xCCCCCCCCu) | (w[j + q] & ~0xCCCCCCCCu);
+    }
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const uint32_t sl = __umulhi(w[j], a.hi31), sh = w[j + 1] * a.x2;
+    w[j + 1] = (sl & 0x55555555u) | (w[j + 1] & ~0x55555555u);
+    w[j] = (sh & 0xAAAAAAAAu) | (w[j] & ~0xAAAAAAAAu);
+  }
+}
+
+// Asynchronous copy of this thread's 32 bytes of input `col` into ring slot
+// `slot` of the shared-memory staging area (cp.async, one commit group per
+// input).  Each thread reads back only what it copied, so no barrier is
+// needed; cp.async.wait_group orders the read after the copy.
+__device__ __forceinline__ void bs_prefetch(const BsCtx &x, int col, int slot) {
+  extern __shared__ __align__(16) uint8_t bs_smem[];
+  const uint8_t *src = x.a->ptr[col] + x.off;
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(
+      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16), "l"(src + 16)
+               : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// An empty commit group: keeps the number of groups in flight the same for
+// every input of a block shorter than the prefetch distance.
+__device__ __forceinline__ void bs_commit_empty() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bs_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bs_planes(const BsCtx &x, int slot, uint32_t (&Q)[16],
+                                          uint32_t (&R)[16]) {
+  extern __shared__ __align__(16) uint8_t bs_smem[];
+  const uint4 *p = reinterpret_cast<const uint4 *>(
+      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
+  const uint4 u = p[0], v = p[1];
+  uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+  bs_transpose(w, *x.a);
+  Q[0] = 0;
+  Q[1] = w[0];
+  Q[2] = w[1];
+  Q[3] = w[0] ^ w[1];
+  Q[4] = w[2];
+  Q[5] = w[2] ^ w[0];
+  Q[6] = w[2] ^ w[1];
+  Q[7] = w[2] ^ Q[3];
+  Q[8] = w[3];
+#pragma unroll
+  for (int s = 9; s < 16; s++) Q[s] = w[3] ^ Q[s - 8];
+  R[0] = 0;
+  R[1] = w[4];
+  R[2] = w[5];
+  R[3] = w[4] ^ w[5];
+  R[4] = w[6];
+  R[5] = w[6] ^ w[4];
+  R[6] = w[6] ^ w[5];
+  R[7] = w[6] ^ R[3];
+  R[8] = w[7];
+#pragma unroll
+  for (int s = 9; s < 16; s++) R[s] = w[7] ^ R[s - 8];
+}
+
+__device__ __forceinline__ void bs_store(const BsCtx &x, int slot, uint32_t (&planes)[8]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) w[i] = planes[i];
+  bs_transpose(w, *x.a);
+  uint4 *p = reinterpret_cast<uint4 *>(x.a->ptr[slot] + x.off);
+  __stcs(p, make_uint4(w[0], w[1], w[2], w[3]));
+  __stcs(p + 1, make_uint4(w[4], w[5], w[6], w[7]));
+}
+

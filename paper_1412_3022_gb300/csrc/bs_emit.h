@@ -1,0 +1,51 @@
+// Generation of bitsliced XOR schedules (host side).
+//
+// Multiplication by a constant c is the 8x8 bit matrix M_c whose column j
+// holds the bits of c * 2^j; with an input byte column cut into eight bit
+// planes p0..p7, output plane i of c*x is the XOR of the planes j with
+// M_c[i][j] = 1.  Splitting j into 0..3 and 4..7, every such XOR is
+// Q[a] ^ R[b] where Q (R) holds the XORs of all subsets of p0..p3 (p4..p7)
+// and a, b are the two nibbles of row i of M_c.  For each dense block of a
+// matrix (at most 8 rows sharing their inputs) the emitter writes a device
+// function that walks the block's inputs and accumulates those terms, and a
+// persistent kernel over the blocks (bitslice_dev.cuh supplies the rest).
+//
+// Used at build time for the built-in encode matrices (gen_bitslice.cpp) and
+// at run time for matrices known only then (jit.cpp).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pmrc {
+
+constexpr int kBsEmitRows = 8;        // rows per block (8 x 8 bit-plane accumulators)
+constexpr int kBsEmitMaxBlocks = 32;  // bitslice_dev.cuh: kBsMaxBlocks
+
+struct BsBlock {
+  std::vector<int> rows, inputs;
+};
+
+// Rows with the same non-zero columns form a group; each group is cut into
+// blocks of at most 8 rows (encode matrices: the rows of one slot share the
+// symbols of one column of the message matrix).
+std::vector<BsBlock> bs_blocks_by_support(const uint8_t *M, int rows, int cols);
+
+// Consecutive rows in blocks of at most 8, each reading the union of its
+// rows' non-zero columns (dense matrices such as reconstruction rows).
+std::vector<BsBlock> bs_blocks_chunked(const uint8_t *M, int rows, int cols);
+
+struct BsEmitted {
+  std::string code;       // block functions and the kernel
+  std::vector<int> cost;  // relative cost of each block per warp tile
+  long long xors = 0;     // XOR operations per 32-byte column
+};
+
+// Source of the block functions and of the kernel `name` for the matrix M
+// (rows x cols, row-major): output row r goes to pointer slot cols + r.  With
+// extern_c the kernel gets C linkage (for lookup by name after run-time
+// compilation).
+BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
+                         const std::string &name, bool extern_c);
+
+}  // namespace pmrc

@@ -1,0 +1,24 @@
+// Run-time compilation of generated device code (jit.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "code.h"
+
+namespace pmrc {
+
+// Whether NVRTC could be loaded in this process.
+bool jit_available();
+
+// Compiles CUDA source for sm_103a into a cubin (kEUnsupported with the
+// compiler log in err when NVRTC is missing or the source does not build).
+int jit_compile(const std::string &src, const char *kernel_name, std::vector<char> &cubin,
+                std::string &err);
+
+// Loads a cubin as a CUDA library and finds its kernel `kernel_name`.
+int jit_load(const std::vector<char> &cubin, const char *kernel_name, cudaLibrary_t *lib,
+             cudaKernel_t *fn, std::string &err);
+
+}  // namespace pmrc

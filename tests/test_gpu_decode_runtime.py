@@ -1,0 +1,106 @@
+"""Reconstruction through bitsliced kernels compiled at run time
+(pmrc_set_decode_kernel): bit-exact against the CPU oracle and the data, on
+every subset at k=3, random subsets at k=8 (with a ragged tail and lazy
+aliasing), Reed-Solomon; refusals when the kernel cannot be built."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1412_3022_gb300 as P
+from paper_1412_3022_gb300 import inputs
+from test_gpu_parity import Blocks
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def decode(c, S, Y, nbytes, lazy=False, shift=0):
+    a, K = c.alpha, c.data_blocks
+    rows = [a * i + j for i in S for j in range(a)]
+    yin = Blocks(len(rows), nbytes, shift, Y[rows])
+    xout = Blocks(K, nbytes, shift)
+    ptrs = xout.ptrs()
+    if lazy and c.form == P.PMRC_SYSTEMATIC:
+        for pos, i in enumerate(S):
+            if i < c.k:
+                for j in range(a):
+                    ptrs[a * i + j] = yin.ptr(a * pos + j)
+    c.decode(S, yin.ptrs(), ptrs, nbytes)
+    assert xout.guards_intact()
+    got = xout.get()
+    return got, [ptrs[r] == xout.ptr(r) for r in range(K)]
+
+
+@pytest.mark.parametrize("form", [P.PMRC_SYSTEMATIC, P.PMRC_NONSYSTEMATIC])
+def test_runtime_decode_every_subset_k3(form):
+    n, k, nbytes = 6, 3, 4096 + 7
+    c = P.Code(n, k, P.PMRC_SPARSE, form)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    X = inputs.blocks(6, nbytes, seed=80)
+    Y = O.encode(n, k, O.SPARSE, bool(form), X)
+    for S in itertools.combinations(range(n), k):
+        got, _ = decode(c, list(S), Y, nbytes)
+        assert np.array_equal(got, X), S
+
+
+def test_runtime_decode_k8_random_lazy_and_tail():
+    n, k = 16, 8
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    rng = np.random.default_rng(81)
+    for t, nbytes in enumerate((64 * 1024 + 13, 3 * 4096 + 32)):
+        X = inputs.blocks(56, nbytes, seed=82 + t)
+        Y = O.encode(n, k, O.SPARSE, True, X)
+        for _ in range(2):
+            S = rng.permutation(rng.choice(n, k, replace=False)).tolist()
+            got, computed = decode(c, S, Y, nbytes, lazy=True)
+            for r in range(56):
+                if computed[r]:
+                    assert np.array_equal(got[r], X[r]), (S, r)
+                else:
+                    assert (got[r] == 0xA5).all(), (S, r)
+
+
+def test_runtime_decode_matches_generic_and_rs():
+    n, k, nbytes = 16, 8, 32 * 1024
+    gen = P.Code(n, k, P.PMRC_VANILLA, P.PMRC_NONSYSTEMATIC)
+    X = inputs.blocks(56, nbytes, seed=83)
+    Y = O.encode(n, k, O.VANILLA, False, X)
+    S = [15, 3, 9, 0, 12, 6, 1, 10]
+    outs = []
+    for which in (P.PMRC_KERNEL_BITSLICED, P.PMRC_KERNEL_GENERIC):
+        gen.set_decode_kernel(which)
+        outs.append(decode(gen, S, Y, nbytes)[0])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], X)
+    rs = P.Code(16, 8, P.PMRC_RS, P.PMRC_SYSTEMATIC)
+    rs.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    X = inputs.blocks(8, nbytes, seed=84)
+    Y = O.rs_encode(16, 8, True, X)
+    got, _ = decode(rs, [9, 2, 14, 11, 4, 15, 0, 7], Y, nbytes)
+    assert np.array_equal(got, X)
+
+
+def test_runtime_decode_refusals():
+    c = P.Code(16, 8, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    X = inputs.blocks(56, 4096, seed=85)
+    Y = O.encode(16, 8, O.SPARSE, True, X)
+    with pytest.raises(P.PMRCError) as e:      # misaligned blocks cannot take this path
+        decode(c, [8, 9, 10, 11, 12, 13, 14, 15], Y, 4096, shift=3)
+    assert e.value.rc == P.PMRC_EUNSUPPORTED
+    m = P.Code(16, 8, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=14)   # 112 inputs per block
+    m.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    a, B = O.mbr_params(16, 8, 14)
+    Xm = inputs.blocks(B, 4096, seed=86)
+    Ym = O.mbr_encode(16, 8, 14, Xm)
+    with pytest.raises(P.PMRCError) as e:
+        decode(m, [8, 9, 10, 11, 12, 13, 14, 15], Ym, 4096)
+    assert e.value.rc == P.PMRC_EUNSUPPORTED
+    m.set_decode_kernel(P.PMRC_KERNEL_AUTO)    # AUTO keeps the split-table kernel
+    got, _ = decode(m, [8, 9, 10, 11, 12, 13, 14, 15], Ym, 4096)
+    assert np.array_equal(got, Xm)
