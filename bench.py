@@ -47,6 +47,38 @@ FLUSH_BYTES = 512 << 20
 SMS = 152   # GB300 streaming multiprocessors
 
 
+# ------------------------------------------------------------ ALU models
+ALU_MODEL_REGION = ("split-table region kernel: 12 PRMT + 6 LOP3 = 18 ALU lane-ops per "
+                    "16-byte product (planner products, zeros included)")
+ALU_MODEL_BITSLICED = ("bitsliced kernel, per 32-byte lane and block: 44 lane-ops per input "
+                       "(24 transpose + 20 subset-table XORs), 24 per output row (transpose "
+                       "back), 8 per non-zero coefficient (one 3-input XOR per output plane)")
+
+
+def alu_ops_bitsliced(M, kind):
+    """ALU lane-ops per 32-byte column of the bitsliced kernels for the
+    matrix M, with their block rule: rows of identical support in blocks of
+    at most 8 ("support", the built-in encode kernels) or consecutive rows
+    in balanced blocks of at most 8 over the union of their inputs
+    ("chunked", the run-time reconstruction kernels)."""
+    rows = M.shape[0]
+    blocks = []
+    if kind == "support":
+        groups = {}
+        for r in range(rows):
+            groups.setdefault(tuple(np.flatnonzero(M[r]).tolist()), []).append(r)
+        for sup, rs in groups.items():
+            nb = -(-len(rs) // 8)
+            for b in range(nb):
+                blocks.append((len(rs) * (b + 1) // nb - len(rs) * b // nb, len(sup)))
+    else:
+        nb = -(-rows // 8)
+        for b in range(nb):
+            rs = list(range(rows * b // nb, rows * (b + 1) // nb))
+            blocks.append((len(rs), int((M[rs] != 0).any(axis=0).sum())))
+    return sum(44 * c + 24 * r for r, c in blocks) + 8 * int((M != 0).sum())
+
+
 # ------------------------------------------------------------ multi-rank
 # Stripes are independent, so N ranks run N replicas of the step on their own
 # seeded stripes (weak scaling) with no collective on the data path; the only
@@ -202,7 +234,6 @@ class Workload:
 
     def _bytes(self):
         """Algorithmic HBM bytes and user bytes per operation."""
-        import numpy as np
         B, a, K = self.B, A_, K_ * A_
         coef = self.sysc.helper_coefficients(self.f)
         reads_per_helper = int((coef != 0).sum())
@@ -221,12 +252,30 @@ class Workload:
         self.user = {"gen_encode": K * B, "sys_encode": K * B, "repair": a * B, "decode": K * B}
         self.decode_missing = len(missing)
         self.helper_reads = reads_per_helper
-        # products per byte column the region kernel computes (planner blocks,
-        # zero products included) for the ops it runs
+        # the kernel each operation runs, and its ALU lane-ops per launch
+        # (alu_model); the reconstruction runs the run-time bitsliced kernel
+        # (blocks of at least 256 KiB), the helper projections and the
+        # newcomer the split-table region kernel
         P = self.P
-        dec_st = P.pmrc_plan_stats(R[missing]) if missing else {"entries": 0}
-        self.entries = {"decode": int(dec_st["entries"])}
-        del np
+        G = self.genc.generator()
+        Gs = self.sysc.generator()[K:]
+        Dn = self.sysc.newcomer_matrix(self.f, self.H)
+        Mh = np.zeros((D_, D_ * a), np.uint8)
+        for h in range(D_):
+            Mh[h, h * a:h * a + a] = coef
+        Rm = R[missing] if missing else np.zeros((0, K), np.uint8)
+        self.kernel = {"gen_encode": "bitsliced encode bs_n16_k8_c0_f0",
+                       "sys_encode": "bitsliced encode bs_n16_k8_c1_f1",
+                       "repair_helpers": "region_kernel<1>", "repair_newcomer": "region_kernel<8>",
+                       "decode": "bitsliced reconstruction (compiled at run time)"}
+        self.alu_ops, self.alu_model = {}, {}
+        for n, M, kind in (("gen_encode", G, "support"), ("sys_encode", Gs, "support"),
+                           ("decode", Rm, "chunked")):
+            self.alu_ops[n] = alu_ops_bitsliced(M, kind) * (B // 32)
+            self.alu_model[n] = ALU_MODEL_BITSLICED
+        for n, M in (("repair_helpers", Mh), ("repair_newcomer", Dn)):
+            self.alu_ops[n] = int(P.pmrc_plan_stats(M)["entries"]) * (B // 16) * 18
+            self.alu_model[n] = ALU_MODEL_REGION
 
     def ops(self, stream=None):
         s, B, a = self, self.B, self.c_args
@@ -314,22 +363,23 @@ def run_ours(args, rank, world, local_rank):
     per_op["decode"]["missing_rows"] = W.decode_missing
     dom = max(names, key=lambda n: op_ms[n])
     ach = W.alg[dom] / (op_ms[dom] * 1e-3) / 1e9
-    roofline = {"kernel": "region_kernel (" + dom + ")", "bound": "hbm",
+    roofline = {"kernel": W.kernel[dom] + " (" + dom + ")", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(ach / hbm, 4), "peak_source": peak_src + " hbm_gbs (burst copy)",
                 "traffic": None}
-    # the same kernel against its integer-ALU ceiling: the region kernel
-    # spends 12 PRMT + 6 LOP3 (18 ALU lane-ops) per 16 GF(2^8) byte-products,
-    # and the ALU pipe issues 64 lanes/clk/SM on 152 SMs at the sampled clock
-    if dom in W.entries:
-        mhz = (ck or {}).get("sm_mhz") or 2070.0
-        peak_p = 64.0 / 18.0 * 16.0 * SMS * mhz * 1e6 / 1e9
-        ach_p = W.entries[dom] * B / (op_ms[dom] * 1e-3) / 1e9
-        roofline["alu"] = {"unit": "G byte-products/s", "achieved": round(ach_p, 1),
-                           "peak": round(peak_p, 1), "frac": round(ach_p / peak_p, 4),
-                           "products_per_launch": W.entries[dom] * B, "sm_mhz": mhz,
-                           "model": "18 ALU lane-ops per 16 byte-products; 64 ALU "
-                                    "lanes/clk/SM x 152 SMs x sampled SM clock"}
+    # the same kernel against its integer-ALU ceiling (64 ALU lanes/clk/SM
+    # on 152 SMs at the sampled clock); lane-ops per launch from the
+    # kernel's instruction model (alu_model)
+    mhz = (ck or {}).get("sm_mhz") or 2070.0
+    peak_ops = 64.0 * SMS * mhz * 1e6 / 1e12
+    ach_ops = W.alu_ops[dom] / (op_ms[dom] * 1e-3) / 1e12
+    roofline["alu"] = {"unit": "T lane-ops/s", "achieved": round(ach_ops, 2),
+                       "peak": round(peak_ops, 2), "frac": round(ach_ops / peak_ops, 4),
+                       "lane_ops_per_launch": W.alu_ops[dom], "sm_mhz": mhz,
+                       "model": W.alu_model[dom]}
+    for n in names:
+        per_op[n]["kernel"] = W.kernel[n]
+        per_op[n]["alu_frac"] = round(W.alu_ops[n] / (op_ms[n] * 1e-3) / 1e12 / peak_ops, 4)
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
