@@ -265,7 +265,11 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * built (NVRTC missing, blocks not 16-byte aligned, or more than 64 inputs
  * per 8-row block).  PMRC_KERNEL_GENERIC: always the split-table kernel.
  * PMRC_KERNEL_BITSLICED: the run-time kernel at any size, PMRC_EUNSUPPORTED
- * from pmrc_decode when it cannot be built.  Results are identical. */
+ * from pmrc_decode when it cannot be built.  Results are identical.  The
+ * same choice applies to pmrc_repair_newcomer (its D, per failed node and
+ * helper list), where AUTO takes the run-time kernel from 4 MiB blocks and
+ * PMRC_KERNEL_BITSLICED falls back to the split-table kernel rather than
+ * failing. */
 int pmrc_set_decode_kernel(pmrc_code *code, int which);
 
 /* ---- batched execution ---------------------------------------------------

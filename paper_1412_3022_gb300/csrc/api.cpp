@@ -166,6 +166,7 @@ namespace {
 // node set, is paid once per handle), and for reconstructions whose blocks
 // read at most this many inputs
 constexpr size_t kRuntimeMinBytes = 256 << 10;
+constexpr size_t kRuntimeNewcomerMinBytes = 4 << 20;
 constexpr int kRuntimeMaxInputs = 64;
 
 // GF(2^16) codes: user block i (B bytes, two byte planes) is the pair of
@@ -204,6 +205,10 @@ int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
                          pmrc_stream_t stream);
 int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream);
+std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
+                                                const std::function<int(Mat &, std::string &)> &make,
+                                                std::string &err);
+bool want_runtime(const pmrc_code *c, int policy, size_t nbytes, size_t auto_min);
 
 }  // namespace
 
@@ -432,7 +437,41 @@ int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
   std::string err;
   int rc = newcomer_plan(c, f, helpers, p, err);
   if (rc) return fail(rc, err);
-  rc = launch_region(*p, received, out, nbytes, (cudaStream_t)stream, err);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int d = c->m.d * c->m.beta, a = c->m.alpha;
+  size_t done = 0;
+  // bitsliced newcomer, compiled at run time per (failed node, helpers)
+  // like the reconstruction rows; a single 8-row block fills the GPU only on
+  // long columns (one 1 KiB tile per warp), so AUTO takes it from 4 MiB
+  if (want_runtime(c, c->decode_kernel, nbytes, kRuntimeNewcomerMinBytes)) {
+    bool aligned = true;
+    for (int i = 0; i < d && aligned; i++) aligned = received[i] && (uintptr_t)received[i] % 16 == 0;
+    for (int j = 0; j < a && aligned; j++) aligned = (uintptr_t)out[j] % 16 == 0;
+    std::string key = "n:" + std::to_string(f);
+    for (int i = 0; i < c->m.d; i++) key += "," + std::to_string(helpers[i]);
+    std::string rerr;
+    std::shared_ptr<BsRuntimeKernel> k;
+    if (aligned)
+      k = runtime_kernel(c, key, [&](Mat &M, std::string &e) {
+        return newcomer_matrix(c->m, f, helpers, M, e);
+      }, rerr);
+    if (k) {
+      done = nbytes & ~(size_t)31;
+      const cudaError_t e = bitslice_launch_runtime(*k, received, out, done, st);
+      if (e != cudaSuccess)
+        return fail(PMRC_ECUDA, std::string("bitsliced newcomer launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (done == nbytes) return PMRC_OK;
+  if (done == 0) {
+    rc = launch_region(*p, received, out, nbytes, st, err);
+  } else {  // ragged tail of the blocks
+    std::vector<const uint8_t *> in2(d);
+    std::vector<uint8_t *> out2(a);
+    for (int i = 0; i < d; i++) in2[i] = received[i] + done;
+    for (int j = 0; j < a; j++) out2[j] = out[j] + done;
+    rc = launch_region(*p, in2.data(), out2.data(), nbytes - done, st, err);
+  }
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
@@ -543,16 +582,11 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
 
 namespace {
 
-// Bitsliced reconstruction compiled at run time for this (nodes, wanted
-// rows), cached in the handle; null when the pattern is not eligible or the
-// build failed (the reason in err).
-std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *nodes,
-                                                const std::vector<char> &want,
+// A bitsliced kernel compiled at run time for matrix M, cached in the handle
+// under `key`; null when it cannot be built (the reason in err, also cached).
+std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
+                                                const std::function<int(Mat &, std::string &)> &make,
                                                 std::string &err) {
-  std::string key;
-  for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
-  key += ":";
-  for (char w : want) key += w ? '1' : '0';
   std::lock_guard<std::mutex> g(c->jit_mu);
   {
     std::lock_guard<std::mutex> g2(c->mu);
@@ -563,22 +597,43 @@ std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *n
     }
   }
   std::shared_ptr<BsRuntimeKernel> k;
-  Mat R;
-  int rc = decode_matrix(c->m, nodes, R, err);
-  if (!rc) {
-    std::vector<int> rows;
-    for (int r = 0; r < c->m.K; r++)
-      if (want[r]) rows.push_back(r);
-    Mat M((int)rows.size(), R.cols);
-    for (size_t q = 0; q < rows.size(); q++)
-      for (int col = 0; col < R.cols; col++) M.at((int)q, col) = R.at(rows[q], col);
-    if (!rows.empty()) rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, k, err);
-  }
+  Mat M;
+  int rc = make(M, err);
+  if (!rc && M.rows > 0) rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, k, err);
   std::lock_guard<std::mutex> g2(c->mu);
   if (c->rt.size() >= kPlanCacheCap) c->rt.erase(c->rt.begin());
   c->rt[key] = k;
   if (!k) c->rt_err[key] = err;
   return k;
+}
+
+// Bitsliced reconstruction rows for this (nodes, wanted rows).
+std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *nodes,
+                                                const std::vector<char> &want,
+                                                std::string &err) {
+  std::string key = "d:";
+  for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
+  key += ":";
+  for (char w : want) key += w ? '1' : '0';
+  return runtime_kernel(c, key, [&](Mat &M, std::string &e) {
+    Mat R;
+    int rc = decode_matrix(c->m, nodes, R, e);
+    if (rc) return rc;
+    std::vector<int> rows;
+    for (int r = 0; r < c->m.K; r++)
+      if (want[r]) rows.push_back(r);
+    M = Mat((int)rows.size(), R.cols);
+    for (size_t q = 0; q < rows.size(); q++)
+      for (int col = 0; col < R.cols; col++) M.at((int)q, col) = R.at(rows[q], col);
+    return (int)kOk;
+  }, err);
+}
+
+// Whether a call of nbytes takes a run-time bitsliced kernel under the
+// handle's policy (GF(2^8) codes only; AUTO from auto_min bytes per block).
+bool want_runtime(const pmrc_code *c, int policy, size_t nbytes, size_t auto_min) {
+  return c->m.w == 8 && nbytes >= 32 &&
+         (policy == PMRC_KERNEL_BITSLICED || (policy == PMRC_KERNEL_AUTO && nbytes >= auto_min));
 }
 
 int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
@@ -597,9 +652,7 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
   // bitsliced path: reconstruction rows compiled at run time (GF(2^8)
   // codes; AUTO for blocks of at least kRuntimeMinBytes)
   const bool forced = c->decode_kernel == PMRC_KERNEL_BITSLICED;
-  const bool want_rt = c->m.w == 8 && nbytes >= 32 &&
-                       (forced || (c->decode_kernel == PMRC_KERNEL_AUTO && nbytes >= kRuntimeMinBytes));
-  if (want_rt) {
+  if (want_runtime(c, c->decode_kernel, nbytes, kRuntimeMinBytes)) {
     std::vector<int> rows;
     for (int r = 0; r < c->m.K; r++)
       if (want[r]) rows.push_back(r);

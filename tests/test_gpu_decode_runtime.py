@@ -104,3 +104,33 @@ def test_runtime_decode_refusals():
     m.set_decode_kernel(P.PMRC_KERNEL_AUTO)    # AUTO keeps the split-table kernel
     got, _ = decode(m, [8, 9, 10, 11, 12, 13, 14, 15], Ym, 4096)
     assert np.array_equal(got, Xm)
+
+
+def test_runtime_newcomer_every_node_k8_and_mbr():
+    """The newcomer's D compiled at run time per (failed node, helpers)."""
+    n, k, nbytes = 16, 8, 64 * 1024 + 20
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    a, d = 7, 14
+    X = inputs.blocks(56, nbytes, seed=87)
+    Y = O.encode(n, k, O.SPARSE, True, X)
+    for f in range(n):
+        H = c.default_helpers(f)
+        sent = np.stack([O.repair_helper(n, k, O.SPARSE, f, Y[a * h:a * h + a]) for h in H])
+        recv = Blocks(d, nbytes, 0, sent)
+        out = Blocks(a, nbytes)
+        c.repair_newcomer(f, H, recv.ptrs(), out.ptrs(), nbytes)
+        assert out.guards_intact()
+        assert np.array_equal(out.get(), Y[a * f:a * f + a]), f
+    m = P.Code(16, 8, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=14)
+    m.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    am, B = O.mbr_params(16, 8, 14)
+    Xm = inputs.blocks(B, 4096 + 32, seed=88)
+    Ym = O.mbr_encode(16, 8, 14, Xm)
+    for f in (0, 13):
+        H = m.default_helpers(f)
+        sent = np.stack([O.mbr_repair_helper(16, 8, 14, f, Ym[am * h:am * h + am]) for h in H])
+        recv = Blocks(14, 4096 + 32, 0, sent)
+        out = Blocks(am, 4096 + 32)
+        m.repair_newcomer(f, H, recv.ptrs(), out.ptrs(), 4096 + 32)
+        assert np.array_equal(out.get(), Ym[am * f:am * f + am]), f
