@@ -64,7 +64,7 @@ enum {
 };
 
 enum { PMRC_VANILLA = 0, PMRC_SPARSE = 1 };            /* Sec. 3.3 (PM-MSR)   */
-enum { PMRC_MBR = 2 };                                 /* Sec. 2, 3.2, 4.3    */
+enum { PMRC_MBR = 2 };                                 /* Sec. 2, 3.2, 4.2    */
 enum { PMRC_RS = 3 };                                  /* Sec. 4 baseline     */
 enum { PMRC_NONSYSTEMATIC = 0, PMRC_SYSTEMATIC = 1 };  /* Sec. 3.1 / Sec. 3.2 */
 

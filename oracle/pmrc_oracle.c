@@ -707,7 +707,7 @@ int or_encode_precode(int n, int k, int construction, const uint8_t *data, uint8
 
 /* ------------------------------------------------------------------------ */
 /* Product-matrix MBR codes (Sec. 2: alpha = d, Delta = (2d-k+1)/2; Sec. 3.2: */
-/* a systematic encoding matrix Psi = [I; Psi''] given directly; Sec. 4.3    */
+/* a systematic encoding matrix Psi = [I; Psi''] given directly; Sec. 4.2    */
 /* evaluates encode, repair and decode).  The message matrix of the seminal  */
 /* PM paper, restated:                                                       */
 /*     M = [ S    T ]    (d x d, symmetric)                                  */

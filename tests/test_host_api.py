@@ -199,7 +199,7 @@ def test_mbr_create_rejects_bad_points():
 
 
 def test_mbr_encode_plan_is_sparse():
-    """Parity rows touch d or k data blocks (Sec. 4.3: naturally sparse)."""
+    """Parity rows touch d or k data blocks (Sec. 4.2: naturally sparse)."""
     c = P.Code(16, 8, P.PMRC_MBR, P.PMRC_SYSTEMATIC, d=14)
     G = P.pmrc_code_generator(c.handle)
     par = G[8 * 14:]

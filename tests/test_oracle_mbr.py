@@ -1,5 +1,5 @@
 """Pins of the oracle's product-matrix MBR code (Sec. 2 parameters, Sec. 3.2
-systematic Psi = [I; Psi''], Sec. 4.3 operations) against facts the paper
+systematic Psi = [I; Psi''], Sec. 4.2 operations) against facts the paper
 and the mathematics fix: the MBR point alpha = d, k Delta = k(2d-k+1)/2; the
 product form C = Psi M with M = [S T; T^t 0] symmetric; the systematic
 nodes holding message symbols verbatim; exact repair from every helper set
@@ -117,7 +117,7 @@ def test_mbr_psi_rank_conditions(n, k, d):
 
 def test_mbr_parity_rows_are_sparse():
     """Each parity row touches only column j of M: d symbols for j < k, k for
-    j >= k (the paper's "naturally sparse" MBR encode, Sec. 4.3)."""
+    j >= k (the paper's "naturally sparse" MBR encode, Sec. 4.2)."""
     n, k, d = 16, 8, 14
     a, B = O.mbr_params(n, k, d)
     G = O.mbr_generator(n, k, d)
