@@ -121,6 +121,8 @@ def parse():
     p.add_argument("--batch-stripes", type=int, default=4096)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-mbr", action="store_true")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the block-size sweep (64 KiB - 4 MiB) of encode, repair, decode")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the rows outside the step (fused repair, specific algorithms, "
                         "PM-MBR, Reed-Solomon), e.g. for a launch list of the step alone")
@@ -419,6 +421,8 @@ def run_ours(args, rank, world, local_rank):
             per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
             per_op.update(run_rs(torch, P, inputs, args, flush, stream, dev, hbm))
             per_op.update(run_gf16(torch, P, inputs, args, flush, stream, dev, hbm))
+    sweep = None if (args.no_sweep or args.no_extra) else run_sweep(torch, P, inputs, args, flush,
+                                                                    stream, dev, hbm)
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
@@ -441,6 +445,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if e2e:
         result["e2e"] = e2e
+    if sweep:
+        result["block_sweep"] = sweep
     if batched:
         result["batched"] = batched
     if serving:
@@ -450,6 +456,30 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def run_sweep(torch, P, inputs, args, flush, stream, dev, hbm):
+    """The n=16 k=8 sparse systematic code at block sizes 64 KiB - 4 MiB:
+    encode, repair of a seeded node (helpers + newcomer) and reconstruction
+    from a seeded 8-node set, each on its own seeded stripe of that size."""
+    out = {}
+    for B in (64 << 10, 256 << 10, 1 << 20, 4 << 20):
+        W = Workload(torch, P, inputs, B, args.seed + 500 + B % 977, dev)
+        ops = dict(W.ops())
+        row = {}
+        for name, fn, user, alg in (
+                ("sys_encode", ops["sys_encode"], W.user["sys_encode"], W.alg["sys_encode"]),
+                ("repair", lambda: (ops["repair_helpers"](), ops["repair_newcomer"]()),
+                 W.user["repair"], W.alg["repair_helpers"] + W.alg["repair_newcomer"]),
+                ("decode", ops["decode"], W.user["decode"], W.alg["decode"])):
+            ms = time_op(torch, stream, flush, args, fn)
+            row[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2),
+                         "frac_hbm": round(alg / (ms * 1e-3) / 1e9 / hbm, 4)}
+        row["decode"]["missing_rows"] = W.decode_missing
+        out[f"{B >> 10} KiB"] = row
+        del W
+    torch.cuda.synchronize()
+    return out
 
 
 def run_mbr(torch, P, inputs, args, flush, stream, dev, hbm):
