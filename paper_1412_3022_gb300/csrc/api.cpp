@@ -601,7 +601,11 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
   int rc = make(M, err);
   if (!rc && M.rows > 0) rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, k, err);
   std::lock_guard<std::mutex> g2(c->mu);
-  if (c->rt.size() >= kPlanCacheCap) c->rt.erase(c->rt.begin());
+  if (c->rt.size() >= kPlanCacheCap) {
+    if (c->rt.begin()->second) c->rt_retired.push_back(c->rt.begin()->second);
+    c->rt_err.erase(c->rt.begin()->first);
+    c->rt.erase(c->rt.begin());
+  }
   c->rt[key] = k;
   if (!k) c->rt_err[key] = err;
   return k;

@@ -29,6 +29,9 @@ struct pmrc_code {
   mutable std::mutex jit_mu;                // one compilation at a time per handle
   mutable std::map<std::string, std::shared_ptr<pmrc::BsRuntimeKernel>> rt;
   mutable std::map<std::string, std::string> rt_err;
+  // evicted run-time kernels stay loaded until the handle is destroyed: a
+  // launch from them may still be running
+  mutable std::vector<std::shared_ptr<pmrc::BsRuntimeKernel>> rt_retired;
 };
 
 namespace pmrc {
