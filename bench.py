@@ -860,6 +860,12 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1, inputs=None):
     hout = torch.empty((out_rows, B), dtype=torch.uint8).pin_memory()
     present = {a * i + j for i in W.S if i < K_ for j in range(a)}
     missing = [r for r in range(K) if r not in present]
+    runs = []                                 # consecutive missing rows: one copy each
+    for r in missing:
+        if runs and runs[-1][1] == r:
+            runs[-1][1] = r + 1
+        else:
+            runs.append([r, r + 1])
     sets = [W, Workload(torch, W.P, inputs, B, W.seed, dev)]   # same stripe, own buffers
     s_in, s_comp, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
     opsets = [S.ops(int(s_comp.cuda_stream)) for S in sets]
@@ -889,9 +895,9 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1, inputs=None):
             o += K
             hout[o:o + a].copy_(S.node, non_blocking=True)
             o += a
-            for r in missing:
-                hout[o].copy_(S.data_out[r], non_blocking=True)
-                o += 1
+            for r0, r1 in runs:
+                hout[o:o + r1 - r0].copy_(S.data_out[r0:r1], non_blocking=True)
+                o += r1 - r0
         ev_out[b].record(s_out)
 
     for i in range(max(2, args.warmup)):
@@ -910,10 +916,44 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1, inputs=None):
         dist.barrier()
     ms = ranks_max(dist, e0.elapsed_time(e1) / args.steps, dev)
     user = sum(W.user.values())
+    h2d, d2h = K * B, out_rows * B
+    link = link_bandwidth(torch, dev)
+    # the host link moves each step's inputs in and results out; with the
+    # two directions fully overlapped the step cannot beat the slower one
+    floor_ms = max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6
+    link["bound_gbs"] = round(whole_job_gbps(user, world, floor_ms), 2)
+    link["frac"] = round(floor_ms / ms, 3)
     return {"value": round(whole_job_gbps(user, world, ms), 2), "unit": "GB/s",
-            "ms_per_step": round(ms, 4), "h2d_bytes_per_step": K * B,
-            "d2h_bytes_per_step": out_rows * B,
-            "pipeline": "2 buffer sets, 3 streams (H2D / compute / D2H)"}
+            "ms_per_step": round(ms, 4), "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "pipeline": "2 buffer sets, 3 streams (H2D / compute / D2H)",
+            "link": link}
+
+
+def link_bandwidth(torch, dev, nbytes=256 << 20, reps=5):
+    """Pinned host <-> device copy bandwidth of this machine's host link, each
+    direction on its own (GB/s, median of `reps` timed copies of `nbytes`):
+    the ceiling of the end-to-end number."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, fn in (("h2d_gbs", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h_gbs", lambda: h.copy_(d, non_blocking=True))):
+        times = []
+        with torch.cuda.stream(s):
+            fn()
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                fn()
+                e1.record(s)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        out[name] = round(nbytes / (sorted(times)[len(times) // 2] * 1e6), 1)
+    s.synchronize()
+    return out
 
 
 # ------------------------------------------------------------------ oracle

@@ -100,12 +100,13 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   a.tab1_base = (uint32_t)plan.tab1_base;
   const int sms = current_sm_count();
   const uint64_t nb = plan.blocks.size();
-  // launches of few blocks on short columns (a newcomer apply, say) would
-  // leave most SMs idle with 4 KiB tiles: they run 128-thread CTAs on 2 KiB
-  // tiles instead, twice as many
+  // 128-thread CTAs on 2 KiB tiles for blocks of one or two rows (their
+  // tiles are mostly loads, and smaller CTAs leave a shorter tail) and for
+  // launches of few blocks on short columns (a newcomer apply, say), which
+  // would leave most SMs idle with 4 KiB tiles
   unsigned threads = kThreads;
-  if (nb * ((nbytes + (uint64_t)kThreads * kVec - 1) / ((uint64_t)kThreads * kVec)) <
-      (uint64_t)sms * 4)
+  if (R <= 2 || nb * ((nbytes + (uint64_t)kThreads * kVec - 1) / ((uint64_t)kThreads * kVec)) <
+                    (uint64_t)sms * 4)
     threads = kThreads / 2;
   const uint64_t tile = (uint64_t)threads * kVec;
   a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
@@ -120,7 +121,7 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   // the tail better
   uint64_t gy = a.ntiles;
   if (R <= 2) {
-    const uint64_t target = (uint64_t)sms * 8;  // 4 resident CTAs per SM, two waves
+    const uint64_t target = (uint64_t)sms * 16;  // 8 resident CTAs per SM, two waves
     gy = (target + nb - 1) / nb;
     if (gy > a.ntiles) gy = a.ntiles;
   }
