@@ -35,6 +35,11 @@
  *     an (operation, failure pattern, device) combination (a synchronous
  *     cudaMalloc + cudaMemcpy); make that first call outside CUDA stream
  *     capture.  Later calls with the same pattern allocate nothing.
+ *   - An operation over more than 1024 blocks (inputs + outputs, e.g. the
+ *     encode of k >= 24 at n = 2k) or with rows over more than 512 inputs
+ *     runs as several kernel launches on the stream, later launches XORing
+ *     into outputs the first one wrote; the batched and served calls take
+ *     only operations of one launch (PMRC_EUNSUPPORTED otherwise).
  *   - One code handle may be used from several threads at once.
  *   - On failure the call returns a negative PMRC_E* status, writes nothing
  *     and pmrc_last_error() describes the problem (thread-local).

@@ -235,8 +235,6 @@ int pmrc_create_field(int n, int k, int d, int construction, int form, int field
   // encode plan: all rows (non-systematic) or the parity nodes' rows
   // (systematic: the first k nodes hold the data)
   const int first = form ? k * c->m.alpha : 0;
-  if (K + N - first > kMaxSlots)
-    return fail(PMRC_EUNSUPPORTED, "code too large: more than 1024 block pointers per encode");
   Mat M(N - first, K);
   std::copy(c->m.Gcode.v.begin() + (size_t)first * K, c->m.Gcode.v.end(), M.v.begin());
   std::vector<int> slot(N - first);
@@ -323,13 +321,19 @@ int pmrc_plan_stats(int rows, int cols, const uint8_t *m, int64_t *st) {
   std::vector<int> slot(rows);
   for (int r = 0; r < rows; r++) slot[r] = r;
   auto p = make_plan(M, slot, rows);
-  int64_t ent = 0, ins = 0;
-  for (auto &b : p->blocks) {
-    ent += (int64_t)b.inputs.size() * b.rows.size();
-    ins += (int64_t)b.inputs.size();
-  }
-  st[0] = (int64_t)p->blocks.size();
-  st[1] = p->R;
+  int64_t nb = 0, R = 0, ent = 0, ins = 0;
+  auto add = [&](const Plan &q) {  // the plan itself, or each of its parts
+    nb += (int64_t)q.blocks.size();
+    if (!q.blocks.empty()) R = std::max<int64_t>(R, q.R);
+    for (auto &b : q.blocks) {
+      ent += (int64_t)b.inputs.size() * b.rows.size();
+      ins += (int64_t)b.inputs.size();
+    }
+  };
+  add(*p);
+  for (auto &pt : p->parts) add(*pt.plan);
+  st[0] = nb;
+  st[1] = R;
   st[2] = ent;
   st[3] = ins;
   st[4] = p->nnz;
@@ -412,7 +416,6 @@ int encode_body(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *
 int repair_helpers_body(const pmrc_code *c, int f, int nh, const int *helpers,
                         const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
                         pmrc_stream_t stream) {
-  if (nh * (c->m.alpha + c->m.beta) > kMaxSlots) return fail(PMRC_EUNSUPPORTED, "too many helpers");
   if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
   if (helpers)
     for (int h = 0; h < nh; h++)
@@ -648,9 +651,8 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
   std::string err;
   int rc = decode_plan(c, nodes, want, p, err);
   if (rc) return fail(rc, err);
-  for (const auto &blk : p->blocks)
-    for (uint16_t in : blk.inputs)
-      if (!node_blocks[in]) return fail(PMRC_EINVAL, "a node block the reconstruction reads is NULL");
+  for (int in : plan_reads(*p))
+    if (!node_blocks[in]) return fail(PMRC_EINVAL, "a node block the reconstruction reads is NULL");
   const cudaStream_t st = (cudaStream_t)stream;
   size_t done = 0;
   // bitsliced path: reconstruction rows compiled at run time (GF(2^8)

@@ -132,6 +132,10 @@ int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const
   }
   s.type = 0;
   s.plan = c->encode;
+  if (!s.plan->parts.empty()) {
+    err = "code too large for the batched kernel (its encode runs as several launches)";
+    return kEUnsupported;
+  }
   for (int i = 0; i < s.plan->nin; i++) {
     if (!data[i]) {
       err = "data block is NULL";
@@ -209,6 +213,10 @@ int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *no
   s.type = 0;
   int rc = decode_plan(c, nodes, want, s.plan, err);
   if (rc) return rc;
+  if (!s.plan->parts.empty()) {
+    err = "code too large for the batched kernel (its reconstruction runs as several launches)";
+    return kEUnsupported;
+  }
   const int KA = c->m.k * c->m.alpha, K = c->m.K;  // node blocks read, data blocks out
   for (int i = 0; i < KA; i++) s.ptrs.push_back(const_cast<uint8_t *>(node_blocks[i]));
   for (int r = 0; r < K; r++) s.ptrs.push_back(want[r] ? data_out[r] : nullptr);

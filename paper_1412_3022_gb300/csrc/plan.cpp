@@ -56,7 +56,85 @@ static int round_rows(int r) {
   return R;
 }
 
+// A plan above kMaxSlots slots, or with a block of more split tables than
+// shared memory holds (see plan.h): the wanted rows, in the order
+// of their support groups, are packed into sets of at most kPartRows rows.
+// A set of rows with at most kPartCols non-zero columns each grows while the
+// union of its columns stays within kPartCols (block-diagonal and sparse
+// matrices then need no accumulation); a set holding a wider row takes rows
+// up to kPartRows and its columns are cut into balanced chunks of at most
+// kPartCols.  One part per (row set, column chunk): the first chunk of a set
+// writes its outputs, the later ones accumulate into them.
+static std::shared_ptr<Plan> make_parts(const Mat &M, const std::vector<int> &out_slot, int nout) {
+  auto plan = std::make_shared<Plan>();
+  plan->nin = M.cols;
+  plan->nout = nout;
+  std::map<std::vector<int>, std::vector<int>> groups;
+  std::vector<std::vector<int>> order;
+  for (int r = 0; r < M.rows; r++) {
+    if (out_slot[r] < 0) continue;
+    std::vector<int> sup;
+    for (int c = 0; c < M.cols; c++)
+      if (M.at(r, c)) sup.push_back(c);
+    auto it = groups.find(sup);
+    if (it == groups.end()) {
+      order.push_back(sup);
+      groups[sup].push_back(r);
+    } else {
+      it->second.push_back(r);
+    }
+  }
+  std::vector<int> set;
+  std::vector<char> used(M.cols, 0);
+  int nused = 0;
+  bool wide = false;
+  auto flush = [&]() {
+    std::vector<int> cols;
+    for (int c = 0; c < M.cols; c++)
+      if (used[c]) cols.push_back(c);
+    const size_t nch = std::max<size_t>(1, (cols.size() + kPartCols - 1) / kPartCols);
+    for (size_t j = 0; j < nch; j++) {
+      PlanPart pt;
+      pt.in_cols.assign(cols.begin() + cols.size() * j / nch, cols.begin() + cols.size() * (j + 1) / nch);
+      pt.accumulate = j > 0;
+      Mat S((int)set.size(), (int)pt.in_cols.size());
+      std::vector<int> slot(set.size());
+      for (size_t q = 0; q < set.size(); q++) {
+        bool any = false;
+        for (size_t i = 0; i < pt.in_cols.size(); i++) {
+          S.at((int)q, (int)i) = M.at(set[q], pt.in_cols[i]);
+          any = any || S.at((int)q, (int)i) != 0;
+        }
+        slot[q] = (pt.accumulate && !any) ? -1 : (int)q;  // nothing to add from this chunk
+        pt.out_slots.push_back(out_slot[set[q]]);
+      }
+      pt.plan = make_plan(S, slot, (int)set.size());
+      plan->nnz += pt.plan->nnz;
+      plan->parts.push_back(std::move(pt));
+    }
+    set.clear();
+    std::fill(used.begin(), used.end(), 0);
+    nused = 0;
+    wide = false;
+  };
+  for (auto &sup : order)
+    for (int r : groups[sup]) {
+      const bool w = (int)sup.size() > kPartCols;
+      if (!set.empty()) {
+        int grown = nused;
+        for (int c : sup) grown += !used[c];
+        if ((int)set.size() == kPartRows || (!wide && (w || grown > kPartCols))) flush();
+      }
+      set.push_back(r);
+      for (int c : sup) nused += !used[c], used[c] = 1;
+      wide = wide || w;
+    }
+  if (!set.empty()) flush();
+  return plan;
+}
+
 std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, int nout) {
+  if (M.cols + nout > kMaxSlots) return make_parts(M, out_slot, nout);
   auto plan = std::make_shared<Plan>();
   plan->nin = M.cols;
   plan->nout = nout;
@@ -153,6 +231,8 @@ std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, 
     nent += b.coef.size();
     plan->max_entries = std::max(plan->max_entries, (int)b.coef.size());
   }
+  // a block's split tables are staged in shared memory (20 bytes an entry)
+  if (plan->max_entries > kPartCols * kMaxBlockRows) return make_parts(M, out_slot, nout);
   plan->idx_base = nb * sizeof(BlockDesc);
   plan->tab4_base = (plan->idx_base + nidx * 2 + 15) & ~(size_t)15;
   plan->tab1_base = plan->tab4_base + nent * sizeof(TabEntry);
@@ -181,6 +261,19 @@ std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, 
     memcpy(img + i * sizeof(BlockDesc), &d, sizeof d);
   }
   return plan;
+}
+
+std::vector<int> plan_reads(const Plan &p) {
+  std::vector<char> r(p.nin, 0);
+  for (const auto &b : p.blocks)
+    for (uint16_t s : b.inputs) r[s] = 1;
+  for (const auto &pt : p.parts)
+    for (const auto &b : pt.plan->blocks)
+      for (uint16_t s : b.inputs) r[pt.in_cols[s]] = 1;
+  std::vector<int> out;
+  for (int i = 0; i < p.nin; i++)
+    if (r[i]) out.push_back(i);
+  return out;
 }
 
 }  // namespace pmrc

@@ -20,6 +20,12 @@ namespace pmrc {
 
 constexpr int kMaxBlockRows = 16;   // rows held in registers per block
 constexpr int kMaxSlots = 1024;     // input + output pointers per launch
+// a matrix with more inputs + outputs than one launch takes, or a block of
+// more than kPartCols x kMaxBlockRows coefficients (164 KiB of split tables
+// in shared memory), is run as parts of at most kPartRows rows x kPartCols
+// inputs
+constexpr int kPartRows = 512;
+constexpr int kPartCols = 512;
 
 // Device image of one block (the arrays live in the same allocation).
 struct BlockDesc {
@@ -42,6 +48,19 @@ struct PlanBlock {
   std::vector<uint8_t> coef;     // inputs.size() x R, input-major
 };
 
+struct Plan;
+
+// One launch of a plan too large for a single launch: rows `out_slots` of M
+// restricted to the inputs `in_cols` (caller slot numbers).  The first part
+// of a row set writes its outputs; the parts of later input chunks of the
+// same rows XOR into them (accumulate), so they must run after it, in order.
+struct PlanPart {
+  std::shared_ptr<Plan> plan;
+  std::vector<int> in_cols;
+  std::vector<int> out_slots;
+  bool accumulate = false;
+};
+
 struct Plan {
   int nin = 0, nout = 0;  // slots the caller supplies
   int R = 1;              // rows per block in the kernel (1, 2, 4, 8 or 16)
@@ -52,6 +71,8 @@ struct Plan {
   std::vector<uint8_t> image;
   size_t idx_base = 0, tab4_base = 0, tab1_base = 0;
   int max_entries = 0;    // largest ninputs x R of a block
+  // non-empty when nin + nout > kMaxSlots: the launches that replace `blocks`
+  std::vector<PlanPart> parts;
   // per-device copies of `image`
   std::mutex mu;
   std::map<int, void *> dev;
@@ -62,7 +83,11 @@ struct Plan {
 
 // out_slot[r] is the output slot of row r (or -1 to skip the row).  Input
 // slots are the columns of M; in the device image output slots are stored
-// after them (slot index = M.cols + out_slot).
+// after them (slot index = M.cols + out_slot).  Above kMaxSlots slots the
+// plan is cut into parts (see PlanPart).
 std::shared_ptr<Plan> make_plan(const Mat &M, const std::vector<int> &out_slot, int nout);
+
+// The input slots (columns of M) the plan reads, in increasing order.
+std::vector<int> plan_reads(const Plan &p);
 
 }  // namespace pmrc

@@ -42,6 +42,7 @@ struct RegionArgs {
   uint32_t tab1_base;    // byte offset of the T2 word array
   uint32_t ntiles;       // ceil(nbytes / (blockDim.x * kVec))
   int aligned;           // every pointer is 16-byte aligned
+  int accumulate;        // XOR the results into the outputs (a later input chunk)
   MulConsts k;
   uint8_t *ptr[MAXP];    // input slots, then output slots
 };
@@ -83,7 +84,13 @@ __global__ void __launch_bounds__(kThreads)
     for (int r = 0; r < R; r++) {
       if (r < nrows) {
         uint8_t *o = a.ptr[s_slot[nin + r]];
-        if (o) store16(o, off, a.nbytes, vec, acc_bytes(acc[r]));
+        if (!o) continue;
+        uint4 v = acc_bytes(acc[r]);
+        if (a.accumulate) {
+          const uint4 p = load16(o, off, a.nbytes, vec);
+          v = make_uint4(v.x ^ p.x, v.y ^ p.y, v.z ^ p.z, v.w ^ p.w);
+        }
+        store16(o, off, a.nbytes, vec, v);
       }
     }
   }
@@ -91,7 +98,8 @@ __global__ void __launch_bounds__(kThreads)
 
 template <int R, int MAXP>
 cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *in,
-                     uint8_t *const *out, size_t nbytes, bool aligned, cudaStream_t st) {
+                     uint8_t *const *out, size_t nbytes, bool aligned, bool accumulate,
+                     cudaStream_t st) {
   RegionArgs<MAXP> a;
   a.image = static_cast<const uint8_t *>(image);
   a.nbytes = nbytes;
@@ -111,6 +119,7 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   const uint64_t tile = (uint64_t)threads * kVec;
   a.ntiles = (uint32_t)((nbytes + tile - 1) / tile);
   a.aligned = aligned ? 1 : 0;
+  a.accumulate = accumulate ? 1 : 0;
   a.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
   for (int i = 0; i < plan.nin; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
   for (int j = 0; j < plan.nout; j++) a.ptr[plan.nin + j] = out[j];
@@ -140,20 +149,18 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
 
 template <int MAXP>
 cudaError_t launch_p(const Plan &plan, const void *image, const uint8_t *const *in,
-                     uint8_t *const *out, size_t nbytes, bool aligned, cudaStream_t st) {
+                     uint8_t *const *out, size_t nbytes, bool aligned, bool acc, cudaStream_t st) {
   switch (plan.R) {
-    case 1: return launch_t<1, MAXP>(plan, image, in, out, nbytes, aligned, st);
-    case 2: return launch_t<2, MAXP>(plan, image, in, out, nbytes, aligned, st);
-    case 4: return launch_t<4, MAXP>(plan, image, in, out, nbytes, aligned, st);
-    case 8: return launch_t<8, MAXP>(plan, image, in, out, nbytes, aligned, st);
-    default: return launch_t<16, MAXP>(plan, image, in, out, nbytes, aligned, st);
+    case 1: return launch_t<1, MAXP>(plan, image, in, out, nbytes, aligned, acc, st);
+    case 2: return launch_t<2, MAXP>(plan, image, in, out, nbytes, aligned, acc, st);
+    case 4: return launch_t<4, MAXP>(plan, image, in, out, nbytes, aligned, acc, st);
+    case 8: return launch_t<8, MAXP>(plan, image, in, out, nbytes, aligned, acc, st);
+    default: return launch_t<16, MAXP>(plan, image, in, out, nbytes, aligned, acc, st);
   }
 }
 
-}  // namespace
-
-int launch_region(Plan &plan, const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
-                  cudaStream_t stream, std::string &err) {
+int launch_one(Plan &plan, const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
+               bool accumulate, cudaStream_t stream, std::string &err) {
   if (plan.nin + plan.nout > kMaxSlots) {
     err = "too many blocks for one launch (input + output pointers > 1024)";
     return kEUnsupported;
@@ -172,12 +179,40 @@ int launch_region(Plan &plan, const uint8_t *const *in, uint8_t *const *out, siz
   const void *image = nullptr;
   int rc = plan.device_image(&image, err);
   if (rc) return rc;
-  cudaError_t e = (plan.nin + plan.nout <= 256)
-                      ? launch_p<256>(plan, image, in, out, nbytes, aligned, stream)
-                      : launch_p<kMaxSlots>(plan, image, in, out, nbytes, aligned, stream);
+  cudaError_t e =
+      (plan.nin + plan.nout <= 256)
+          ? launch_p<256>(plan, image, in, out, nbytes, aligned, accumulate, stream)
+          : launch_p<kMaxSlots>(plan, image, in, out, nbytes, aligned, accumulate, stream);
   if (e != cudaSuccess) {
     err = std::string("region kernel launch: ") + cudaGetErrorString(e);
     return kECuda;
+  }
+  return kOk;
+}
+
+}  // namespace
+
+int launch_region(Plan &plan, const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
+                  cudaStream_t stream, std::string &err) {
+  if (plan.parts.empty()) return launch_one(plan, in, out, nbytes, false, stream, err);
+  // a plan too large for one launch: its parts in order, on the same stream
+  // (an accumulating part follows the part that wrote its outputs); the
+  // inputs are checked before the first part runs
+  if (nbytes == 0) return kOk;
+  for (int s : plan_reads(plan))
+    if (!in[s]) {
+      err = "a block the operation reads is NULL";
+      return kEInval;
+    }
+  std::vector<const uint8_t *> in2;
+  std::vector<uint8_t *> out2;
+  for (auto &pt : plan.parts) {
+    in2.resize(pt.in_cols.size());
+    out2.resize(pt.out_slots.size());
+    for (size_t i = 0; i < pt.in_cols.size(); i++) in2[i] = in[pt.in_cols[i]];
+    for (size_t j = 0; j < pt.out_slots.size(); j++) out2[j] = out[pt.out_slots[j]];
+    const int rc = launch_one(*pt.plan, in2.data(), out2.data(), nbytes, pt.accumulate, stream, err);
+    if (rc) return rc;
   }
   return kOk;
 }

@@ -136,6 +136,43 @@ def test_plan_structure():
     assert st["entries"] <= 1.5 * st["nnz"]
 
 
+def test_plans_above_one_launch_are_cut_into_parts():
+    """Matrices above 1024 block pointers, or with blocks whose split tables
+    would overflow shared memory, run as parts: every non-zero coefficient
+    is still planned exactly once, and a block-diagonal matrix (helper
+    projections of a k = 32 code) needs no zero products or accumulation."""
+    a = 31
+    phi = np.arange(1, a + 1, dtype=np.uint8)
+    M = np.zeros((62, 62 * a), np.uint8)
+    for h in range(62):
+        M[h, h * a:(h + 1) * a] = phi
+    st = P.pmrc_plan_stats(M)
+    assert st["nnz"] == st["entries"] == 62 * a and st["R"] == 1
+    assert st["input_splits"] == 62 * a            # each helper block read once
+    rng = np.random.default_rng(5)
+    D = rng.integers(0, 256, (700, 600), dtype=np.uint8)  # dense rows of 600 inputs
+    st = P.pmrc_plan_stats(D)
+    assert st["nnz"] == int((D != 0).sum())
+    assert st["R"] <= 16 and st["entries"] >= st["nnz"]
+    # 600 columns > 512 per part: every block reads one of two 300-input chunks
+    assert st["input_splits"] == 300 * st["blocks"]
+    S = rng.integers(0, 256, (300, 900), dtype=np.uint8) * (rng.random((300, 900)) < 0.05)
+    st = P.pmrc_plan_stats(S.astype(np.uint8))
+    assert st["nnz"] == int((S != 0).sum())
+
+
+@pytest.mark.parametrize("n,k", [(48, 24), (64, 32)])
+def test_codes_beyond_one_launch_are_created(n, k):
+    """k >= 24 at n = 2k needs more than 1024 block pointers per encode; the
+    code is built (its operations run as several launches)."""
+    for cons, form in [(P.PMRC_SPARSE, P.PMRC_SYSTEMATIC), (P.PMRC_VANILLA, P.PMRC_NONSYSTEMATIC)]:
+        c = P.Code(n, k, cons, form)
+        assert (c.alpha, c.data_blocks, c.coded_blocks) == (k - 1, k * (k - 1), n * (k - 1))
+    if k == 24:
+        G = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC).generator()
+        assert np.array_equal(G, O.generator(n, k, 1, systematic=True))
+
+
 def test_encode_kernel_choice():
     for n, k, cons, form in [(16, 8, 1, 1), (16, 8, 0, 0), (8, 4, 1, 1)]:
         c = P.Code(n, k, cons, form)
