@@ -122,7 +122,8 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-mbr", action="store_true")
     p.add_argument("--no-sweep", action="store_true",
-                   help="skip the block-size sweep (64 KiB - 4 MiB) of encode, repair, decode")
+                   help="skip the block-size sweep (64 KiB - 4 MiB) and the k sweep (4 - 32) "
+                        "of encode, repair, decode")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the rows outside the step (fused repair, specific algorithms, "
                         "PM-MBR, Reed-Solomon), e.g. for a launch list of the step alone")
@@ -423,6 +424,8 @@ def run_ours(args, rank, world, local_rank):
             per_op.update(run_gf16(torch, P, inputs, args, flush, stream, dev, hbm))
     sweep = None if (args.no_sweep or args.no_extra) else run_sweep(torch, P, inputs, args, flush,
                                                                     stream, dev, hbm)
+    ksweep = None if (args.no_sweep or args.no_extra) else run_ksweep(torch, P, inputs, args, flush,
+                                                                      stream, dev)
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
@@ -447,6 +450,8 @@ def run_ours(args, rank, world, local_rank):
         result["e2e"] = e2e
     if sweep:
         result["block_sweep"] = sweep
+    if ksweep:
+        result["k_sweep"] = ksweep
     if batched:
         result["batched"] = batched
     if serving:
@@ -478,6 +483,61 @@ def run_sweep(torch, P, inputs, args, flush, stream, dev, hbm):
         row["decode"]["missing_rows"] = W.decode_missing
         out[f"{B >> 10} KiB"] = row
         del W
+    torch.cuda.synchronize()
+    return out
+
+
+def run_ksweep(torch, P, inputs, args, flush, stream, dev):
+    """Throughput against k, the axis of the paper's encode and repair
+    figures (Sec. 4, k up to 32 at 16 KB blocks): the n = 2k sparse
+    systematic code for k in {4, 8, 12, 16, 24, 32} at 16 KiB and 1 MiB
+    blocks -- systematic encode, repair of a seeded node (helper projections
+    + newcomer) and lazy reconstruction from a seeded k-node set.  From
+    k = 24 the operations exceed one launch's 1024 block pointers and run as
+    several launches."""
+    out = {}
+    st = int(torch.cuda.current_stream(dev).cuda_stream)
+    for B in (16 << 10, 1 << 20):
+        rows = {}
+        for k in (4, 8, 12, 16, 24, 32):
+            n, a, d, K = 2 * k, k - 1, 2 * k - 2, k * (k - 1)
+            seed = args.seed + 900 + k
+            c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+            Y = torch.empty((n * a, B), dtype=torch.uint8, device=dev)
+            Y[:K] = inputs.device_blocks(K, B, seed, device=dev)
+            x_arr = P.ptr_array([Y[i] for i in range(K)])
+            par_arr = P.ptr_array([Y[K + r] for r in range(n * a - K)])
+            c.encode(x_arr, par_arr, B, st)
+            f = inputs.failed_node(n, seed)
+            H_arr = P.int_array(c.default_helpers(f))
+            h_in = P.ptr_array([Y[a * h + j] for h in H_arr for j in range(a)])
+            recv = torch.empty((d, B), dtype=torch.uint8, device=dev)
+            node = torch.empty((a, B), dtype=torch.uint8, device=dev)
+            recv_arr = P.ptr_array([recv[i] for i in range(d)])
+            node_arr = P.ptr_array([node[j] for j in range(a)])
+            S = inputs.node_subset(n, k, seed)
+            Xr = torch.empty((K, B), dtype=torch.uint8, device=dev)
+            dec_in = [Y[a * i + j] for i in S for j in range(a)]
+            dec_out = [Xr[r] for r in range(K)]
+            for pos, i in enumerate(S):       # data blocks of surviving data nodes stay put
+                if i < k:
+                    for j in range(a):
+                        dec_out[a * i + j] = dec_in[a * pos + j]
+            S_arr, din, dout = P.int_array(S), P.ptr_array(dec_in), P.ptr_array(dec_out)
+            ops = {
+                "sys_encode": (lambda: c.encode(x_arr, par_arr, B, st), K * B),
+                "repair": (lambda: (c.repair_helpers(f, H_arr, h_in, recv_arr, B, st),
+                                    c.repair_newcomer(f, H_arr, recv_arr, node_arr, B, st)), a * B),
+                "decode": (lambda: c.decode(S_arr, din, dout, B, st), K * B),
+            }
+            row = {}
+            for name, (fn, user) in ops.items():
+                ms = time_op(torch, stream, flush, args, fn)
+                row[name] = {"ms": round(ms, 4), "user_GBps": round(user / (ms * 1e-3) / 1e9, 2)}
+            row["decode"]["missing_rows"] = a * sum(1 for i in range(k) if i not in S)
+            rows[f"k={k}"] = row
+            del Y, recv, node, Xr, c
+        out[f"{B >> 10} KiB"] = rows
     torch.cuda.synchronize()
     return out
 
