@@ -250,13 +250,25 @@ int pmrc_encode_precode(const pmrc_code *code, const uint8_t *const *data,
                         uint8_t *const *parity, size_t block_bytes, void *workspace,
                         size_t workspace_bytes, pmrc_stream_t stream);
 
-/* Encode kernel of a handle.  PMRC_KERNEL_AUTO (default): the bitsliced
- * kernel when one was generated at build time for this code (and the call's
- * pointers are 16-byte aligned, with no NULL output), the nibble-table kernel
- * otherwise.  PMRC_KERNEL_GENERIC: always the nibble-table kernel.
- * PMRC_KERNEL_BITSLICED: like AUTO, but PMRC_EUNSUPPORTED here if this code
- * has no generated kernel.  Results are identical; only speed differs.  Do
- * not change it while encodes on the handle are being issued. */
+/* Encode kernel of a handle.  A bitsliced kernel runs when the call's
+ * pointers are 16-byte aligned with no NULL output: the one generated at
+ * build time for this code, or one compiled at run time (NVRTC) for its
+ * encode matrix on the first such encode and cached in the handle.  A
+ * run-time schedule fits when inputs + outputs <= 512 blocks, in at most 64
+ * blocks of 8 rows (rows of identical support, else consecutive rows) of at
+ * most 64 inputs each -- e.g. the sparse systematic codes up to k = 16 at
+ * n = 2k; its compilation takes seconds to minutes as the matrix grows (the
+ * per-code initialization Sec. 4 reports apart from throughput).
+ * PMRC_KERNEL_AUTO (default): the built-in kernel; a run-time one for blocks
+ * of at least 256 KiB and encode matrices of at most 2048 non-zero
+ * coefficients (k <= 10 sparse systematic at n = 2k); the nibble-table
+ * kernel otherwise.  PMRC_KERNEL_GENERIC: always the nibble-table kernel.
+ * PMRC_KERNEL_BITSLICED: a bitsliced kernel at any size and matrix that
+ * fits; PMRC_EUNSUPPORTED here if the code has no built-in kernel and its
+ * matrix does not fit a run-time one (or NVRTC is missing), and from
+ * pmrc_encode if the compilation fails.  Results are identical; only speed
+ * differs.  Do not change it while encodes on the handle are being
+ * issued. */
 enum { PMRC_KERNEL_AUTO = 0, PMRC_KERNEL_GENERIC = 1, PMRC_KERNEL_BITSLICED = 2 };
 int pmrc_set_encode_kernel(pmrc_code *code, int which);
 

@@ -14,6 +14,7 @@
 #include "api_internal.h"
 #include "bitslice.h"
 #include "code.h"
+#include "jit.h"
 #include "plan.h"
 #include "region.h"
 
@@ -168,6 +169,11 @@ namespace {
 constexpr size_t kRuntimeMinBytes = 256 << 10;
 constexpr size_t kRuntimeNewcomerMinBytes = 4 << 20;
 constexpr int kRuntimeMaxInputs = 64;
+// AUTO compiles an encode schedule at run time only for encode matrices of
+// at most this many non-zero coefficients: NVRTC's time grows faster than
+// the schedule (GB300 host: a few seconds at 2048, tens of seconds at
+// k = 16, n = 32); larger codes take it with PMRC_KERNEL_BITSLICED
+constexpr int64_t kRuntimeAutoMaxNnz = 2048;
 
 // GF(2^16) codes: user block i (B bytes, two byte planes) is the pair of
 // GF(2^8) sub-blocks 2i (low plane) and 2i + 1 (high plane) of B/2 bytes.
@@ -207,7 +213,8 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream);
 std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
                                                 const std::function<int(Mat &, std::string &)> &make,
-                                                std::string &err);
+                                                std::string &err, bool by_support = false);
+void encode_matrix(const pmrc_code *c, Mat &M);
 bool want_runtime(const pmrc_code *c, int policy, size_t nbytes, size_t auto_min);
 
 }  // namespace
@@ -231,15 +238,13 @@ int pmrc_create_field(int n, int k, int d, int construction, int form, int field
   int rc = field_bits == 16 ? build_code16(n, k, d, construction, form, c->m, err)
                             : build_code(n, k, d, construction, form, c->m, err);
   if (rc) return fail(rc, err);
-  const int K = c->m.K, N = c->m.N;
   // encode plan: all rows (non-systematic) or the parity nodes' rows
   // (systematic: the first k nodes hold the data)
-  const int first = form ? k * c->m.alpha : 0;
-  Mat M(N - first, K);
-  std::copy(c->m.Gcode.v.begin() + (size_t)first * K, c->m.Gcode.v.end(), M.v.begin());
-  std::vector<int> slot(N - first);
-  for (int r = 0; r < N - first; r++) slot[r] = r;
-  c->encode = make_plan(M, slot, N - first);
+  Mat M;
+  encode_matrix(c.get(), M);
+  std::vector<int> slot(M.rows);
+  for (int r = 0; r < M.rows; r++) slot[r] = r;
+  c->encode = make_plan(M, slot, M.rows);
   c->bs_id = bitslice_find(n, k, construction, form, bitslice_checksum(M.v.data(), M.v.size()));
   *out = c.release();
   g_last_error.clear();
@@ -358,8 +363,16 @@ int pmrc_set_decode_kernel(pmrc_code *c, int which) {
 int pmrc_set_encode_kernel(pmrc_code *c, int which) {
   if (!c || which < PMRC_KERNEL_AUTO || which > PMRC_KERNEL_BITSLICED)
     return fail(PMRC_EINVAL, "bad handle or kernel choice");
-  if (which == PMRC_KERNEL_BITSLICED && c->bs_id < 0)
-    return fail(PMRC_EUNSUPPORTED, "no bitsliced kernel was generated for this code");
+  if (which == PMRC_KERNEL_BITSLICED && c->bs_id < 0) {
+    // no built-in schedule: the encode matrix must fit a run-time kernel
+    if (!jit_available())
+      return fail(PMRC_EUNSUPPORTED, "no built-in bitsliced kernel for this code, and NVRTC is missing");
+    Mat M;
+    encode_matrix(c, M);
+    std::string err;
+    if (bitslice_check(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, true, err))
+      return fail(PMRC_EUNSUPPORTED, "no bitsliced kernel for this code: " + err);
+  }
   c->encode_kernel = which;
   return PMRC_OK;
 }
@@ -387,15 +400,33 @@ int encode_body(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *
   std::string err;
   const Plan &P = *c->encode;
   size_t done = 0;
-  if (c->bs_id >= 0 && c->encode_kernel != PMRC_KERNEL_GENERIC && nbytes >= 32) {
+  const int policy = c->encode_kernel;
+  if (policy != PMRC_KERNEL_GENERIC && nbytes >= 32) {
     bool ok = true;
     for (int i = 0; i < P.nin && ok; i++) ok = data[i] && ((uintptr_t)data[i] % 16 == 0);
     for (int j = 0; j < P.nout && ok; j++) ok = out[j] && ((uintptr_t)out[j] % 16 == 0);
-    if (ok) {
+    if (ok && c->bs_id >= 0) {
       done = nbytes & ~(size_t)31;
       cudaError_t e = bitslice_launch(c->bs_id, data, out, done, (cudaStream_t)stream);
       if (e != cudaSuccess)
         return fail(PMRC_ECUDA, std::string("bitsliced encode launch: ") + cudaGetErrorString(e));
+    } else if (ok && (policy == PMRC_KERNEL_BITSLICED ||
+                      (nbytes >= kRuntimeMinBytes && P.nnz <= kRuntimeAutoMaxNnz))) {
+      // no built-in schedule for this code: its encode matrix compiled at
+      // run time (rows of identical support in blocks, as the built-in ones)
+      std::string rerr;
+      std::shared_ptr<BsRuntimeKernel> k = runtime_kernel(c, "e", [&](Mat &M, std::string &) {
+        encode_matrix(c, M);
+        return (int)kOk;
+      }, rerr, true);
+      if (k) {
+        done = nbytes & ~(size_t)31;
+        const cudaError_t e = bitslice_launch_runtime(*k, data, out, done, (cudaStream_t)stream);
+        if (e != cudaSuccess)
+          return fail(PMRC_ECUDA, std::string("bitsliced encode launch: ") + cudaGetErrorString(e));
+      } else if (policy == PMRC_KERNEL_BITSLICED) {
+        return fail(PMRC_EUNSUPPORTED, "bitsliced encode: " + rerr);
+      }
     }
   }
   if (done == nbytes) return PMRC_OK;
@@ -585,11 +616,21 @@ int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node
 
 namespace {
 
-// A bitsliced kernel compiled at run time for matrix M, cached in the handle
-// under `key`; null when it cannot be built (the reason in err, also cached).
+// The rows pmrc_encode writes: every row of the code's generator
+// (non-systematic form) or the parity nodes' rows of G' (systematic form).
+void encode_matrix(const pmrc_code *c, Mat &M) {
+  const int K = c->m.K, N = c->m.N, first = c->m.systematic ? c->m.k * c->m.alpha : 0;
+  M = Mat(N - first, K);
+  std::copy(c->m.Gcode.v.begin() + (size_t)first * K, c->m.Gcode.v.end(), M.v.begin());
+}
+
+// A bitsliced kernel compiled at run time for matrix M (blocks of rows of
+// identical support when by_support, else consecutive rows), cached in the
+// handle under `key`; null when it cannot be built (the reason in err, also
+// cached).
 std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
                                                 const std::function<int(Mat &, std::string &)> &make,
-                                                std::string &err) {
+                                                std::string &err, bool by_support) {
   std::lock_guard<std::mutex> g(c->jit_mu);
   {
     std::lock_guard<std::mutex> g2(c->mu);
@@ -602,7 +643,8 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
   std::shared_ptr<BsRuntimeKernel> k;
   Mat M;
   int rc = make(M, err);
-  if (!rc && M.rows > 0) rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, k, err);
+  if (!rc && M.rows > 0)
+    rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support, k, err);
   std::lock_guard<std::mutex> g2(c->mu);
   if (c->rt.size() >= kPlanCacheCap) {
     if (c->rt.begin()->second) c->rt_retired.push_back(c->rt.begin()->second);

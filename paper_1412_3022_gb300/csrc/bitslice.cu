@@ -159,13 +159,9 @@ struct BsRuntimeKernel {
   }
 };
 
-int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs,
-                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
-  if (rows <= 0 || cols <= 0 || rows + cols > kBsMaxPtr) {
-    err = "matrix too large for one bitsliced launch";
-    return kEUnsupported;
-  }
-  const std::vector<BsBlock> blks = bs_blocks_chunked(M, rows, cols);
+namespace {
+
+int check_blocks(const std::vector<BsBlock> &blks, int max_inputs, std::string &err) {
   if ((int)blks.size() > kBsMaxBlocks) {
     err = "too many blocks for one bitsliced launch";
     return kEUnsupported;
@@ -175,6 +171,39 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs,
       err = "a block reads more inputs than the run-time kernels take";
       return kEUnsupported;
     }
+  return kOk;
+}
+
+// The blocks of a run-time schedule: rows of identical support when asked
+// (encode matrices), unless that gives too many blocks or too wide ones;
+// consecutive rows over the union of their inputs otherwise.
+int runtime_blocks(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                   std::vector<BsBlock> &blks, std::string &err) {
+  if (rows <= 0 || cols <= 0 || rows + cols > kBsMaxPtr) {
+    err = "matrix too large for one bitsliced launch";
+    return kEUnsupported;
+  }
+  if (by_support) {
+    blks = bs_blocks_by_support(M, rows, cols);
+    if (!check_blocks(blks, max_inputs, err)) return kOk;
+  }
+  blks = bs_blocks_chunked(M, rows, cols);
+  return check_blocks(blks, max_inputs, err);
+}
+
+}  // namespace
+
+int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                   std::string &err) {
+  std::vector<BsBlock> blks;
+  return runtime_blocks(M, rows, cols, max_inputs, by_support, blks, err);
+}
+
+int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
+  std::vector<BsBlock> blks;
+  int rc = runtime_blocks(M, rows, cols, max_inputs, by_support, blks, err);
+  if (rc) return rc;
   const char *kname = "bs_runtime_kernel";
   const BsEmitted em = bs_emit_kernel(M, rows, cols, blks, kname, true);
   const std::string src =
@@ -182,7 +211,7 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs,
       "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n" +
       std::string(kBsDevSrc) + "\n" + em.code;
   std::vector<char> cubin;
-  int rc = jit_compile(src, kname, cubin, err);
+  rc = jit_compile(src, kname, cubin, err);
   if (rc) return rc;
   auto k = std::make_shared<BsRuntimeKernel>();
   rc = jit_load(cubin, kname, &k->lib, &k->fn, err);

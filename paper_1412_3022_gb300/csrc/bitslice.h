@@ -28,15 +28,23 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
 int bitslice_max_pointers();
 
 // A bitsliced kernel compiled at run time (NVRTC) for a matrix known only
-// then, e.g. the rows of a reconstruction: rows in blocks of at most 8 over
-// the union of their inputs, the same device code as the built-in kernels.
+// then: the rows of a reconstruction or a newcomer's apply (consecutive rows
+// in blocks of at most 8 over the union of their inputs), or the encode
+// matrix of a code without a built-in kernel (by_support: rows of identical
+// support in blocks of at most 8, unless those do not fit the limits below,
+// then consecutive rows); the same device code as the built-in kernels.
 struct BsRuntimeKernel;
 
-// Builds the kernel for M (rows x cols, row-major).  kEUnsupported when the
-// matrix is too large for one launch (cols + rows > 256 pointers, more than
-// 32 blocks or more than `max_inputs` inputs in a block) or NVRTC is missing
-// or fails (message in err).
-int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs,
+// kOk if M (rows x cols, row-major) fits one run-time launch: cols + rows
+// <= bitslice_max_pointers() (512), at most 64 blocks, at most `max_inputs`
+// inputs in a block; kEUnsupported with a message in err otherwise.  Host
+// only.
+int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                   std::string &err);
+
+// Builds the kernel for M.  kEUnsupported when bitslice_check fails or NVRTC
+// is missing or fails (message in err).
+int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
                    std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
 
 // out[r] = sum_c M[r][c] in[c] over bytes [0, nbytes); nbytes a multiple of

@@ -6,11 +6,11 @@
 // uint16_t, uint32_t and uint64_t to be defined.
 constexpr int kBsThreads = 512;       // one CTA per SM (128 registers a thread)
 constexpr int kBsBytes = 32;          // bytes per thread per tile
-constexpr int kBsMaxPtr = 256;
+constexpr int kBsMaxPtr = 512;       // block pointers per launch
 constexpr int kBsAhead = 4;           // inputs prefetched ahead of the one in use
 constexpr int kBsSlots = kBsAhead + 1;  // shared-memory ring (never the slot being read)
 constexpr uint32_t kBsUnit = 32 * kBsBytes;  // bytes of column per warp tile
-constexpr int kBsMaxBlocks = 32;
+constexpr int kBsMaxBlocks = 64;     // dense blocks per schedule
 
 struct BsArgs {
   uint64_t nbytes;  // bytes covered by this launch (multiple of kBsBytes)

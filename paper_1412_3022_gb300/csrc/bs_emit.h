@@ -20,7 +20,7 @@
 namespace pmrc {
 
 constexpr int kBsEmitRows = 8;        // rows per block (8 x 8 bit-plane accumulators)
-constexpr int kBsEmitMaxBlocks = 32;  // bitslice_dev.cuh: kBsMaxBlocks
+constexpr int kBsEmitMaxBlocks = 64;  // bitslice_dev.cuh: kBsMaxBlocks
 
 struct BsBlock {
   std::vector<int> rows, inputs;

@@ -178,11 +178,20 @@ def test_encode_kernel_choice():
         c = P.Code(n, k, cons, form)
         c.set_encode_kernel(P.PMRC_KERNEL_BITSLICED)
         c.set_encode_kernel(P.PMRC_KERNEL_GENERIC)
+    # no built-in schedule: a run-time one when the encode matrix fits it
+    # (k = 12: 264 blocks, 22 blocks of 22 inputs), unless NVRTC is missing
     c = P.Code(24, 12, 1, 1)
+    try:
+        c.set_encode_kernel(P.PMRC_KERNEL_BITSLICED)
+    except P.PMRCError as e:
+        assert e.rc == P.PMRC_EUNSUPPORTED and "NVRTC" in str(e)
+    c.set_encode_kernel(P.PMRC_KERNEL_AUTO)
+    # too large for one bitsliced launch (1984 block pointers)
+    c = P.Code(64, 32, 1, 1)
     with pytest.raises(P.PMRCError) as e:
         c.set_encode_kernel(P.PMRC_KERNEL_BITSLICED)
     assert e.value.rc == P.PMRC_EUNSUPPORTED
-    c.set_encode_kernel(P.PMRC_KERNEL_AUTO)
+    c.set_encode_kernel(P.PMRC_KERNEL_GENERIC)
 
 
 @pytest.mark.parametrize("S", [list(range(16)), list(range(16, 32)),
