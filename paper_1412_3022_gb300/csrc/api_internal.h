@@ -23,8 +23,9 @@ struct pmrc_code {
   mutable std::map<std::string, std::shared_ptr<pmrc::Plan>> cache;
   mutable std::map<std::string, std::shared_ptr<pmrc::FusedRepairPlan>> fused;
   mutable std::map<std::string, std::shared_ptr<pmrc::SpecificPlan>> specific;
-  // reconstruction kernels compiled at run time, per (nodes, wanted rows);
-  // a null kernel records a pattern that could not be built
+  // bitsliced kernels compiled at run time: reconstruction rows per (nodes,
+  // wanted rows), newcomer applies per (failed node, helpers), the encode
+  // ("e"); a null kernel records a matrix that could not be built
   int decode_kernel = 0;                    // PMRC_KERNEL_*
   mutable std::mutex jit_mu;                // one compilation at a time per handle
   mutable std::map<std::string, std::shared_ptr<pmrc::BsRuntimeKernel>> rt;

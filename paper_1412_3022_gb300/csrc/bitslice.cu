@@ -1,7 +1,10 @@
-// Bitsliced encode kernels for the codes listed in gen_bitslice.cpp.
+// Bitsliced region kernels: the encodes of the codes listed in
+// gen_bitslice.cpp, and schedules compiled at run time (jit.cpp) for other
+// matrices (reconstruction rows, newcomer applies, encodes of other codes).
 //
 // Same operation as region.cu (out[r] = sum_c M[r][c] * in[c], Sec. 2/3.1),
-// for an encode matrix fixed at build time, with a different inner loop:
+// for a matrix fixed when the schedule is generated, with a different inner
+// loop:
 //
 //   * each thread owns 32 consecutive bytes of every block of a tile; it
 //     streams its inputs through a 5-slot shared-memory ring with cp.async,
@@ -26,9 +29,10 @@
 //     KiB), fetched into its instruction caches once and then re-executed;
 //     blocks get CTAs in proportion to their cost.
 //
-// The XOR schedules are generated at build time from the library's own
-// construction (gen_bitslice.cpp); the launcher only uses a kernel whose
-// matrix checksum equals the code's encode matrix.
+// The built-in XOR schedules are generated at build time from the library's
+// own construction (gen_bitslice.cpp); the launcher only uses a kernel whose
+// matrix checksum equals the code's encode matrix.  Run-time schedules come
+// from the same emitter (bs_emit.cpp).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,4 +1,5 @@
-// Bitsliced encode kernels generated at build time (bitslice.cu).
+// Bitsliced region kernels (bitslice.cu): encode schedules generated at
+// build time, and schedules compiled at run time for other matrices.
 #pragma once
 #include <cuda_runtime.h>
 
