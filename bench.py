@@ -426,6 +426,7 @@ def run_ours(args, rank, world, local_rank):
                                                                     stream, dev, hbm)
     ksweep = None if (args.no_sweep or args.no_extra) else run_ksweep(torch, P, inputs, args, flush,
                                                                       stream, dev)
+    init = None if args.no_extra else run_init(torch, P, inputs, args, dev)
     e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
@@ -452,6 +453,8 @@ def run_ours(args, rank, world, local_rank):
         result["block_sweep"] = sweep
     if ksweep:
         result["k_sweep"] = ksweep
+    if init:
+        result["init"] = init
     if batched:
         result["batched"] = batched
     if serving:
@@ -483,6 +486,59 @@ def run_sweep(torch, P, inputs, args, flush, stream, dev, hbm):
         row["decode"]["missing_rows"] = W.decode_missing
         out[f"{B >> 10} KiB"] = row
         del W
+    torch.cuda.synchronize()
+    return out
+
+
+def run_init(torch, P, inputs, args, dev):
+    """Initialization, which the paper reports apart from throughput (Sec. 4):
+    host wall time of building the n=16 k=8 codes (pmrc_create), and of the
+    first reconstruction of a node set and the first repair of a failed node
+    on a fresh handle beyond the same call repeated (host plans, their
+    upload, and the reconstruction kernel compiled at run time), 1 MiB
+    blocks."""
+    B = args.block_bytes
+    out = {}
+    t0 = time.perf_counter()
+    c = P.Code(N_, K_, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    out["create_sparse_systematic_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+    t0 = time.perf_counter()
+    P.Code(N_, K_, P.PMRC_VANILLA, P.PMRC_NONSYSTEMATIC)
+    out["create_vanilla_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+    a, K = A_, K_ * A_
+    seed = args.seed + 700
+    Y = torch.empty((N_ * a, B), dtype=torch.uint8, device=dev)
+    Y[:K] = inputs.device_blocks(K, B, seed, device=dev)
+    c.encode([Y[i] for i in range(K)], [Y[K + r] for r in range(K)], B)
+    S = inputs.node_subset(N_, K_, seed)
+    Xr = torch.empty((K, B), dtype=torch.uint8, device=dev)
+    din = [Y[a * i + j] for i in S for j in range(a)]
+    f = inputs.failed_node(N_, seed)
+    H = c.default_helpers(f)
+    hin = [Y[a * h + j] for h in H for j in range(a)]
+    recv = torch.empty((D_, B), dtype=torch.uint8, device=dev)
+    node = torch.empty((a, B), dtype=torch.uint8, device=dev)
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3
+
+    dec = lambda: c.decode(S, din, [Xr[r] for r in range(K)], B)
+    rep = lambda: (c.repair_helpers(f, H, hin, [recv[i] for i in range(D_)], B),
+                   c.repair_newcomer(f, H, [recv[i] for i in range(D_)], [node[j] for j in range(a)], B))
+    first = wall(dec)
+    again = min(wall(dec) for _ in range(3))
+    out["decode_pattern_first_call_ms"] = round(first, 2)
+    out["decode_pattern_init_ms"] = round(first - again, 2)
+    first = wall(rep)
+    again = min(wall(rep) for _ in range(3))
+    out["repair_pattern_init_ms"] = round(first - again, 2)
+    out["note"] = ("host wall clock; the decode pattern's first call includes compiling its "
+                   "bitsliced kernel (NVRTC)")
+    del Y, Xr, recv, node, c
     torch.cuda.synchronize()
     return out
 
