@@ -286,7 +286,13 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * same choice applies to pmrc_repair_newcomer (its D, per failed node and
  * helper list), where AUTO takes the run-time kernel from 4 MiB blocks and
  * PMRC_KERNEL_BITSLICED falls back to the split-table kernel rather than
- * failing. */
+ * failing.
+ *
+ * Kernels compiled at run time (encode, reconstruction, newcomer) can be
+ * kept across handles and processes: when the environment variable
+ * PMRC_KERNEL_CACHE names a writable directory, each compiled cubin is
+ * stored there under a hash of its source, and a later compilation of the
+ * same schedule reads the file instead of running NVRTC. */
 int pmrc_set_decode_kernel(pmrc_code *code, int which);
 
 /* ---- batched execution ---------------------------------------------------

@@ -8,7 +8,11 @@
 
 #include <dlfcn.h>
 #include <nvrtc.h>
+#include <unistd.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -25,6 +29,7 @@ struct Nvrtc {
   decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
   decltype(&nvrtcGetCUBIN) cubin = nullptr;
   decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  int major = 0, minor = 0;  // NVRTC version (part of the cache key)
 };
 
 const Nvrtc &nvrtc() {
@@ -43,8 +48,55 @@ const Nvrtc &nvrtc() {
     n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
     n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
     n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+    auto version = reinterpret_cast<decltype(&nvrtcVersion)>(dlsym(h, "nvrtcVersion"));
+    if (version) version(&n.major, &n.minor);
   });
   return n;
+}
+
+constexpr int kNumOpts = 3;
+const char *const kOpts[kNumOpts] = {"--gpu-architecture=sm_103a", "-std=c++17", "-w"};
+
+// Path of the cached cubin for this source, or "" without a cache directory.
+std::string cache_path(const std::string &src, const Nvrtc &n) {
+  const char *dir = getenv("PMRC_KERNEL_CACHE");
+  if (!dir || !*dir) return "";
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over source, options, version
+  auto mix = [&](const char *p, size_t len) {
+    for (size_t i = 0; i < len; i++) {
+      h ^= (uint8_t)p[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(src.data(), src.size());
+  for (const char *o : kOpts) mix(o, strlen(o) + 1);
+  const int ver[2] = {n.major, n.minor};
+  mix(reinterpret_cast<const char *>(ver), sizeof ver);
+  char name[64];
+  snprintf(name, sizeof name, "/pmrc-%016llx.cubin", (unsigned long long)h);
+  return std::string(dir) + name;
+}
+
+bool read_cached(const std::string &path, std::vector<char> &cubin) {
+  FILE *f = fopen(path.c_str(), "rb");
+  if (!f) return false;
+  std::vector<char> buf;
+  char chunk[65536];
+  size_t got;
+  while ((got = fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+  fclose(f);
+  if (buf.size() < 4 || memcmp(buf.data(), "\x7f" "ELF", 4) != 0) return false;  // not a cubin
+  cubin.swap(buf);
+  return true;
+}
+
+// Written to a temporary name and renamed, so readers never see a partial file.
+void write_cached(const std::string &path, const std::vector<char> &cubin) {
+  const std::string tmp = path + "." + std::to_string((long long)getpid()) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  const bool ok = fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
+  if (fclose(f) != 0 || !ok || rename(tmp.c_str(), path.c_str()) != 0) remove(tmp.c_str());
 }
 
 }  // namespace
@@ -58,13 +110,14 @@ int jit_compile(const std::string &src, const char *kernel_name, std::vector<cha
     err = "NVRTC (libnvrtc) could not be loaded";
     return kEUnsupported;
   }
+  const std::string cached = cache_path(src, n);
+  if (!cached.empty() && read_cached(cached, cubin)) return kOk;
   nvrtcProgram prog;
   if (n.create(&prog, src.c_str(), kernel_name, 0, nullptr, nullptr) != NVRTC_SUCCESS) {
     err = "nvrtcCreateProgram failed";
     return kEUnsupported;
   }
-  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-w"};
-  const nvrtcResult rc = n.compile(prog, 3, opts);
+  const nvrtcResult rc = n.compile(prog, kNumOpts, kOpts);
   if (rc != NVRTC_SUCCESS) {
     size_t ls = 0;
     n.log_size(prog, &ls);
@@ -79,6 +132,7 @@ int jit_compile(const std::string &src, const char *kernel_name, std::vector<cha
   cubin.assign(cs, 0);
   n.cubin(prog, cubin.data());
   n.destroy(&prog);
+  if (!cached.empty()) write_cached(cached, cubin);
   return kOk;
 }
 

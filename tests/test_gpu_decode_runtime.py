@@ -134,3 +134,27 @@ def test_runtime_newcomer_every_node_k8_and_mbr():
         out = Blocks(am, 4096 + 32)
         m.repair_newcomer(f, H, recv.ptrs(), out.ptrs(), 4096 + 32)
         assert np.array_equal(out.get(), Ym[am * f:am * f + am]), f
+
+
+def test_runtime_kernels_cached_on_disk(tmp_path, monkeypatch):
+    """With PMRC_KERNEL_CACHE set, a compiled schedule is written once and a
+    fresh handle meeting the same node set reads it back."""
+    monkeypatch.setenv("PMRC_KERNEL_CACHE", str(tmp_path))
+    n, k, nbytes = 16, 8, 8192 + 32
+    X = inputs.blocks(56, nbytes, seed=97)
+    Y = O.encode(n, k, O.SPARSE, True, X)
+    S = [15, 0, 9, 2, 11, 4, 13, 6]
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    got, _ = decode(c, S, Y, nbytes)
+    assert np.array_equal(got, X)
+    files = list(tmp_path.glob("pmrc-*.cubin"))
+    assert len(files) == 1
+    stamp = files[0].stat().st_mtime_ns
+    c2 = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c2.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    got, _ = decode(c2, S, Y, nbytes)
+    assert np.array_equal(got, X)
+    assert list(tmp_path.glob("pmrc-*.cubin")) == files
+    assert files[0].stat().st_mtime_ns == stamp     # read back, not rewritten
+    assert not list(tmp_path.glob("*.tmp"))
