@@ -391,6 +391,7 @@ def run_ours(args, rank, world, local_rank):
         except (OSError, ValueError):
             pass
 
+    degraded = None
     if not args.no_extra:
         # the fused single-GPU repair (helper projections kept in scratch)
         fused_ms = time_op(torch, stream, flush, args, lambda: W.sysc.repair(
@@ -418,6 +419,7 @@ def run_ours(args, rank, world, local_rank):
                             "linear_op": linear, "linear_over_specific": round(op_ms[linear] / ms, 3),
                             "launches": 5 if name == "encode_precode" else 4 + (W.decode_missing > 0)}
         del ws
+        degraded = run_degraded(torch, P, inputs, W, args, flush, stream, dev, hbm)
         if not args.no_mbr:
             per_op.update(run_mbr(torch, P, inputs, args, flush, stream, dev, hbm))
             per_op.update(run_rs(torch, P, inputs, args, flush, stream, dev, hbm))
@@ -455,6 +457,8 @@ def run_ours(args, rank, world, local_rank):
         result["k_sweep"] = ksweep
     if init:
         result["init"] = init
+    if degraded:
+        result["degraded_read"] = degraded
     if batched:
         result["batched"] = batched
     if serving:
@@ -488,6 +492,47 @@ def run_sweep(torch, P, inputs, args, flush, stream, dev, hbm):
         del W
     torch.cuda.synchronize()
     return out
+
+
+def run_degraded(torch, P, inputs, W, args, flush, stream, dev, hbm):
+    """Degraded read of a lost systematic node of the stripe's code (a seeded
+    node among the alpha first, whose helpers each contribute one block,
+    Sec. 3.3): its alpha data blocks rebuilt by pmrc_read_degraded from the
+    d helpers, against reading them through a reconstruction from k nodes
+    (the other data nodes and one parity node, only the lost node's rows
+    computed)."""
+    B, a, K = W.B, A_, K_ * A_
+    node = inputs.failed_node(A_, args.seed + 300)
+    c, st = W.sysc, W.stream
+    H = c.default_helpers(node)
+    reads = int((c.helper_coefficients(node) != 0).sum())
+    h_in = P.ptr_array([W.Y[a * h + j] for h in H for j in range(a)])
+    out = torch.empty((a, B), dtype=torch.uint8, device=dev)
+    out_arr = P.ptr_array([out[j] for j in range(a)])
+    H_arr = P.int_array(H)
+    S = [i for i in range(K_) if i != node] + [K_]
+    dec_in = [W.Y[a * i + j] for i in S for j in range(a)]
+    dec_out = [W.data_out[r] for r in range(K)]
+    for pos, i in enumerate(S):             # surviving data stays in place
+        if i < K_:
+            for j in range(a):
+                dec_out[a * i + j] = dec_in[a * pos + j]
+    for j in range(a):
+        dec_out[a * node + j] = out[j]
+    S_arr, din, dout = P.int_array(S), P.ptr_array(dec_in), P.ptr_array(dec_out)
+    R = c.decode_matrix(S)
+    dec_reads = int((R[a * node:a * node + a] != 0).any(axis=0).sum())
+    rows = {}
+    for name, fn, alg in (
+            ("via_repair", lambda: c.read_degraded(node, H_arr, h_in, out_arr, 0, B, st),
+             (D_ * reads + a) * B),
+            ("via_reconstruction", lambda: c.decode(S_arr, din, dout, B, st), (dec_reads + a) * B)):
+        ms = time_op(torch, stream, flush, args, fn)
+        rows[name] = {"ms": round(ms, 4), "user_GBps": round(a * B / (ms * 1e-3) / 1e9, 2),
+                      "blocks_read": alg // B - a, "frac_hbm": round(alg / (ms * 1e-3) / 1e9 / hbm, 4)}
+    rows["node"] = node
+    del out
+    return rows
 
 
 def run_init(torch, P, inputs, args, dev):

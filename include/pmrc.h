@@ -169,6 +169,21 @@ int pmrc_repair(const pmrc_code *code, int failed, const int *helpers,
                 const uint8_t *const *helper_blocks, uint8_t *const *out, size_t block_bytes,
                 pmrc_stream_t stream);
 
+/* Degraded read: bytes [offset, offset + length) of the alpha blocks of a
+ * lost systematic node (node < k on a PMRC_SYSTEMATIC handle), rebuilt by
+ * the repair above from d helpers instead of a reconstruction from k nodes
+ * (the systematic nodes store data verbatim, Sec. 3.2: for PM-MSR node i
+ * holds data blocks alpha*i .. alpha*i + alpha-1).  With the sparse code and
+ * node < alpha each helper contributes one block (Sec. 3.3), so the read
+ * touches d blocks where a reconstruction reads k*alpha.  helper_blocks:
+ * d*alpha pointers to the helpers' whole blocks (as for pmrc_repair; the
+ * call adds `offset`); out: alpha device pointers receiving `length` bytes
+ * each.  PMRC_EINVAL for a non-systematic handle or node >= k; otherwise the
+ * conditions and errors of pmrc_repair. */
+int pmrc_read_degraded(const pmrc_code *code, int node, const int *helpers,
+                       const uint8_t *const *helper_blocks, uint8_t *const *out, size_t offset,
+                       size_t length, pmrc_stream_t stream);
+
 /* pmrc_repair_noalloc: the same repair as pmrc_repair (same arguments, same
  * bytes out) for callers that cannot allocate GPU memory -- for example a
  * library running inside a process whose device memory is owned by another

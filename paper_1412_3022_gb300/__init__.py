@@ -96,6 +96,7 @@ _SIGNATURES = {
     "pmrc_set_encode_kernel": (_i, [_vp, _i]),
     "pmrc_repair": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
     "pmrc_repair_noalloc": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _vp]),
+    "pmrc_read_degraded": (_i, [_vp, _i, _ip, _pp, _pp, _sz, _sz, _vp]),
     "pmrc_batch_create": (_i, [ctypes.POINTER(_vp)]),
     "pmrc_batch_destroy": (None, [_vp]),
     "pmrc_batch_add_encode": (_i, [_vp, _vp, _pp, _pp, _sz]),
@@ -226,6 +227,11 @@ def pmrc_repair_newcomer(code, failed, helpers, received, out, block_bytes, stre
 def pmrc_repair(code, failed, helpers, helper_blocks, out, block_bytes, stream=None):
     _check(lib().pmrc_repair(code, failed, _ints(helpers), _ptrs(helper_blocks), _ptrs(out),
                              block_bytes, _stream(stream)), "pmrc_repair")
+
+
+def pmrc_read_degraded(code, node, helpers, helper_blocks, out, offset, length, stream=None):
+    _check(lib().pmrc_read_degraded(code, node, _ints(helpers), _ptrs(helper_blocks), _ptrs(out),
+                                    offset, length, _stream(stream)), "pmrc_read_degraded")
 
 
 def pmrc_repair_noalloc(code, failed, helpers, helper_blocks, out, block_bytes, stream=None):
@@ -594,6 +600,11 @@ class Code:
 
     def repair(self, failed, helpers, helper_blocks, out, block_bytes, stream=None):
         pmrc_repair(self.handle, failed, helpers, helper_blocks, out, block_bytes, stream)
+
+    def read_degraded(self, node, helpers, helper_blocks, out, offset, length, stream=None):
+        """Bytes [offset, offset + length) of a lost systematic node's blocks,
+        rebuilt from its helpers' whole blocks."""
+        pmrc_read_degraded(self.handle, node, helpers, helper_blocks, out, offset, length, stream)
 
     def decode(self, nodes, node_blocks, data_out, block_bytes, stream=None):
         pmrc_decode(self.handle, nodes, node_blocks, data_out, block_bytes, stream)

@@ -578,6 +578,18 @@ int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *co
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
+int pmrc_read_degraded(const pmrc_code *c, int node, const int *helpers,
+                       const uint8_t *const *blocks, uint8_t *const *out, size_t offset,
+                       size_t length, pmrc_stream_t stream) {
+  if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
+  if (!c->m.systematic) return fail(PMRC_EINVAL, "degraded reads need a systematic handle");
+  if (node < 0 || node >= c->m.k) return fail(PMRC_EINVAL, "node is not a systematic node");
+  const int nb = c->m.d * (is16(c) ? c->m.f16.alpha : c->m.alpha);
+  std::vector<const uint8_t *> shifted(nb);
+  for (int i = 0; i < nb; i++) shifted[i] = blocks[i] ? blocks[i] + offset : nullptr;
+  return pmrc_repair(c, node, helpers, shifted.data(), out, length, stream);
+}
+
 int pmrc_repair_noalloc(const pmrc_code *c, int f, const int *helpers,
                         const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
                         pmrc_stream_t stream) {

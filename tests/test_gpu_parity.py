@@ -432,3 +432,34 @@ def test_fused_repair_full_size_sampled():
             Yc = Y[:, cs].cpu().numpy()
             sent = np.stack([O.repair_helper(n, k, 1, f, Yc[a * h:a * h + a]) for h in H])
             assert np.array_equal(out[:, cs].cpu().numpy(), O.repair_newcomer(n, k, 1, f, H, sent))
+
+
+@pytest.mark.parametrize("node", [3, 7])
+def test_degraded_read_returns_the_nodes_data(node):
+    """A lost systematic node's data, byte ranges included, rebuilt from its
+    helpers (node 3 < alpha: one block per helper; node 7: seven)."""
+    n, k, a, d = 16, 8, 7, 14
+    nbytes = 3 * 4096 + 29
+    X = inputs.blocks(k * a, nbytes, seed=98 + node)
+    Y = O.encode(n, k, 1, True, X)
+    c = code(n, k, 1, 1)
+    H = c.default_helpers(node)
+    hin = Blocks(d * a, nbytes, 0, np.concatenate([Y[a * h:a * h + a] for h in H]))
+    for off, length in ((0, nbytes), (1000, 5003), (nbytes - 17, 17)):
+        out = Blocks(a, length)
+        c.read_degraded(node, H, hin.ptrs(), out.ptrs(), off, length)
+        assert out.guards_intact()
+        assert np.array_equal(out.get(), X[a * node:a * node + a, off:off + length]), (off, length)
+
+
+def test_degraded_read_reed_solomon():
+    n, k, nbytes = 16, 8, 4096 + 3
+    X = inputs.blocks(k, nbytes, seed=99)
+    Y = O.rs_encode(n, k, True, X)
+    c = P.Code(n, k, P.PMRC_RS, P.PMRC_SYSTEMATIC)
+    node = 5
+    H = c.default_helpers(node)
+    hin = Blocks(k, nbytes, 0, Y[H])
+    out = Blocks(1, nbytes - 100)
+    c.read_degraded(node, H, hin.ptrs(), out.ptrs(), 100, nbytes - 100)
+    assert np.array_equal(out.get()[0], X[node, 100:])

@@ -313,3 +313,19 @@ def test_gf16_vanilla_k16_valid_and_errors():
     for f in range(8):
         H = c.default_helpers(f)
         O.gf16_newcomer_matrix(8, 4, O.SPARSE, f, H)   # the oracle agrees it is invertible
+
+
+def test_degraded_read_argument_checks():
+    """Refused before any device work: a non-systematic handle, a node that
+    is not systematic."""
+    H = list(range(1, 15))
+    blocks, out = [0] * (14 * 7), [0] * 7
+    c = P.Code(16, 8, P.PMRC_SPARSE, P.PMRC_NONSYSTEMATIC)
+    with pytest.raises(P.PMRCError) as e:
+        P.pmrc_read_degraded(c.handle, 2, H, blocks, out, 0, 16)
+    assert e.value.rc == P.PMRC_EINVAL
+    c = P.Code(16, 8, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    for node in (8, 15, -1):
+        with pytest.raises(P.PMRCError) as e:
+            P.pmrc_read_degraded(c.handle, node, H, blocks, out, 0, 16)
+        assert e.value.rc == P.PMRC_EINVAL
