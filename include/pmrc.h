@@ -291,7 +291,7 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * (default): for blocks of at least 256 KiB, a bitsliced kernel generated
  * for the call's decode rows and compiled at run time (NVRTC, loaded on
  * demand) on the first reconstruction of each (node set, wanted rows) --
- * about a second, part of the per-failure-pattern initialization that
+ * a few seconds, part of the per-failure-pattern initialization that
  * Sec. 4 reports apart from throughput -- then cached in the handle; the
  * split-table kernel otherwise, and whenever the run-time kernel cannot be
  * built (NVRTC missing, blocks not 16-byte aligned, or more than 64 inputs
