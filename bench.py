@@ -328,6 +328,10 @@ def run_ours(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         step(False)
+    # kernels compiled at run time in the background (the reconstruction's)
+    # are ready and loaded before the timed steps
+    P.wait_kernels()
+    step(False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -574,15 +578,21 @@ def run_init(torch, P, inputs, args, dev):
     dec = lambda: c.decode(S, din, [Xr[r] for r in range(K)], B)
     rep = lambda: (c.repair_helpers(f, H, hin, [recv[i] for i in range(D_)], B),
                    c.repair_newcomer(f, H, [recv[i] for i in range(D_)], [node[j] for j in range(a)], B))
-    first = wall(dec)
+    first = wall(dec)                    # host plan; compilation started
+    t = time.perf_counter()
+    c.wait_kernels()
+    ready = first + (time.perf_counter() - t) * 1e3
+    wall(dec)                            # loads the compiled kernel
     again = min(wall(dec) for _ in range(3))
     out["decode_pattern_first_call_ms"] = round(first, 2)
+    out["decode_pattern_kernel_ready_ms"] = round(ready, 2)
     out["decode_pattern_init_ms"] = round(first - again, 2)
     first = wall(rep)
     again = min(wall(rep) for _ in range(3))
     out["repair_pattern_init_ms"] = round(first - again, 2)
-    out["note"] = ("host wall clock; the decode pattern's first call includes compiling its "
-                   "bitsliced kernel (NVRTC)")
+    out["note"] = ("host wall clock; the decode pattern's first call builds its plan and starts "
+                   "compiling its bitsliced kernel (NVRTC) in the background, running the "
+                   "split-table kernel meanwhile; kernel_ready is when the compilation ended")
     del Y, Xr, recv, node, c
     torch.cuda.synchronize()
     return out
@@ -794,10 +804,15 @@ def run_gf16(torch, P, inputs, args, flush, stream, dev, hbm):
 
 
 def time_op(torch, stream, flush, args, fn):
-    """Average device time of fn over args.steps runs, L2 flushed before each."""
+    """Average device time of fn over args.steps runs, L2 flushed before each;
+    after the warm-up, any kernel compiled at run time in the background is
+    waited for and loaded, so the timed runs use it."""
+    import paper_1412_3022_gb300 as P
     for _ in range(args.warmup):
         flush.fill_(3)
         fn()
+    P.wait_kernels()
+    fn()
     tot = 0.0
     for _ in range(args.steps):
         flush.fill_(5)
@@ -1062,6 +1077,10 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1, inputs=None):
         ev_out[b].record(s_out)
 
     for i in range(max(2, args.warmup)):
+        step(i)
+    import paper_1412_3022_gb300 as P
+    P.wait_kernels()
+    for i in range(2):              # both buffer sets load their kernels
         step(i)
     torch.cuda.synchronize()
     if dist:

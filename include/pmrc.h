@@ -290,10 +290,11 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
 /* Reconstruction kernel of a handle (GF(2^8) codes).  PMRC_KERNEL_AUTO
  * (default): for blocks of at least 256 KiB, a bitsliced kernel generated
  * for the call's decode rows and compiled at run time (NVRTC, loaded on
- * demand) on the first reconstruction of each (node set, wanted rows) --
- * a few seconds, part of the per-failure-pattern initialization that
- * Sec. 4 reports apart from throughput -- then cached in the handle; the
- * split-table kernel otherwise, and whenever the run-time kernel cannot be
+ * demand) from the first reconstruction of each (node set, wanted rows) --
+ * a few seconds in the background, part of the per-failure-pattern
+ * initialization that Sec. 4 reports apart from throughput -- then cached
+ * in the handle; the split-table kernel until then, otherwise, and whenever
+ * the run-time kernel cannot be
  * built (NVRTC missing, blocks not 16-byte aligned, or more than 64 inputs
  * per 8-row block).  PMRC_KERNEL_GENERIC: always the split-table kernel.
  * PMRC_KERNEL_BITSLICED: the run-time kernel at any size, PMRC_EUNSUPPORTED
@@ -303,12 +304,27 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * PMRC_KERNEL_BITSLICED falls back to the split-table kernel rather than
  * failing.
  *
- * Kernels compiled at run time (encode, reconstruction, newcomer) can be
- * kept across handles and processes: when the environment variable
- * PMRC_KERNEL_CACHE names a writable directory, each compiled cubin is
- * stored there under a hash of its source, and a later compilation of the
- * same schedule reads the file instead of running NVRTC. */
+ * Under PMRC_KERNEL_AUTO the run-time compilations (encode, reconstruction,
+ * newcomer) run on background threads: the call that needs one starts it
+ * and runs the split-table kernel, as do later calls until it has finished
+ * (pmrc_wait_kernels waits for it); the first call after that loads it.
+ * Under PMRC_KERNEL_BITSLICED the call compiles before it launches.
+ *
+ * Kernels compiled at run time can be kept across handles and processes:
+ * when the environment variable PMRC_KERNEL_CACHE names a writable
+ * directory, each compiled cubin is stored there under a hash of its
+ * source, and a later compilation of the same schedule reads the file
+ * instead of running NVRTC. */
 int pmrc_set_decode_kernel(pmrc_code *code, int which);
+
+/* Waits until the handle's background compilations have finished, at most
+ * timeout_ms milliseconds (negative: no limit); PMRC_ETIMEOUT if some are
+ * still running.  Host only. */
+int pmrc_wait_kernels(const pmrc_code *code, int timeout_ms);
+
+/* Number of the handle's run-time kernels compiled (*ready) and still
+ * compiling (*pending).  Host only. */
+int pmrc_runtime_kernels(const pmrc_code *code, int *ready, int *pending);
 
 /* ---- batched execution ---------------------------------------------------
  * Many stripes (any mix of codes, block sizes and operations) run by one

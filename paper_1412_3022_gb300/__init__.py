@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpmrc.so")
@@ -85,6 +86,8 @@ _SIGNATURES = {
     "pmrc_code_params": (_i, [_vp, _ip]),
     "pmrc_code_blocks": (_i, [_vp, _ip, _ip]),
     "pmrc_set_decode_kernel": (_i, [_vp, _i]),
+    "pmrc_wait_kernels": (_i, [_vp, _i]),
+    "pmrc_runtime_kernels": (_i, [_vp, _ip, _ip]),
     "pmrc_create_field": (_i, [_i, _i, _i, _i, _i, _i, ctypes.POINTER(_vp)]),
     "pmrc_code_field_bits": (_i, [_vp]),
     "pmrc_code_generator16": (_i, [_vp, ctypes.POINTER(ctypes.c_uint16)]),
@@ -265,6 +268,24 @@ def pmrc_encode_precode(code, data, parity, block_bytes, workspace, workspace_by
 
 def pmrc_set_decode_kernel(code, which: int) -> None:
     _check(lib().pmrc_set_decode_kernel(code, which), "pmrc_set_decode_kernel")
+
+
+def pmrc_wait_kernels(code, timeout_ms: int = -1) -> None:
+    _check(lib().pmrc_wait_kernels(code, timeout_ms), "pmrc_wait_kernels")
+
+
+def pmrc_runtime_kernels(code) -> tuple:
+    ready, pending = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pmrc_runtime_kernels(code, ctypes.byref(ready), ctypes.byref(pending)),
+           "pmrc_runtime_kernels")
+    return ready.value, pending.value
+
+
+def wait_kernels(timeout_ms: int = -1) -> None:
+    """pmrc_wait_kernels on every live Code of this process."""
+    for c in list(_live_codes):
+        if c.handle:
+            pmrc_wait_kernels(c.handle, timeout_ms)
 
 
 def pmrc_set_encode_kernel(code, which: int) -> None:
@@ -553,6 +574,9 @@ class Server:
 
 
 # ---------------------------------------------------------------- handle
+_live_codes = weakref.WeakSet()
+
+
 class Code:
     """Owns a pmrc_code handle; methods are the C calls on it."""
 
@@ -569,6 +593,7 @@ class Code:
         self.n, self.k, self.d, self.alpha = p["n"], p["k"], p["d"], p["alpha"]
         self.construction, self.form = construction, form
         self.data_blocks, self.coded_blocks = pmrc_code_blocks(self.handle)
+        _live_codes.add(self)
 
     def close(self):
         if self.handle:
@@ -628,6 +653,13 @@ class Code:
             workspace_bytes = int(workspace.numel() * workspace.element_size())
         pmrc_encode_precode(self.handle, data, parity, block_bytes, workspace, workspace_bytes,
                             stream)
+
+    def wait_kernels(self, timeout_ms: int = -1):
+        pmrc_wait_kernels(self.handle, timeout_ms)
+
+    def runtime_kernels(self) -> tuple:
+        """(compiled, still compiling) run-time kernels of this handle."""
+        return pmrc_runtime_kernels(self.handle)
 
     def set_decode_kernel(self, which: int):
         pmrc_set_decode_kernel(self.handle, which)

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -213,7 +214,7 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream);
 std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
                                                 const std::function<int(Mat &, std::string &)> &make,
-                                                std::string &err, bool by_support = false);
+                                                std::string &err, bool by_support, bool background);
 void encode_matrix(const pmrc_code *c, Mat &M);
 bool want_runtime(const pmrc_code *c, int policy, size_t nbytes, size_t auto_min);
 
@@ -352,6 +353,39 @@ int pmrc_default_helpers(const pmrc_code *c, int f, int *helpers_out) {
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
+int pmrc_wait_kernels(const pmrc_code *c, int timeout_ms) {
+  if (!c) return fail(PMRC_EINVAL, "NULL argument");
+  std::vector<std::shared_ptr<BsJob>> jobs;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    for (auto &kv : c->rt_jobs) jobs.push_back(kv.second);
+  }
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (auto &j : jobs) {
+    std::unique_lock<std::mutex> lk(j->mu);
+    if (timeout_ms < 0)
+      j->cv.wait(lk, [&] { return j->done; });
+    else if (!j->cv.wait_until(lk, deadline, [&] { return j->done; }))
+      return fail(PMRC_ETIMEOUT, "run-time kernels are still compiling");
+  }
+  return PMRC_OK;
+}
+
+int pmrc_runtime_kernels(const pmrc_code *c, int *ready, int *pending) {
+  if (!c || !ready || !pending) return fail(PMRC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(c->mu);
+  *ready = *pending = 0;
+  for (auto &kv : c->rt) *ready += kv.second != nullptr;
+  for (auto &kv : c->rt_jobs) {
+    std::lock_guard<std::mutex> g2(kv.second->mu);
+    if (!kv.second->done)
+      ++*pending;
+    else
+      *ready += kv.second->rc == 0;
+  }
+  return PMRC_OK;
+}
+
 int pmrc_set_decode_kernel(pmrc_code *c, int which) {
   if (!c) return fail(PMRC_EINVAL, "NULL argument");
   if (which != PMRC_KERNEL_AUTO && which != PMRC_KERNEL_GENERIC && which != PMRC_KERNEL_BITSLICED)
@@ -418,7 +452,7 @@ int encode_body(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *
       std::shared_ptr<BsRuntimeKernel> k = runtime_kernel(c, "e", [&](Mat &M, std::string &) {
         encode_matrix(c, M);
         return (int)kOk;
-      }, rerr, true);
+      }, rerr, true, policy != PMRC_KERNEL_BITSLICED);
       if (k) {
         done = nbytes & ~(size_t)31;
         const cudaError_t e = bitslice_launch_runtime(*k, data, out, done, (cudaStream_t)stream);
@@ -488,7 +522,7 @@ int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
     if (aligned)
       k = runtime_kernel(c, key, [&](Mat &M, std::string &e) {
         return newcomer_matrix(c->m, f, helpers, M, e);
-      }, rerr);
+      }, rerr, false, c->decode_kernel != PMRC_KERNEL_BITSLICED);
     if (k) {
       done = nbytes & ~(size_t)31;
       const cudaError_t e = bitslice_launch_runtime(*k, received, out, done, st);
@@ -636,41 +670,109 @@ void encode_matrix(const pmrc_code *c, Mat &M) {
   std::copy(c->m.Gcode.v.begin() + (size_t)first * K, c->m.Gcode.v.end(), M.v.begin());
 }
 
+// Moves a finished compilation into the handle's kernel cache (loading its
+// cubin on the calling thread) and returns the kernel, or null with the
+// reason in err.  Caller holds c->mu.
+std::shared_ptr<BsRuntimeKernel> finish_job(const pmrc_code *c, const std::string &key,
+                                            BsJob &job, std::string &err) {
+  auto it = c->rt.find(key);
+  if (it == c->rt.end()) {  // not yet moved by another thread
+    std::shared_ptr<BsRuntimeKernel> k;
+    std::string e = job.err;
+    if (!job.rc) bitslice_load(job.out, k, e);
+    if (c->rt.size() >= kPlanCacheCap) {
+      if (c->rt.begin()->second) c->rt_retired.push_back(c->rt.begin()->second);
+      c->rt_err.erase(c->rt.begin()->first);
+      c->rt.erase(c->rt.begin());
+    }
+    it = c->rt.emplace(key, k).first;
+    if (!k) c->rt_err[key] = e;
+  }
+  c->rt_jobs.erase(key);
+  if (!it->second) err = c->rt_err[key];
+  return it->second;
+}
+
 // A bitsliced kernel compiled at run time for matrix M (blocks of rows of
 // identical support when by_support, else consecutive rows), cached in the
 // handle under `key`; null when it cannot be built (the reason in err, also
-// cached).
+// cached).  In the background (AUTO policies) the first call only starts the
+// compilation and returns null with an empty err, as do later calls until it
+// has finished: the caller runs the split-table kernel meanwhile.
 std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
                                                 const std::function<int(Mat &, std::string &)> &make,
-                                                std::string &err, bool by_support) {
-  std::lock_guard<std::mutex> g(c->jit_mu);
+                                                std::string &err, bool by_support, bool background) {
+  std::shared_ptr<BsJob> job;
   {
-    std::lock_guard<std::mutex> g2(c->mu);
+    std::lock_guard<std::mutex> g(c->mu);
     auto it = c->rt.find(key);
     if (it != c->rt.end()) {
       if (!it->second) err = c->rt_err[key];
       return it->second;
     }
+    auto jt = c->rt_jobs.find(key);
+    if (jt != c->rt_jobs.end()) job = jt->second;
   }
-  std::shared_ptr<BsRuntimeKernel> k;
-  Mat M;
-  int rc = make(M, err);
-  if (!rc && M.rows > 0)
-    rc = bitslice_build(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support, k, err);
-  std::lock_guard<std::mutex> g2(c->mu);
-  if (c->rt.size() >= kPlanCacheCap) {
-    if (c->rt.begin()->second) c->rt_retired.push_back(c->rt.begin()->second);
-    c->rt_err.erase(c->rt.begin()->first);
-    c->rt.erase(c->rt.begin());
+  if (!job) {
+    Mat M;
+    int rc = make(M, err);
+    if (!rc && M.rows == 0) {
+      err = "no rows to compute";
+      rc = kEUnsupported;
+    }
+    if (rc) {
+      std::lock_guard<std::mutex> g(c->mu);
+      c->rt[key] = nullptr;
+      c->rt_err[key] = err;
+      return nullptr;
+    }
+    auto fresh = std::make_shared<BsJob>();
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      auto jt = c->rt_jobs.find(key);
+      if (jt != c->rt_jobs.end()) {  // another thread started it meanwhile
+        job = jt->second;
+      } else {
+        job = fresh;
+        c->rt_jobs[key] = job;
+      }
+    }
+    if (job == fresh) {
+      auto work = [job, M, by_support]() {
+        BsCompiled out;
+        std::string e;
+        const int rc =
+            bitslice_compile(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support, out, e);
+        {
+          std::lock_guard<std::mutex> g(job->mu);
+          job->rc = rc;
+          job->err = e;
+          job->out = std::move(out);
+          job->done = true;
+        }
+        job->cv.notify_all();
+      };
+      if (background)
+        jit_background(work);
+      else
+        work();
+    }
   }
-  c->rt[key] = k;
-  if (!k) c->rt_err[key] = err;
-  return k;
+  {
+    std::unique_lock<std::mutex> lk(job->mu);
+    if (background && !job->done) {
+      err.clear();
+      return nullptr;
+    }
+    job->cv.wait(lk, [&] { return job->done; });
+  }
+  std::lock_guard<std::mutex> g(c->mu);
+  return finish_job(c, key, *job, err);
 }
 
 // Bitsliced reconstruction rows for this (nodes, wanted rows).
 std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *nodes,
-                                                const std::vector<char> &want,
+                                                const std::vector<char> &want, bool background,
                                                 std::string &err) {
   std::string key = "d:";
   for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
@@ -687,7 +789,7 @@ std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *n
     for (size_t q = 0; q < rows.size(); q++)
       for (int col = 0; col < R.cols; col++) M.at((int)q, col) = R.at(rows[q], col);
     return (int)kOk;
-  }, err);
+  }, err, false, background);
 }
 
 // Whether a call of nbytes takes a run-time bitsliced kernel under the
@@ -722,7 +824,8 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
       aligned = !node_blocks[i] || (uintptr_t)node_blocks[i] % 16 == 0;
     for (int r : rows) aligned = aligned && (uintptr_t)data_out[r] % 16 == 0;
     std::string rerr;
-    std::shared_ptr<BsRuntimeKernel> k = aligned ? decode_runtime(c, nodes, want, rerr) : nullptr;
+    std::shared_ptr<BsRuntimeKernel> k =
+        aligned ? decode_runtime(c, nodes, want, !forced, rerr) : nullptr;
     if (!k && forced)
       return fail(PMRC_EUNSUPPORTED, aligned ? "bitsliced reconstruction: " + rerr
                                              : "bitsliced reconstruction needs 16-byte aligned blocks");

@@ -1,6 +1,7 @@
 // Internal view of the code handle, shared by the C ABI and the batching
 // and serving layers.
 #pragma once
+#include <condition_variable>
 #include <functional>
 #include <map>
 #include <memory>
@@ -13,6 +14,21 @@
 #include "plan.h"
 #include "repair.h"
 #include "specific.h"
+
+namespace pmrc {
+
+// One compilation of a run-time schedule (host only), shared by the handle
+// and the thread that runs it.
+struct BsJob {
+  std::mutex mu;
+  std::condition_variable cv;
+  bool done = false;
+  int rc = 0;
+  std::string err;
+  BsCompiled out;
+};
+
+}  // namespace pmrc
 
 struct pmrc_code {
   pmrc::CodeMatrices m;
@@ -27,9 +43,11 @@ struct pmrc_code {
   // wanted rows), newcomer applies per (failed node, helpers), the encode
   // ("e"); a null kernel records a matrix that could not be built
   int decode_kernel = 0;                    // PMRC_KERNEL_*
-  mutable std::mutex jit_mu;                // one compilation at a time per handle
   mutable std::map<std::string, std::shared_ptr<pmrc::BsRuntimeKernel>> rt;
   mutable std::map<std::string, std::string> rt_err;
+  // compilations in flight (background under PMRC_KERNEL_AUTO), per key;
+  // the first call that finds one finished loads it into `rt`
+  mutable std::map<std::string, std::shared_ptr<pmrc::BsJob>> rt_jobs;
   // evicted run-time kernels stay loaded until the handle is destroyed: a
   // launch from them may still be running
   mutable std::vector<std::shared_ptr<pmrc::BsRuntimeKernel>> rt_retired;

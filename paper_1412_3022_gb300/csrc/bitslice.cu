@@ -203,8 +203,8 @@ int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by
   return runtime_blocks(M, rows, cols, max_inputs, by_support, blks, err);
 }
 
-int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
-                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
+int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                     BsCompiled &out, std::string &err) {
   std::vector<BsBlock> blks;
   int rc = runtime_blocks(M, rows, cols, max_inputs, by_support, blks, err);
   if (rc) return rc;
@@ -214,18 +214,32 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by
       "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\n"
       "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n" +
       std::string(kBsDevSrc) + "\n" + em.code;
-  std::vector<char> cubin;
-  rc = jit_compile(src, kname, cubin, err);
+  rc = jit_compile(src, kname, out.cubin, err);
   if (rc) return rc;
+  out.nblocks = (int)blks.size();
+  out.ninputs = cols;
+  out.noutputs = rows;
+  out.cost = em.cost;
+  return kOk;
+}
+
+int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
   auto k = std::make_shared<BsRuntimeKernel>();
-  rc = jit_load(cubin, kname, &k->lib, &k->fn, err);
+  const int rc = jit_load(c.cubin, "bs_runtime_kernel", &k->lib, &k->fn, err);
   if (rc) return rc;
-  k->nblocks = (int)blks.size();
-  k->ninputs = cols;
-  k->noutputs = rows;
-  k->cost = em.cost;
+  k->nblocks = c.nblocks;
+  k->ninputs = c.ninputs;
+  k->noutputs = c.noutputs;
+  k->cost = c.cost;
   out = k;
   return kOk;
+}
+
+int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
+  BsCompiled c;
+  const int rc = bitslice_compile(M, rows, cols, max_inputs, by_support, c, err);
+  return rc ? rc : bitslice_load(c, out, err);
 }
 
 cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,

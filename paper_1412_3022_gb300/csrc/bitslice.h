@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <memory>
 #include <string>
+#include <vector>
 
 namespace pmrc {
 
@@ -43,8 +44,24 @@ struct BsRuntimeKernel;
 int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
                    std::string &err);
 
-// Builds the kernel for M.  kEUnsupported when bitslice_check fails or NVRTC
-// is missing or fails (message in err).
+// A compiled schedule not yet loaded: the cubin and what its launches need.
+struct BsCompiled {
+  std::vector<char> cubin;
+  int nblocks = 0, ninputs = 0, noutputs = 0;
+  std::vector<int> cost;
+};
+
+// Emits and compiles the schedule for M (host only: NVRTC, no CUDA call, so
+// it may run on any thread).  kEUnsupported when bitslice_check fails or
+// NVRTC is missing or fails (message in err).
+int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
+                     BsCompiled &out, std::string &err);
+
+// Loads a compiled schedule as a CUDA library (the calling thread's device
+// context must be usable).
+int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
+
+// bitslice_compile, then bitslice_load.
 int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
                    std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
 

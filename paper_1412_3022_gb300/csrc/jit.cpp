@@ -10,8 +10,11 @@
 #include <nvrtc.h>
 #include <unistd.h>
 
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
+#include <deque>
+#include <thread>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -99,9 +102,65 @@ void write_cached(const std::string &path, const std::vector<char> &cubin) {
   if (fclose(f) != 0 || !ok || rename(tmp.c_str(), path.c_str()) != 0) remove(tmp.c_str());
 }
 
+// A small pool of compile threads, started on first use and joined when
+// the process exits (a function-local static whose destructor is registered
+// after NVRTC's, see jit_background, and so runs before them).
+class JitPool {
+ public:
+  void submit(std::function<void()> fn) {
+    std::lock_guard<std::mutex> g(mu_);
+    if (stop_) return;
+    q_.push_back(std::move(fn));
+    if (workers_.size() < kWorkers) workers_.emplace_back([this] { run(); });
+    cv_.notify_one();
+  }
+  ~JitPool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+      q_.clear();
+    }
+    cv_.notify_all();
+    for (auto &t : workers_) t.join();
+  }
+
+ private:
+  static constexpr size_t kWorkers = 2;
+  void run() {
+    for (;;) {
+      std::function<void()> job;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [this] { return stop_ || !q_.empty(); });
+        if (stop_) return;
+        job = std::move(q_.front());
+        q_.pop_front();
+      }
+      job();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::deque<std::function<void()>> q_;
+  std::vector<std::thread> workers_;
+  bool stop_ = false;
+};
+
+JitPool &pool() {
+  static JitPool p;
+  return p;
+}
+
 }  // namespace
 
 bool jit_available() { return nvrtc().ok; }
+
+void jit_background(std::function<void()> fn) {
+  // NVRTC is loaded before the pool exists, so its exit-time destructors,
+  // registered at load, run after the pool's, which waits for the workers
+  nvrtc();
+  pool().submit(std::move(fn));
+}
 
 int jit_compile(const std::string &src, const char *kernel_name, std::vector<char> &cubin,
                 std::string &err) {

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,12 @@ bool jit_available();
 // written are ignored.
 int jit_compile(const std::string &src, const char *kernel_name, std::vector<char> &cubin,
                 std::string &err);
+
+// Runs fn on one of a few background threads (compilations that must not
+// hold up the call that asked for them).  Jobs still queued when the
+// process exits are dropped; a job already running is waited for, so no
+// compilation is left inside NVRTC while the process tears down.
+void jit_background(std::function<void()> fn);
 
 // Loads a cubin as a CUDA library and finds its kernel `kernel_name`.
 int jit_load(const std::vector<char> &cubin, const char *kernel_name, cudaLibrary_t *lib,

@@ -158,3 +158,34 @@ def test_runtime_kernels_cached_on_disk(tmp_path, monkeypatch):
     assert list(tmp_path.glob("pmrc-*.cubin")) == files
     assert files[0].stat().st_mtime_ns == stamp     # read back, not rewritten
     assert not list(tmp_path.glob("*.tmp"))
+
+
+def test_auto_compiles_in_the_background():
+    """AUTO: the first reconstruction of a node set starts its compilation
+    and runs the split-table kernel; once compiled, the next call loads and
+    runs the bitsliced kernel.  Both results are the data."""
+    n, k, nbytes = 16, 8, 256 * 1024 + 32
+    X = inputs.blocks(56, nbytes, seed=100)
+    Y = O.encode(n, k, O.SPARSE, True, X)
+    S = [1, 3, 5, 7, 8, 10, 12, 14]
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    got, _ = decode(c, S, Y, nbytes)
+    assert np.array_equal(got, X)
+    ready, pending = c.runtime_kernels()
+    assert ready + pending == 1
+    c.wait_kernels()
+    assert c.runtime_kernels() == (1, 0)
+    got, _ = decode(c, S, Y, nbytes)
+    assert np.array_equal(got, X)
+    assert c.runtime_kernels() == (1, 0)
+
+
+def test_forced_bitsliced_compiles_before_it_launches():
+    n, k, nbytes = 16, 8, 4096 + 32
+    X = inputs.blocks(56, nbytes, seed=101)
+    Y = O.encode(n, k, O.SPARSE, True, X)
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    got, _ = decode(c, [0, 2, 4, 6, 9, 11, 13, 15], Y, nbytes)
+    assert np.array_equal(got, X)
+    assert c.runtime_kernels() == (1, 0)

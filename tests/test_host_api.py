@@ -329,3 +329,12 @@ def test_degraded_read_argument_checks():
         with pytest.raises(P.PMRCError) as e:
             P.pmrc_read_degraded(c.handle, node, H, blocks, out, 0, 16)
         assert e.value.rc == P.PMRC_EINVAL
+
+
+def test_runtime_kernel_queries_on_a_fresh_handle():
+    """Nothing compiled or compiling before any call (host only)."""
+    c = P.Code(16, 8, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    assert c.runtime_kernels() == (0, 0)
+    c.wait_kernels(0)
+    c.wait_kernels()
+    P.wait_kernels(0)
