@@ -43,7 +43,7 @@ def _case(i):
     return rng, c, n, k, cons, form, nbytes, shift, enc_k, dec_k
 
 
-@pytest.mark.parametrize("case", range(40))
+@pytest.mark.parametrize("case", range(100))
 def test_fuzz_case(case):
     rng, c, n, k, cons, form, nbytes, shift, enc_k, dec_k = _case(case)
     a, K = k - 1, k * (k - 1)
@@ -100,3 +100,70 @@ def test_fuzz_case(case):
         c.decode(S, yin.ptrs(), xout.ptrs(), nbytes)
     assert xout.guards_intact()
     assert np.array_equal(xout.get(), X), ("decode", S)
+
+
+def _other(i):
+    """A random PM-MBR, Reed-Solomon or GF(2^16) PM-MSR case."""
+    rng = np.random.default_rng(5000 + i)
+    kind = ("mbr", "rs", "gf16")[i % 3]
+    if kind == "mbr":
+        k = int(rng.integers(2, 8))
+        n = int(rng.integers(k + 1, min(2 * k + 5, 24) + 1))
+        d = int(rng.integers(k, n))
+        c = P.Code(n, k, P.PMRC_MBR, int(rng.integers(0, 2)), d=d)
+    elif kind == "rs":
+        k = int(rng.integers(1, 12))
+        n = int(rng.integers(k + 1, k + 10))
+        c = P.Code(n, k, P.PMRC_RS, int(rng.integers(0, 2)))
+    else:
+        k = int(rng.integers(2, 7))
+        n = int(rng.integers(2 * k - 1, 2 * k + 4))
+        c = P.Code(n, k, int(rng.integers(0, 2)), int(rng.integers(0, 2)), field_bits=16)
+    nbytes = 2 * int(rng.integers(1, 8000))
+    shift = int(rng.choice([0, 16, 2 * int(rng.integers(1, 8))]))
+    return rng, kind, c, nbytes, shift
+
+
+def _oracle_codeword(kind, c, X):
+    n, k, d = c.n, c.k, c.d
+    sysf = c.form == P.PMRC_SYSTEMATIC
+    if kind == "mbr":
+        return O.mbr_encode(n, k, d, X)
+    if kind == "rs":
+        return O.rs_encode(n, k, sysf, X)
+    return O.gf16_encode(n, k, c.construction, sysf, X)
+
+
+@pytest.mark.parametrize("case", range(36))
+def test_fuzz_other_codes(case):
+    rng, kind, c, nbytes, shift = _other(case)
+    n, k, a, K = c.n, c.k, c.alpha, c.data_blocks
+    X = inputs.blocks(K, nbytes, seed=5000 + case)
+    Y = _oracle_codeword(kind, c, X)
+    first = k * a if c.form == P.PMRC_SYSTEMATIC else 0
+    xin = Blocks(K, nbytes, shift, X)
+    y = Blocks(c.n_outputs, nbytes, shift)
+    c.encode(xin.ptrs(), y.ptrs(), nbytes)
+    assert y.guards_intact()
+    assert np.array_equal(y.get(), Y[first:]), (kind, "encode")
+    f = int(rng.integers(0, n))
+    H = c.default_helpers(f)
+    if kind == "rs":
+        hin = Blocks(k, nbytes, shift, Y[H])
+        node = Blocks(1, nbytes, shift)
+        c.repair(f, H, hin.ptrs(), node.ptrs(), nbytes)
+    else:
+        hin = Blocks(len(H) * a, nbytes, shift, np.concatenate([Y[a * h:a * h + a] for h in H]))
+        recv = Blocks(len(H), nbytes, shift)
+        node = Blocks(a, nbytes, shift)
+        c.repair_helpers(f, H, hin.ptrs(), recv.ptrs(), nbytes)
+        c.repair_newcomer(f, H, recv.ptrs(), node.ptrs(), nbytes)
+    assert node.guards_intact()
+    assert np.array_equal(node.get(), Y[a * f:a * f + a]), (kind, "repair", f)
+    S = rng.permutation(rng.choice(n, k, replace=False)).tolist()
+    rows = [a * i + j for i in S for j in range(a)]
+    yin = Blocks(len(rows), nbytes, shift, Y[rows])
+    xout = Blocks(K, nbytes, shift)
+    c.decode(S, yin.ptrs(), xout.ptrs(), nbytes)
+    assert xout.guards_intact()
+    assert np.array_equal(xout.get(), X), (kind, "decode", S)
