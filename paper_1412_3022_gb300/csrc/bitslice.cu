@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <vector>
@@ -86,8 +87,7 @@ long long bitslice_xors(int id) { return id >= 0 && id < kBsNumKernels ? kBsKern
 
 namespace {
 
-// One CTA per SM; each block of the schedule gets CTAs in proportion to its
-// cost, at least one, and no more than it has warp tiles to hand out.
+// One CTA per SM, each with an equal share of the schedule's cost.
 cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs, int noutputs,
                       const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
                       cudaStream_t stream, std::atomic<uint64_t> (&smem_set)[kMaxDevices],
@@ -109,32 +109,30 @@ cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs,
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const uint64_t units = (nbytes + kBsUnit - 1) / kBsUnit;
-  const uint64_t cap = std::max<uint64_t>(1, (units + kBsThreads / 32 - 1) / (kBsThreads / 32));
+  // the work is the sequence of (block, tile) items g = b * ntiles + t; CTA
+  // c takes a contiguous range of it holding 1/ncta of the total cost, so
+  // every SM gets the same work whatever the block count, and a CTA runs one
+  // block's code (two at a range boundary)
+  const uint64_t ntiles = (nbytes + kBsUnit - 1) / kBsUnit;
+  const uint64_t items = (uint64_t)nblocks * ntiles;
+  const int ncta = (int)std::max<uint64_t>(1, std::min<uint64_t>(std::min(sms, kBsMaxCtas), items));
+  a.ntiles = (uint32_t)ntiles;
   double total = 0;
-  for (int i = 0; i < nblocks; i++) total += cost[i];
-  int cnt[kBsMaxBlocks];
-  int used = 0;
-  for (int i = 0; i < nblocks; i++) {
-    cnt[i] = std::max(1, (int)(sms * cost[i] / total));
-    cnt[i] = (int)std::min<uint64_t>(cnt[i], cap);
-    used += cnt[i];
+  for (int i = 0; i < nblocks; i++) total += (double)cost[i] * (double)ntiles;
+  a.cta_g[0] = 0;
+  int b = 0;
+  double before = 0;  // cost of the blocks before b
+  for (int c = 1; c < ncta; c++) {
+    const double target = total * c / ncta;
+    while (b + 1 < nblocks && before + (double)cost[b] * ntiles < target) before += (double)cost[b++] * ntiles;
+    const double t = std::ceil((target - before) / (double)cost[b]);
+    uint64_t g = (uint64_t)b * ntiles + (uint64_t)std::min<double>(std::max(t, 0.0), (double)ntiles);
+    a.cta_g[c] = (uint32_t)std::max<uint64_t>(g, a.cta_g[c - 1]);
   }
-  for (; used < sms; used++) {  // hand out the rest to the slowest block
-    int best = -1;
-    double worst = 0;
-    for (int i = 0; i < nblocks; i++) {
-      const double t = (double)cost[i] / cnt[i];
-      if ((uint64_t)cnt[i] < cap && t > worst) worst = t, best = i;
-    }
-    if (best < 0) break;
-    cnt[best]++;
-  }
-  a.cta_start[0] = 0;
-  for (int i = 0; i < nblocks; i++) a.cta_start[i + 1] = (uint16_t)(a.cta_start[i] + cnt[i]);
-  for (int i = nblocks + 1; i <= kBsMaxBlocks; i++) a.cta_start[i] = a.cta_start[nblocks];
+  a.cta_g[ncta] = (uint32_t)items;
+  for (int c = ncta + 1; c <= kBsMaxCtas; c++) a.cta_g[c] = (uint32_t)items;
   void *args[] = {&a};
-  return cudaLaunchKernel(fn, dim3(a.cta_start[nblocks]), dim3(kBsThreads), args, smem, stream);
+  return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);
 }
 
 std::atomic<uint64_t> g_static_smem_set[kMaxDevices];

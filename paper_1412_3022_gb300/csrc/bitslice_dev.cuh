@@ -11,12 +11,16 @@ constexpr int kBsAhead = 4;           // inputs prefetched ahead of the one in u
 constexpr int kBsSlots = kBsAhead + 1;  // shared-memory ring (never the slot being read)
 constexpr uint32_t kBsUnit = 32 * kBsBytes;  // bytes of column per warp tile
 constexpr int kBsMaxBlocks = 64;     // dense blocks per schedule
+constexpr int kBsMaxCtas = 256;      // CTAs per launch (one per SM)
 
 struct BsArgs {
   uint64_t nbytes;  // bytes covered by this launch (multiple of kBsBytes)
   uint32_t hi28, hi30, hi31;  // 2^28, 2^30, 2^31: right shifts as multiply-high
   uint32_t x16, x4, x2;       // left shifts as multiplies
-  uint16_t cta_start[kBsMaxBlocks + 1];  // CTAs [cta_start[b], cta_start[b+1]) run block b
+  // the launch's work is the sequence of warp tiles g = b * ntiles + t
+  // (block b, 1 KiB column tile t); CTA c takes tiles [cta_g[c], cta_g[c+1])
+  uint32_t ntiles;
+  uint32_t cta_g[kBsMaxCtas + 1];
   uint8_t *ptr[kBsMaxPtr];    // K input blocks, then the output blocks
 };
 

@@ -140,17 +140,16 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
     f += "    default: break;\n    }\n  }\n";
     f += "}\n\n";
   }
-  // persistent kernel, one CTA per SM: CTAs [cta_start[b], cta_start[b+1])
-  // all run block b, so an SM only ever holds one block's straight-line
-  // code, fetched once and then re-executed from its instruction caches;
-  // inside the group the warps take 1 KiB column tiles in turn
+  // persistent kernel, one CTA per SM: the host splits the sequence of
+  // (block, 1 KiB column tile) items into equal-cost ranges, one per CTA, so
+  // an SM runs one block's straight-line code (two at a range boundary),
+  // fetched into its instruction caches once and then re-executed; the
+  // warps take the range's tiles in turn
   appendf(f, "%s__global__ void __launch_bounds__(kBsThreads, 1) %s(const __grid_constant__ BsArgs a) {\n",
           extern_c ? "extern \"C\" " : "", name.c_str());
-  appendf(f, "  int b = 0;\n  while (b + 1 < %zu && blockIdx.x >= a.cta_start[b + 1]) b++;\n",
-          blks.size());
-  f += "  const uint32_t c = blockIdx.x - a.cta_start[b], cnt = a.cta_start[b + 1] - a.cta_start[b];\n";
-  f += "  const uint32_t nunits = (uint32_t)((a.nbytes + kBsUnit - 1) / kBsUnit);\n";
-  f += "  for (uint32_t u = (threadIdx.x / 32) * cnt + c; u < nunits; u += cnt * (kBsThreads / 32)) {\n";
+  f += "  const uint32_t g1 = a.cta_g[blockIdx.x + 1];\n";
+  f += "  for (uint32_t g = a.cta_g[blockIdx.x] + threadIdx.x / 32; g < g1; g += kBsThreads / 32) {\n";
+  f += "    const uint32_t b = g / a.ntiles, u = g - b * a.ntiles;\n";
   f += "    BsCtx x;\n    if (!bs_ctx(a, x, u)) continue;\n    uint32_t acc[8][8];\n";
   f += "    bs_zero(acc);\n    switch (b) {\n";
   for (size_t b = 0; b < blks.size(); b++) {
