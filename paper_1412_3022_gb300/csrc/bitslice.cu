@@ -23,11 +23,12 @@
 //     own inverse) and are stored with 16-byte streaming stores;
 //   * the inputs of a block are walked by a loop whose body switches on the
 //     input only for the accumulate XORs, halving the code of a block;
-//   * the grid is persistent, one 512-thread CTA per SM: each CTA stays on
-//     one block of the matrix and its warps loop over that block's 1 KiB
-//     column tiles, so an SM holds one block's straight-line code (tens of
-//     KiB), fetched into its instruction caches once and then re-executed;
-//     blocks get CTAs in proportion to their cost.
+//   * the grid is persistent, one 512-thread CTA per SM: the sequence of
+//     (block, 1 KiB column tile) items is cut into equal-cost contiguous
+//     ranges, one per CTA, whose warps take the tiles in turn; so an SM holds
+//     one block's straight-line code (tens of KiB; two blocks' at a range
+//     boundary), fetched into its instruction caches once and re-executed,
+//     and every SM gets the same work whatever the number of blocks.
 //
 // The built-in XOR schedules are generated at build time from the library's
 // own construction (gen_bitslice.cpp); the launcher only uses a kernel whose
