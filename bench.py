@@ -256,9 +256,9 @@ class Workload:
         self.decode_missing = len(missing)
         self.helper_reads = reads_per_helper
         # the kernel each operation runs, and its ALU lane-ops per launch
-        # (alu_model); the reconstruction runs the run-time bitsliced kernel
-        # (blocks of at least 256 KiB), the helper projections and the
-        # newcomer the split-table region kernel
+        # (alu_model); the reconstruction (blocks of at least 256 KiB) and
+        # the newcomer (at least 1 MiB) run run-time bitsliced kernels, the
+        # helper projections the split-table region kernel
         P = self.P
         G = self.genc.generator()
         Gs = self.sysc.generator()[K:]
@@ -269,14 +269,15 @@ class Workload:
         Rm = R[missing] if missing else np.zeros((0, K), np.uint8)
         self.kernel = {"gen_encode": "bitsliced encode bs_n16_k8_c0_f0",
                        "sys_encode": "bitsliced encode bs_n16_k8_c1_f1",
-                       "repair_helpers": "region_kernel<1>", "repair_newcomer": "region_kernel<8>",
-                       "decode": "bitsliced reconstruction (compiled at run time)"}
+                       "repair_helpers": "region_kernel<1>",
+                       "repair_newcomer": "bitsliced newcomer bs_rt_newcomer (compiled at run time)",
+                       "decode": "bitsliced reconstruction bs_rt_decode (compiled at run time)"}
         self.alu_ops, self.alu_model = {}, {}
         for n, M, kind in (("gen_encode", G, "support"), ("sys_encode", Gs, "support"),
-                           ("decode", Rm, "chunked")):
+                           ("decode", Rm, "chunked"), ("repair_newcomer", Dn, "chunked")):
             self.alu_ops[n] = alu_ops_bitsliced(M, kind) * (B // 32)
             self.alu_model[n] = ALU_MODEL_BITSLICED
-        for n, M in (("repair_helpers", Mh), ("repair_newcomer", Dn)):
+        for n, M in (("repair_helpers", Mh),):
             self.alu_ops[n] = int(P.pmrc_plan_stats(M)["entries"]) * (B // 16) * 18
             self.alu_model[n] = ALU_MODEL_REGION
 

@@ -300,7 +300,7 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * PMRC_KERNEL_BITSLICED: the run-time kernel at any size, PMRC_EUNSUPPORTED
  * from pmrc_decode when it cannot be built.  Results are identical.  The
  * same choice applies to pmrc_repair_newcomer (its D, per failed node and
- * helper list), where AUTO takes the run-time kernel from 4 MiB blocks and
+ * helper list), where AUTO takes the run-time kernel from 1 MiB blocks and
  * PMRC_KERNEL_BITSLICED falls back to the split-table kernel rather than
  * failing.
  *

@@ -168,7 +168,7 @@ namespace {
 // node set, is paid once per handle), and for reconstructions whose blocks
 // read at most this many inputs
 constexpr size_t kRuntimeMinBytes = 256 << 10;
-constexpr size_t kRuntimeNewcomerMinBytes = 4 << 20;
+constexpr size_t kRuntimeNewcomerMinBytes = 1 << 20;
 constexpr int kRuntimeMaxInputs = 64;
 // AUTO compiles an encode schedule at run time only for encode matrices of
 // at most this many non-zero coefficients: NVRTC's time grows faster than
@@ -213,6 +213,7 @@ int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
 int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream);
 std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
+                                                const char *role,
                                                 const std::function<int(Mat &, std::string &)> &make,
                                                 std::string &err, bool by_support, bool background);
 void encode_matrix(const pmrc_code *c, Mat &M);
@@ -449,7 +450,7 @@ int encode_body(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *
       // no built-in schedule for this code: its encode matrix compiled at
       // run time (rows of identical support in blocks, as the built-in ones)
       std::string rerr;
-      std::shared_ptr<BsRuntimeKernel> k = runtime_kernel(c, "e", [&](Mat &M, std::string &) {
+      std::shared_ptr<BsRuntimeKernel> k = runtime_kernel(c, "e", "encode", [&](Mat &M, std::string &) {
         encode_matrix(c, M);
         return (int)kOk;
       }, rerr, true, policy != PMRC_KERNEL_BITSLICED);
@@ -509,8 +510,9 @@ int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
   const int d = c->m.d * c->m.beta, a = c->m.alpha;
   size_t done = 0;
   // bitsliced newcomer, compiled at run time per (failed node, helpers)
-  // like the reconstruction rows; a single 8-row block fills the GPU only on
-  // long columns (one 1 KiB tile per warp), so AUTO takes it from 4 MiB
+  // like the reconstruction rows; a single 8-row block gives one 1 KiB tile
+  // per warp, which beats the split-table kernel from 1 MiB blocks (at 1 MiB
+  // 15 against 19 us), so AUTO takes it from there
   if (want_runtime(c, c->decode_kernel, nbytes, kRuntimeNewcomerMinBytes)) {
     bool aligned = true;
     for (int i = 0; i < d && aligned; i++) aligned = received[i] && (uintptr_t)received[i] % 16 == 0;
@@ -520,7 +522,7 @@ int repair_newcomer_body(const pmrc_code *c, int f, const int *helpers,
     std::string rerr;
     std::shared_ptr<BsRuntimeKernel> k;
     if (aligned)
-      k = runtime_kernel(c, key, [&](Mat &M, std::string &e) {
+      k = runtime_kernel(c, key, "newcomer", [&](Mat &M, std::string &e) {
         return newcomer_matrix(c->m, f, helpers, M, e);
       }, rerr, false, c->decode_kernel != PMRC_KERNEL_BITSLICED);
     if (k) {
@@ -700,6 +702,7 @@ std::shared_ptr<BsRuntimeKernel> finish_job(const pmrc_code *c, const std::strin
 // compilation and returns null with an empty err, as do later calls until it
 // has finished: the caller runs the split-table kernel meanwhile.
 std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
+                                                const char *role,
                                                 const std::function<int(Mat &, std::string &)> &make,
                                                 std::string &err, bool by_support, bool background) {
   std::shared_ptr<BsJob> job;
@@ -738,11 +741,11 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
       }
     }
     if (job == fresh) {
-      auto work = [job, M, by_support]() {
+      auto work = [job, M, by_support, role]() {
         BsCompiled out;
         std::string e;
-        const int rc =
-            bitslice_compile(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support, out, e);
+        const int rc = bitslice_compile(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support,
+                                        role, out, e);
         {
           std::lock_guard<std::mutex> g(job->mu);
           job->rc = rc;
@@ -778,7 +781,7 @@ std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *n
   for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
   key += ":";
   for (char w : want) key += w ? '1' : '0';
-  return runtime_kernel(c, key, [&](Mat &M, std::string &e) {
+  return runtime_kernel(c, key, "decode", [&](Mat &M, std::string &e) {
     Mat R;
     int rc = decode_matrix(c->m, nodes, R, e);
     if (rc) return rc;

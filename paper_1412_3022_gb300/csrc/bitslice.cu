@@ -203,11 +203,12 @@ int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by
 }
 
 int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
-                     BsCompiled &out, std::string &err) {
+                     const char *role, BsCompiled &out, std::string &err) {
   std::vector<BsBlock> blks;
   int rc = runtime_blocks(M, rows, cols, max_inputs, by_support, blks, err);
   if (rc) return rc;
-  const char *kname = "bs_runtime_kernel";
+  out.name = std::string("bs_rt_") + role;
+  const char *kname = out.name.c_str();
   const BsEmitted em = bs_emit_kernel(M, rows, cols, blks, kname, true);
   const std::string src =
       "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\n"
@@ -224,7 +225,7 @@ int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool 
 
 int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
   auto k = std::make_shared<BsRuntimeKernel>();
-  const int rc = jit_load(c.cubin, "bs_runtime_kernel", &k->lib, &k->fn, err);
+  const int rc = jit_load(c.cubin, c.name.c_str(), &k->lib, &k->fn, err);
   if (rc) return rc;
   k->nblocks = c.nblocks;
   k->ninputs = c.ninputs;
@@ -235,9 +236,9 @@ int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, st
 }
 
 int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
-                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
+                   const char *role, std::shared_ptr<BsRuntimeKernel> &out, std::string &err) {
   BsCompiled c;
-  const int rc = bitslice_compile(M, rows, cols, max_inputs, by_support, c, err);
+  const int rc = bitslice_compile(M, rows, cols, max_inputs, by_support, role, c, err);
   return rc ? rc : bitslice_load(c, out, err);
 }
 

@@ -46,16 +46,17 @@ int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by
 
 // A compiled schedule not yet loaded: the cubin and what its launches need.
 struct BsCompiled {
+  std::string name;  // kernel name: bs_rt_<role>
   std::vector<char> cubin;
   int nblocks = 0, ninputs = 0, noutputs = 0;
   std::vector<int> cost;
 };
 
-// Emits and compiles the schedule for M (host only: NVRTC, no CUDA call, so
-// it may run on any thread).  kEUnsupported when bitslice_check fails or
-// NVRTC is missing or fails (message in err).
+// Emits and compiles the schedule for M as kernel bs_rt_<role> (host only:
+// NVRTC, no CUDA call, so it may run on any thread).  kEUnsupported when
+// bitslice_check fails or NVRTC is missing or fails (message in err).
 int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
-                     BsCompiled &out, std::string &err);
+                     const char *role, BsCompiled &out, std::string &err);
 
 // Loads a compiled schedule as a CUDA library (the calling thread's device
 // context must be usable).
@@ -63,7 +64,7 @@ int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, st
 
 // bitslice_compile, then bitslice_load.
 int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
-                   std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
+                   const char *role, std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
 
 // out[r] = sum_c M[r][c] in[c] over bytes [0, nbytes); nbytes a multiple of
 // 32, every pointer 16-byte aligned; in[c] may be NULL for columns no row
