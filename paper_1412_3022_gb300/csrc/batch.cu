@@ -25,6 +25,7 @@
 #include "../../include/pmrc.h"
 #include "api_internal.h"
 #include "batch_internal.h"
+#include "device_info.h"
 #include "gf256.h"
 
 namespace pmrc {
@@ -281,10 +282,11 @@ int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_byte
   return kOk;
 }
 
+static std::atomic<uint64_t> g_batch_smem_set[kMaxDevices];
+
 int worklist_ctas_per_sm(size_t smem) {
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(batch_kernel<kBatchR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    allow_max_smem(reinterpret_cast<const void *>(batch_kernel<kBatchR>), g_batch_smem_set, 0);
   int fit = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<kBatchR>, kThreads, smem);
   return fit < 1 ? 1 : fit;
@@ -293,8 +295,8 @@ int worklist_ctas_per_sm(size_t smem) {
 cudaError_t worklist_launch(const WorkItem *d_items, int nitems, uint8_t *const *d_ptrs,
                             unsigned *d_counter, unsigned grid, size_t smem, cudaStream_t stream) {
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(
-        batch_kernel<kBatchR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e =
+        allow_max_smem(reinterpret_cast<const void *>(batch_kernel<kBatchR>), g_batch_smem_set, 0);
     if (e != cudaSuccess) return e;
   }
   BatchArgs args;

@@ -106,8 +106,8 @@ cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs,
   for (int j = 0; j < noutputs; j++) a.ptr[ninputs + j] = out[j];
   const int sms = current_sm_count();
   const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes;  // 80 KiB
-  if (first_on_device(smem_set, slot)) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    const cudaError_t e = allow_max_smem(fn, smem_set, slot);
     if (e != cudaSuccess) return e;
   }
   // the work is the sequence of (block, tile) items g = b * ntiles + t; CTA

@@ -22,15 +22,30 @@ inline int current_sm_count() {
   return v;
 }
 
-// One bit per (device, slot) for settings made once per device, e.g. a
-// kernel's shared-memory opt-in.  Returns true the first time a pair is
-// claimed.
-inline bool first_on_device(std::atomic<uint64_t> (&mask)[kMaxDevices], int slot) {
+// Lets `fn` be launched with up to all the dynamic shared memory the
+// current device allows a block (its opt-in limit less the kernel's static
+// shared memory).  Made once per (device, slot): the bit in `done` is set
+// only after the setting succeeded, so a thread that finds it set can
+// launch, and concurrent first callers each make the (idempotent) setting.
+// The value is the largest any launch can ask for, so launches of one
+// kernel with different sizes never undo each other's setting.
+inline cudaError_t allow_max_smem(const void *fn, std::atomic<uint64_t> (&done)[kMaxDevices],
+                                  int slot) {
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= kMaxDevices || slot < 0 || slot >= 64) return true;
-  const uint64_t bit = 1ull << slot;
-  return !(mask[dev].fetch_or(bit, std::memory_order_relaxed) & bit);
+  const bool cached = dev >= 0 && dev < kMaxDevices && slot >= 0 && slot < 64;
+  const uint64_t bit = cached ? 1ull << slot : 0;
+  if (cached && (done[dev].load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && cached) done[dev].fetch_or(bit, std::memory_order_release);
+  return e;
 }
 
 }  // namespace pmrc

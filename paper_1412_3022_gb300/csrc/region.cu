@@ -138,9 +138,10 @@ cudaError_t launch_t(const Plan &plan, const void *image, const uint8_t *const *
   if (gy < 1) gy = 1;
   const dim3 grid((unsigned)nb, (unsigned)gy);
   const size_t smem = (size_t)plan.max_entries * 20 + (size_t)(plan.max_inputs + R) * 2 + 16;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(region_kernel<R, MAXP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {  // once per device for this kernel
+    static std::atomic<uint64_t> smem_set[kMaxDevices];
+    const cudaError_t e =
+        allow_max_smem(reinterpret_cast<const void *>(region_kernel<R, MAXP>), smem_set, 0);
     if (e != cudaSuccess) return e;
   }
   region_kernel<R, MAXP><<<grid, threads, smem, st>>>(a);
