@@ -396,6 +396,9 @@ def run_ours(args, rank, world, local_rank):
         except (OSError, ValueError):
             pass
 
+    # the end-to-end run comes before the extra rows: their handles, run-time
+    # compilations and allocations stay out of its pipelined copy timing
+    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     degraded = None
     if not args.no_extra:
         # the fused single-GPU repair (helper projections kept in scratch)
@@ -434,7 +437,6 @@ def run_ours(args, rank, world, local_rank):
     ksweep = None if (args.no_sweep or args.no_extra) else run_ksweep(torch, P, inputs, args, flush,
                                                                       stream, dev)
     init = None if args.no_extra else run_init(torch, P, inputs, args, dev)
-    e2e = None if args.no_e2e else run_e2e(torch, W, args, dev, stream, dist, world, inputs)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
     result = {
@@ -588,12 +590,18 @@ def run_init(torch, P, inputs, args, dev):
     out["decode_pattern_first_call_ms"] = round(first, 2)
     out["decode_pattern_kernel_ready_ms"] = round(ready, 2)
     out["decode_pattern_init_ms"] = round(first - again, 2)
-    first = wall(rep)
+    first = wall(rep)                    # plans; the newcomer's kernel compiling
+    t = time.perf_counter()
+    c.wait_kernels()                     # (no compilation outlives this section)
+    ready = first + (time.perf_counter() - t) * 1e3
+    wall(rep)
     again = min(wall(rep) for _ in range(3))
     out["repair_pattern_init_ms"] = round(first - again, 2)
-    out["note"] = ("host wall clock; the decode pattern's first call builds its plan and starts "
-                   "compiling its bitsliced kernel (NVRTC) in the background, running the "
-                   "split-table kernel meanwhile; kernel_ready is when the compilation ended")
+    out["repair_pattern_kernel_ready_ms"] = round(ready, 2)
+    out["note"] = ("host wall clock; a pattern's first call builds its plans and starts "
+                   "compiling its bitsliced kernel (NVRTC: the reconstruction's, the newcomer's) "
+                   "in the background, running the split-table kernel meanwhile; kernel_ready is "
+                   "when the compilation ended")
     del Y, Xr, recv, node, c
     torch.cuda.synchronize()
     return out
@@ -1079,10 +1087,13 @@ def run_e2e(torch, W, args, dev, stream, dist=None, world=1, inputs=None):
 
     for i in range(max(2, args.warmup)):
         step(i)
+    import gc
+
     import paper_1412_3022_gb300 as P
     P.wait_kernels()
     for i in range(2):              # both buffer sets load their kernels
         step(i)
+    gc.collect()                    # no handle is freed inside the timed steps
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
