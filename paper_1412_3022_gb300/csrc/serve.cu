@@ -84,7 +84,6 @@ class Arena {
   }
   size_t size() const { return size_; }
   size_t peak() const { return peak_; }
-  size_t used() const { return used_; }
 
  private:
   size_t size_, used_ = 0, peak_ = 0;
