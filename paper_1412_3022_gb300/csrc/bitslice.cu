@@ -37,7 +37,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <vector>
@@ -118,19 +117,7 @@ cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs,
   const uint64_t items = (uint64_t)nblocks * ntiles;
   const int ncta = (int)std::max<uint64_t>(1, std::min<uint64_t>(std::min(sms, kBsMaxCtas), items));
   a.ntiles = (uint32_t)ntiles;
-  double total = 0;
-  for (int i = 0; i < nblocks; i++) total += (double)cost[i] * (double)ntiles;
-  a.cta_g[0] = 0;
-  int b = 0;
-  double before = 0;  // cost of the blocks before b
-  for (int c = 1; c < ncta; c++) {
-    const double target = total * c / ncta;
-    while (b + 1 < nblocks && before + (double)cost[b] * ntiles < target) before += (double)cost[b++] * ntiles;
-    const double t = std::ceil((target - before) / (double)cost[b]);
-    uint64_t g = (uint64_t)b * ntiles + (uint64_t)std::min<double>(std::max(t, 0.0), (double)ntiles);
-    a.cta_g[c] = (uint32_t)std::max<uint64_t>(g, a.cta_g[c - 1]);
-  }
-  a.cta_g[ncta] = (uint32_t)items;
+  bs_cta_ranges(nblocks, cost, ntiles, ncta, a.cta_g);
   for (int c = ncta + 1; c <= kBsMaxCtas; c++) a.cta_g[c] = (uint32_t)items;
   void *args[] = {&a};
   return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);

@@ -2,6 +2,7 @@
 #include "bs_emit.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <map>
@@ -65,6 +66,25 @@ std::vector<BsBlock> bs_blocks_chunked(const uint8_t *M, int rows, int cols) {
     blks.push_back(B);
   }
   return blks;
+}
+
+void bs_cta_ranges(int nblocks, const int *cost, uint64_t ntiles, int ncta, uint32_t *cta_g) {
+  double total = 0;
+  for (int i = 0; i < nblocks; i++) total += (double)cost[i] * (double)ntiles;
+  const uint64_t items = (uint64_t)nblocks * ntiles;
+  cta_g[0] = 0;
+  int b = 0;
+  double before = 0;  // cost of the blocks before b
+  for (int c = 1; c < ncta; c++) {
+    const double target = total * c / ncta;
+    while (b + 1 < nblocks && before + (double)cost[b] * ntiles < target)
+      before += (double)cost[b++] * ntiles;
+    const double t = std::ceil((target - before) / (double)cost[b]);
+    const uint64_t g =
+        (uint64_t)b * ntiles + (uint64_t)std::min<double>(std::max(t, 0.0), (double)ntiles);
+    cta_g[c] = (uint32_t)std::max<uint64_t>(g, cta_g[c - 1]);
+  }
+  cta_g[ncta] = (uint32_t)items;
 }
 
 BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,

@@ -35,6 +35,13 @@ std::vector<BsBlock> bs_blocks_by_support(const uint8_t *M, int rows, int cols);
 // rows' non-zero columns (dense matrices such as reconstruction rows).
 std::vector<BsBlock> bs_blocks_chunked(const uint8_t *M, int rows, int cols);
 
+// The launch's work items g = b * ntiles + t (block b < nblocks, 1 KiB
+// column tile t < ntiles) cut into ncta contiguous ranges of about equal
+// cost (cost[b] per tile of block b): CTA c takes [cta_g[c], cta_g[c+1]),
+// with cta_g[0] = 0 <= cta_g[1] <= ... <= cta_g[ncta] = nblocks * ntiles.
+// Host only (the launcher's schedule; tested on the CPU).
+void bs_cta_ranges(int nblocks, const int *cost, uint64_t ntiles, int ncta, uint32_t *cta_g);
+
 struct BsEmitted {
   std::string code;       // block functions and the kernel
   std::vector<int> cost;  // relative cost of each block per warp tile
