@@ -1,7 +1,9 @@
 """Host-side units of the library built and run on the CPU: the split of a
 bitsliced launch's (block, tile) work items into per-CTA ranges, checked on
 20 000 random shapes (endpoints, order, and every CTA within one tile's cost
-of an equal share)."""
+of an equal share); and the bitsliced XOR schedules the emitter writes,
+evaluated statement by statement on the CPU against the GF(2^8) matrix
+product."""
 import os
 import shutil
 import subprocess
@@ -25,3 +27,81 @@ def test_bitsliced_cta_ranges():
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def _gf_mul(a, b):
+    """GF(2^8) product by shift and reduce (modulus 0x11D)."""
+    r = 0
+    while b:
+        if b & 1:
+            r ^= a
+        a <<= 1
+        if a & 0x100:
+            a ^= 0x11D
+        b >>= 1
+    return r
+
+
+def _evaluate_schedule(text, cols, X):
+    """Runs the emitted XOR schedule on byte columns X (cols x T) the way
+    the kernel does: per block, per input, bit planes -> subset tables Q, R
+    -> the case's accumulate statements; then planes back to bytes."""
+    import re
+    import numpy as np
+    T = X.shape[1]
+    planes = [((X >> j) & 1).astype(np.uint8) for j in range(8)]     # [j][col][t]
+    inputs = {int(b): [int(v) for v in lst.split(",")] for b, lst in
+              re.findall(r"k_b(\d+)_in\[\d+\] = \{([^}]*)\};", text)}
+    out = {}
+    for b, body in re.findall(r"void k_b(\d+)\(.*?\{(.*?)\n\}\n", text, re.S):
+        b = int(b)
+        acc = np.zeros((8, 8, T), np.uint8)
+        for i, case in re.findall(r"case (\d+):(.*?)break;", body, re.S):
+            col = inputs[b][int(i)]
+            p = [planes[j][col] for j in range(8)]
+            Q = [np.bitwise_xor.reduce([p[j] for j in range(4) if s >> j & 1] or [np.zeros(T, np.uint8)])
+                 for s in range(16)]
+            R = [np.bitwise_xor.reduce([p[4 + j] for j in range(4) if s >> j & 1] or [np.zeros(T, np.uint8)])
+                 for s in range(16)]
+            for q, bit, terms in re.findall(r"acc\[(\d+)\]\[(\d+)\] \^= ([^;]*);", case):
+                for name, idx in re.findall(r"([QR])\[(\d+)\]", terms):
+                    acc[int(q), int(bit)] ^= (Q if name == "Q" else R)[int(idx)]
+        kernel_case = re.search(r"case %d: \{\s*k_b%d\(x, acc\);(.*?)\} break;" % (b, b), text, re.S)
+        for slot, q in re.findall(r"bs_store\(x, (\d+), acc\[(\d+)\]\)", kernel_case.group(1)):
+            row = int(slot) - cols
+            out[row] = sum((acc[int(q), bit].astype(np.uint16) << bit) for bit in range(8)).astype(np.uint8)
+    return out
+
+
+@pytest.mark.parametrize("rows,cols,by_support,seed", [(13, 9, 0, 1), (21, 56, 0, 2), (8, 3, 1, 3),
+                                                       (30, 17, 1, 4), (1, 1, 0, 5), (7, 64, 0, 6)])
+def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed):
+    """The emitter's XOR schedule (blocks, input lists, subset-table terms,
+    output slots), evaluated on the CPU, equals the GF(2^8) matrix product
+    computed with an independent multiply."""
+    import numpy as np
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("g++ not found")
+    exe = os.path.join(ROOT, "_build", "test_emit_dump")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", exe,
+                        os.path.join(ROOT, "tests", "host", "emit_dump.cpp"),
+                        os.path.join(CSRC, "bs_emit.cpp")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe, str(rows), str(cols), str(by_support), str(seed)], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    head, code = r.stdout.split("CODE\n", 1)
+    lines = head.strip().splitlines()
+    M = np.array([[int(v) for v in ln.split()] for ln in lines[1:]], np.uint8)
+    assert M.shape == (rows, cols)
+    X = np.random.default_rng(seed).integers(0, 256, (cols, 64), dtype=np.uint8)
+    got = _evaluate_schedule(code, cols, X)
+    assert sorted(got) == list(range(rows))           # every row written once
+    for row in range(rows):
+        want = np.zeros(64, np.uint8)
+        for c in range(cols):
+            if M[row, c]:
+                want ^= np.array([_gf_mul(int(M[row, c]), int(x)) for x in X[c]], np.uint8)
+        assert np.array_equal(got[row], want), row
