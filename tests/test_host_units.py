@@ -1,9 +1,10 @@
 """Host-side units of the library built and run on the CPU: the split of a
 bitsliced launch's (block, tile) work items into per-CTA ranges, checked on
 20 000 random shapes (endpoints, order, and every CTA within one tile's cost
-of an equal share); and the bitsliced XOR schedules the emitter writes,
+of an equal share); the bitsliced XOR schedules the emitter writes,
 evaluated statement by statement on the CPU against the GF(2^8) matrix
-product."""
+product; and the on-disk cache of run-time compiled cubins (NVRTC runs on
+the CPU)."""
 import os
 import shutil
 import subprocess
@@ -105,3 +106,49 @@ def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed):
             if M[row, c]:
                 want ^= np.array([_gf_mul(int(M[row, c]), int(x)) for x in X[c]], np.uint8)
         assert np.array_equal(got[row], want), row
+
+
+def test_kernel_cache_on_disk():
+    """jit_compile with PMRC_KERNEL_CACHE: the first compilation writes one
+    cubin file (an ELF image, no temporary left), later ones read it back
+    unchanged; a damaged file is ignored and replaced."""
+    cxx = shutil.which("g++")
+    cuda = "/usr/local/cuda"
+    if not cxx or not os.path.exists(os.path.join(cuda, "include", "nvrtc.h")):
+        pytest.skip("g++ or the CUDA headers not found")
+    build = os.path.join(ROOT, "_build")
+    exe = os.path.join(build, "test_jit_cache")
+    r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-I" + os.path.join(cuda, "include"),
+                        "-o", exe, os.path.join(ROOT, "tests", "host", "jit_cache.cpp"),
+                        os.path.join(CSRC, "jit.cpp"), "-L" + os.path.join(cuda, "lib64"),
+                        "-lcudart", "-ldl", "-lpthread"], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("cannot build against the CUDA runtime here: " + r.stderr[-200:])
+    cache = os.path.join(build, "test_kernel_cache")
+    shutil.rmtree(cache, ignore_errors=True)
+    os.makedirs(cache)
+    env = dict(os.environ, PMRC_KERNEL_CACHE=cache,
+               LD_LIBRARY_PATH=os.path.join(cuda, "lib64") + ":" + os.environ.get("LD_LIBRARY_PATH", ""))
+
+    def run():
+        p = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=300)
+        assert p.returncode == 0, p.stdout + p.stderr
+        return p.stdout.strip()
+
+    first = run()
+    if first == "nonvrtc":
+        pytest.skip("NVRTC is not available")
+    assert first.startswith("ok")
+    files = sorted(os.listdir(cache))
+    assert len(files) == 1 and files[0].startswith("pmrc-") and files[0].endswith(".cubin"), files
+    path = os.path.join(cache, files[0])
+    with open(path, "rb") as f:
+        image = f.read()
+    assert image[:4] == b"\x7fELF"
+    assert run() == first and sorted(os.listdir(cache)) == files
+    with open(path, "wb") as f:                      # damaged: not a cubin
+        f.write(b"garbage")
+    assert run() == first
+    with open(path, "rb") as f:
+        assert f.read() == image                     # replaced by a fresh compilation
+    shutil.rmtree(cache)
