@@ -145,11 +145,17 @@ int pmrc_repair_helpers(const pmrc_code *code, int failed, int nhelpers, const i
                         const uint8_t *const *helper_blocks, uint8_t *const *out,
                         size_t block_bytes, pmrc_stream_t stream);
 
-/* Newcomer side of the repair: from the d projected blocks received from
- * `helpers` (d distinct node ids != failed, host array, same order as
- * received), rebuild the alpha blocks of node `failed` with
- * D = [I | lambda_f I] Psi_H^-1.  PMRC_ESINGULAR when the helpers' rows of
- * Psi are singular (possible at n >= 2k for the sparse code). */
+/* Newcomer side of the repair of node `failed` (Sec. 2: exact repair at the
+ * MSR point from d = 2k-2 helpers, each sending beta = 1 block; Sec. 3.3:
+ * the product-matrix repair the sparse code keeps).  From the d projected
+ * blocks received from `helpers` (d distinct node ids != failed, host
+ * array, same order as received), rebuild the alpha blocks of node `failed`
+ * with D = [I | lambda_f I] Psi_H^-1: Psi_H M phi_f = p gives M phi_f, whose
+ * halves S1 phi_f and S2 phi_f give, by the symmetry of S1 and S2, the
+ * stored content phi_f^t S1 + lambda_f phi_f^t S2.  received: d device
+ * pointers; out: alpha device pointers (never NULL).  PMRC_ESINGULAR when
+ * the helpers' rows of Psi are singular (possible at n >= 2k for the sparse
+ * code). */
 int pmrc_repair_newcomer(const pmrc_code *code, int failed, const int *helpers,
                          const uint8_t *const *received, uint8_t *const *out,
                          size_t block_bytes, pmrc_stream_t stream);

@@ -169,6 +169,10 @@ namespace {
 // read at most this many inputs
 constexpr size_t kRuntimeMinBytes = 256 << 10;
 constexpr size_t kRuntimeNewcomerMinBytes = 1 << 20;
+// helper projections and the fused repair through run-time bitsliced
+// kernels (compiled per failed node, resp. per failed node and helper set)
+constexpr size_t kRuntimeHelperMinBytes = 256 << 10;
+constexpr size_t kRuntimeRepairMinBytes = 256 << 10;
 constexpr int kRuntimeMaxInputs = 64;
 // AUTO compiles an encode schedule at run time only for encode matrices of
 // at most this many non-zero coefficients: NVRTC's time grows faster than
@@ -218,6 +222,10 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
                                                 std::string &err, bool by_support, bool background);
 void encode_matrix(const pmrc_code *c, Mat &M);
 bool want_runtime(const pmrc_code *c, int policy, size_t nbytes, size_t auto_min);
+std::shared_ptr<BsRuntimeKernel> projection_runtime(const pmrc_code *c, int f, bool background,
+                                                    std::string &err);
+std::shared_ptr<BsRuntimeKernel> fused_runtime(const pmrc_code *c, int f, const int *helpers,
+                                               bool background, std::string &err);
 
 }  // namespace
 
@@ -493,7 +501,42 @@ int repair_helpers_body(const pmrc_code *c, int f, int nh, const int *helpers,
   std::string err;
   int rc = helper_plan(c, f, nh, p, err);
   if (rc) return fail(rc, err);
-  rc = launch_region(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int a = c->m.alpha;
+  size_t done = 0;
+  // bitsliced projections, compiled at run time per failed node: each block
+  // phi_f reads is turned into bit planes once and multiplied by its
+  // constant as XORs of planes
+  if (c->m.beta == 1 && nh * a + nh <= bitslice_max_pointers() &&
+      want_runtime(c, c->decode_kernel, nbytes, kRuntimeHelperMinBytes)) {
+    std::vector<uint8_t> phi;
+    helper_coefficients(c->m, f, phi);
+    bool aligned = true;
+    for (int h = 0; h < nh && aligned; h++) {
+      for (int j = 0; j < a; j++)
+        if (phi[j]) aligned = aligned && blocks[h * a + j] && (uintptr_t)blocks[h * a + j] % 16 == 0;
+      aligned = aligned && (uintptr_t)out[h] % 16 == 0;
+    }
+    std::string rerr;
+    std::shared_ptr<BsRuntimeKernel> k;
+    if (aligned) k = projection_runtime(c, f, c->decode_kernel != PMRC_KERNEL_BITSLICED, rerr);
+    if (k) {
+      done = nbytes & ~(size_t)31;
+      const cudaError_t e = bitslice_launch_projection(*k, nh, blocks, out, done, st);
+      if (e != cudaSuccess)
+        return fail(PMRC_ECUDA, std::string("bitsliced projection launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (done == nbytes) return PMRC_OK;
+  if (done == 0) {
+    rc = launch_region(*p, blocks, out, nbytes, st, err);
+  } else {  // ragged tail of the blocks
+    std::vector<const uint8_t *> in2(nh * a);
+    std::vector<uint8_t *> out2(nh);
+    for (int i = 0; i < nh * a; i++) in2[i] = blocks[i] ? blocks[i] + done : nullptr;
+    for (int h = 0; h < nh; h++) out2[h] = out[h] + done;
+    rc = launch_region(*p, in2.data(), out2.data(), nbytes - done, st, err);
+  }
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
@@ -610,7 +653,40 @@ int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *co
   std::shared_ptr<FusedRepairPlan> p;
   int rc = fused_repair_plan(c, f, helpers, p, err);
   if (rc) return fail(rc, err);
-  rc = launch_fused_repair(*p, blocks, out, nbytes, (cudaStream_t)stream, err);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int a = c->m.alpha, d = c->m.d;
+  size_t done = 0;
+  // bitsliced fused repair, compiled at run time per (failed node, helpers):
+  // projections as XORs of bit planes kept in registers, applied straight
+  // to the newcomer matrix
+  if (a <= 8 && want_runtime(c, c->decode_kernel, nbytes, kRuntimeRepairMinBytes)) {
+    std::vector<uint8_t> phi;
+    helper_coefficients(c->m, f, phi);
+    bool aligned = true;
+    for (int q = 0; q < d && aligned; q++)
+      for (int j = 0; j < a; j++)
+        if (phi[j]) aligned = aligned && blocks[q * a + j] && (uintptr_t)blocks[q * a + j] % 16 == 0;
+    for (int r = 0; r < a && aligned; r++) aligned = out[r] && (uintptr_t)out[r] % 16 == 0;
+    std::string rerr;
+    std::shared_ptr<BsRuntimeKernel> k;
+    if (aligned) k = fused_runtime(c, f, helpers, c->decode_kernel != PMRC_KERNEL_BITSLICED, rerr);
+    if (k) {
+      done = nbytes & ~(size_t)31;
+      const cudaError_t e = bitslice_launch_fused_repair(*k, blocks, out, done, st);
+      if (e != cudaSuccess)
+        return fail(PMRC_ECUDA, std::string("bitsliced repair launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (done == nbytes) return PMRC_OK;
+  if (done == 0) {
+    rc = launch_fused_repair(*p, blocks, out, nbytes, st, err);
+  } else {  // ragged tail of the blocks
+    std::vector<const uint8_t *> in2(d * a);
+    std::vector<uint8_t *> out2(a);
+    for (int i = 0; i < d * a; i++) in2[i] = blocks[i] ? blocks[i] + done : nullptr;
+    for (int r = 0; r < a; r++) out2[r] = out[r] + done;
+    rc = launch_fused_repair(*p, in2.data(), out2.data(), nbytes - done, st, err);
+  }
   return rc ? fail(rc, err) : PMRC_OK;
 }
 
@@ -695,16 +771,19 @@ std::shared_ptr<BsRuntimeKernel> finish_job(const pmrc_code *c, const std::strin
   return it->second;
 }
 
-// A bitsliced kernel compiled at run time for matrix M (blocks of rows of
-// identical support when by_support, else consecutive rows), cached in the
-// handle under `key`; null when it cannot be built (the reason in err, also
-// cached).  In the background (AUTO policies) the first call only starts the
-// compilation and returns null with an empty err, as do later calls until it
-// has finished: the caller runs the split-table kernel meanwhile.
-std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
-                                                const char *role,
-                                                const std::function<int(Mat &, std::string &)> &make,
-                                                std::string &err, bool by_support, bool background) {
+using BsCompileFn = std::function<int(BsCompiled &, std::string &)>;
+
+// A bitsliced kernel compiled at run time, cached in the handle under `key`;
+// null when it cannot be built (the reason in err, also cached).  `prepare`
+// runs on the calling thread: it checks the request and returns the
+// compilation to run (or an error code, cached as a failed key).  In the
+// background (AUTO policies) the first call only starts the compilation and
+// returns null with an empty err, as do later calls until it has finished:
+// the caller runs the split-table kernel meanwhile.
+std::shared_ptr<BsRuntimeKernel> runtime_kernel_job(
+    const pmrc_code *c, const std::string &key,
+    const std::function<int(BsCompileFn &, std::string &)> &prepare, std::string &err,
+    bool background) {
   std::shared_ptr<BsJob> job;
   {
     std::lock_guard<std::mutex> g(c->mu);
@@ -717,12 +796,8 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
     if (jt != c->rt_jobs.end()) job = jt->second;
   }
   if (!job) {
-    Mat M;
-    int rc = make(M, err);
-    if (!rc && M.rows == 0) {
-      err = "no rows to compute";
-      rc = kEUnsupported;
-    }
+    BsCompileFn compile;
+    const int rc = prepare(compile, err);
     if (rc) {
       std::lock_guard<std::mutex> g(c->mu);
       c->rt[key] = nullptr;
@@ -741,11 +816,10 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
       }
     }
     if (job == fresh) {
-      auto work = [job, M, by_support, role]() {
+      auto work = [job, compile]() {
         BsCompiled out;
         std::string e;
-        const int rc = bitslice_compile(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support,
-                                        role, out, e);
+        const int rc = compile(out, e);
         {
           std::lock_guard<std::mutex> g(job->mu);
           job->rc = rc;
@@ -771,6 +845,63 @@ std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::s
   }
   std::lock_guard<std::mutex> g(c->mu);
   return finish_job(c, key, *job, err);
+}
+
+// A bitsliced kernel compiled at run time for matrix M (blocks of rows of
+// identical support when by_support, else consecutive rows); see
+// runtime_kernel_job.
+std::shared_ptr<BsRuntimeKernel> runtime_kernel(const pmrc_code *c, const std::string &key,
+                                                const char *role,
+                                                const std::function<int(Mat &, std::string &)> &make,
+                                                std::string &err, bool by_support, bool background) {
+  return runtime_kernel_job(c, key, [&](BsCompileFn &compile, std::string &e) {
+    Mat M;
+    int rc = make(M, e);
+    if (!rc && M.rows == 0) {
+      e = "no rows to compute";
+      rc = kEUnsupported;
+    }
+    if (rc) return rc;
+    compile = [M, by_support, role](BsCompiled &out, std::string &e2) {
+      return bitslice_compile(M.v.data(), M.rows, M.cols, kRuntimeMaxInputs, by_support, role, out,
+                              e2);
+    };
+    return (int)kOk;
+  }, err, background);
+}
+
+// Bitsliced helper projections for failed node f (one kernel serves any
+// number of helpers: phi_f is the same for all of them).
+std::shared_ptr<BsRuntimeKernel> projection_runtime(const pmrc_code *c, int f, bool background,
+                                                    std::string &err) {
+  return runtime_kernel_job(c, "p:" + std::to_string(f), [&](BsCompileFn &compile, std::string &) {
+    std::vector<uint8_t> phi;
+    helper_coefficients(c->m, f, phi);
+    const int alpha = c->m.alpha;
+    compile = [phi, alpha](BsCompiled &out, std::string &e2) {
+      return bitslice_compile_projection(phi.data(), alpha, "project", out, e2);
+    };
+    return (int)kOk;
+  }, err, background);
+}
+
+// Bitsliced fused repair of failed node f from `helpers` (alpha <= 8).
+std::shared_ptr<BsRuntimeKernel> fused_runtime(const pmrc_code *c, int f, const int *helpers,
+                                               bool background, std::string &err) {
+  std::string key = "r:" + std::to_string(f);
+  for (int i = 0; i < c->m.d; i++) key += "," + std::to_string(helpers[i]);
+  return runtime_kernel_job(c, key, [&](BsCompileFn &compile, std::string &e) {
+    Mat D;
+    const int rc = newcomer_matrix(c->m, f, helpers, D, e);
+    if (rc) return rc;
+    std::vector<uint8_t> phi;
+    helper_coefficients(c->m, f, phi);
+    const int alpha = c->m.alpha, d = c->m.d;
+    compile = [phi, alpha, D, d](BsCompiled &out, std::string &e2) {
+      return bitslice_compile_fused_repair(phi.data(), alpha, D.v.data(), d, "repair", out, e2);
+    };
+    return (int)kOk;
+  }, err, background);
 }
 
 // Bitsliced reconstruction rows for this (nodes, wanted rows).

@@ -141,7 +141,9 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
 struct BsRuntimeKernel {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t fn = nullptr;
+  int kind = kBsMatrix;
   int nblocks = 0, ninputs = 0, noutputs = 0;
+  int alpha = 0, d = 0;
   std::vector<int> cost;
   std::atomic<uint64_t> smem_set[kMaxDevices] = {};
   ~BsRuntimeKernel() {
@@ -203,6 +205,7 @@ int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool 
       std::string(kBsDevSrc) + "\n" + em.code;
   rc = jit_compile(src, kname, out.cubin, err);
   if (rc) return rc;
+  out.kind = kBsMatrix;
   out.nblocks = (int)blks.size();
   out.ninputs = cols;
   out.noutputs = rows;
@@ -214,9 +217,12 @@ int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, st
   auto k = std::make_shared<BsRuntimeKernel>();
   const int rc = jit_load(c.cubin, c.name.c_str(), &k->lib, &k->fn, err);
   if (rc) return rc;
+  k->kind = c.kind;
   k->nblocks = c.nblocks;
   k->ninputs = c.ninputs;
   k->noutputs = c.noutputs;
+  k->alpha = c.alpha;
+  k->d = c.d;
   k->cost = c.cost;
   out = k;
   return kOk;
@@ -236,5 +242,114 @@ cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in
 }
 
 int bitslice_max_pointers() { return kBsMaxPtr; }
+
+namespace {
+
+std::string runtime_source(const std::string &code) {
+  return "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\n"
+         "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n" +
+         std::string(kBsDevSrc) + "\n" + code;
+}
+
+bool any_nonzero(const uint8_t *v, int n) {
+  for (int i = 0; i < n; i++)
+    if (v[i]) return true;
+  return false;
+}
+
+// Arguments common to the repair launches; in and out as for the matrix
+// kernels (slot nin + r is output r).
+void repair_args(BsArgs &a, size_t nbytes, int nin, const uint8_t *const *in, int nout,
+                 uint8_t *const *out) {
+  memset(&a, 0, sizeof a);
+  a.nbytes = nbytes;
+  a.hi28 = 1u << 28;
+  a.hi30 = 1u << 30;
+  a.hi31 = 1u << 31;
+  a.x16 = 16;
+  a.x4 = 4;
+  a.x2 = 2;
+  a.ntiles = (uint32_t)((nbytes + kBsUnit - 1) / kBsUnit);
+  for (int i = 0; i < nin; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
+  for (int j = 0; j < nout; j++) a.ptr[nin + j] = out[j];
+}
+
+}  // namespace
+
+int bitslice_compile_projection(const uint8_t *phi, int alpha, const char *role, BsCompiled &out,
+                                std::string &err) {
+  if (alpha <= 0 || alpha + 1 > kBsMaxPtr || !any_nonzero(phi, alpha)) {
+    err = "helper coefficients do not fit a bitsliced projection";
+    return kEUnsupported;
+  }
+  out.name = std::string("bs_rt_") + role;
+  const BsEmitted em = bs_emit_projection(phi, alpha, out.name);
+  const int rc = jit_compile(runtime_source(em.code), out.name.c_str(), out.cubin, err);
+  if (rc) return rc;
+  out.kind = kBsProjection;
+  out.alpha = alpha;
+  out.d = 0;
+  return kOk;
+}
+
+int bitslice_compile_fused_repair(const uint8_t *phi, int alpha, const uint8_t *D, int d,
+                                  const char *role, BsCompiled &out, std::string &err) {
+  if (alpha <= 0 || alpha > kBsFusedMaxAlpha || d < 2 || d * alpha + alpha > kBsMaxPtr ||
+      !any_nonzero(phi, alpha)) {
+    err = "repair does not fit the bitsliced fused kernel (alpha <= 8, d*alpha + alpha <= 512)";
+    return kEUnsupported;
+  }
+  out.name = std::string("bs_rt_") + role;
+  const BsEmitted em = bs_emit_fused_repair(phi, alpha, D, d, out.name);
+  const int rc = jit_compile(runtime_source(em.code), out.name.c_str(), out.cubin, err);
+  if (rc) return rc;
+  out.kind = kBsFusedRepair;
+  out.alpha = alpha;
+  out.d = d;
+  return kOk;
+}
+
+int bitslice_kind(const BsRuntimeKernel &k) { return k.kind; }
+
+cudaError_t bitslice_launch_projection(BsRuntimeKernel &k, int nh, const uint8_t *const *in,
+                                       uint8_t *const *out, size_t nbytes, cudaStream_t stream) {
+  if (k.kind != kBsProjection || nh <= 0 || nh * k.alpha + nh > kBsMaxPtr || nbytes % kBsBytes)
+    return cudaErrorInvalidValue;
+  BsArgs a;
+  repair_args(a, nbytes, nh * k.alpha, in, nh, out);
+  a.nh = (uint32_t)nh;
+  a.ngroups = (uint32_t)((nh + kBsHelpersPerTask - 1) / kBsHelpersPerTask);
+  a.ntasks = a.ntiles * a.ngroups;
+  const void *fn = reinterpret_cast<const void *>(k.fn);
+  const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes;
+  cudaError_t e = allow_max_smem(fn, k.smem_set, 0);
+  if (e != cudaSuccess) return e;
+  // two CTAs per SM (the projection kernel needs few registers): more loads
+  // in flight for this memory-bound kernel
+  const uint64_t warps = kBsThreads / 32;
+  const int ncta = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>(2 * (uint64_t)current_sm_count(), (a.ntasks + warps - 1) / warps));
+  void *args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);
+}
+
+cudaError_t bitslice_launch_fused_repair(BsRuntimeKernel &k, const uint8_t *const *in,
+                                         uint8_t *const *out, size_t nbytes, cudaStream_t stream) {
+  if (k.kind != kBsFusedRepair || nbytes % kBsBytes) return cudaErrorInvalidValue;
+  BsArgs a;
+  repair_args(a, nbytes, k.d * k.alpha, in, k.alpha, out);
+  a.nh = (uint32_t)k.d;
+  const void *fn = reinterpret_cast<const void *>(k.fn);
+  // the staging ring, then one exchange area (alpha x 8 planes x 32 lanes) per warp pair
+  const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes +
+                      (size_t)(kBsThreads / 64) * k.alpha * 8 * 32 * 4;
+  cudaError_t e = allow_max_smem(fn, k.smem_set, 0);
+  if (e != cudaSuccess) return e;
+  const uint64_t pairs = kBsThreads / 64;
+  const int ncta = (int)std::max<uint64_t>(
+      1, std::min<uint64_t>(current_sm_count(), (a.ntiles + pairs - 1) / pairs));
+  void *args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);
+}
 
 }  // namespace pmrc

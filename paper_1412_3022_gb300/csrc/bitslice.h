@@ -29,6 +29,7 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
 
 int bitslice_max_pointers();
 
+
 // A bitsliced kernel compiled at run time (NVRTC) for a matrix known only
 // then: the rows of a reconstruction or a newcomer's apply (consecutive rows
 // in blocks of at most 8 over the union of their inputs), or the encode
@@ -44,11 +45,18 @@ struct BsRuntimeKernel;
 int bitslice_check(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
                    std::string &err);
 
+// Kinds of run-time kernels: a matrix schedule (reconstruction rows,
+// newcomer apply, encode), helper projections for one failed node, and the
+// fused repair of one (failed node, helper set).
+enum BsKind { kBsMatrix = 0, kBsProjection = 1, kBsFusedRepair = 2 };
+
 // A compiled schedule not yet loaded: the cubin and what its launches need.
 struct BsCompiled {
   std::string name;  // kernel name: bs_rt_<role>
   std::vector<char> cubin;
+  int kind = kBsMatrix;
   int nblocks = 0, ninputs = 0, noutputs = 0;
+  int alpha = 0, d = 0;  // repair kernels: blocks per node, helpers
   std::vector<int> cost;
 };
 
@@ -71,5 +79,29 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by
 // reads, out[r] may not be NULL.
 cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,
                                     uint8_t *const *out, size_t nbytes, cudaStream_t stream);
+
+// Repair schedules compiled at run time (host only, like bitslice_compile).
+// Projection: phi (alpha entries, at least one non-zero), kernel
+// bs_rt_<role>.  Fused repair: phi and the newcomer matrix D (alpha x d,
+// row-major, alpha <= 8).  kEUnsupported when a limit is exceeded or NVRTC
+// is missing or fails.
+int bitslice_compile_projection(const uint8_t *phi, int alpha, const char *role, BsCompiled &out,
+                                std::string &err);
+int bitslice_compile_fused_repair(const uint8_t *phi, int alpha, const uint8_t *D, int d,
+                                  const char *role, BsCompiled &out, std::string &err);
+
+// Helper projections of nh helpers: in = nh*alpha blocks (helper h's at
+// [h*alpha, h*alpha + alpha); blocks phi does not read may be NULL), out = nh
+// blocks; nbytes a multiple of 32, pointers 16-byte aligned;
+// nh*alpha + nh <= bitslice_max_pointers().
+cudaError_t bitslice_launch_projection(BsRuntimeKernel &k, int nh, const uint8_t *const *in,
+                                       uint8_t *const *out, size_t nbytes, cudaStream_t stream);
+
+// Fused repair: in = d*alpha helper blocks (as above), out = alpha blocks.
+cudaError_t bitslice_launch_fused_repair(BsRuntimeKernel &k, const uint8_t *const *in,
+                                         uint8_t *const *out, size_t nbytes, cudaStream_t stream);
+
+// The kind of a loaded run-time kernel (BsKind).
+int bitslice_kind(const BsRuntimeKernel &k);
 
 }  // namespace pmrc

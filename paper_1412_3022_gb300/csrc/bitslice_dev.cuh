@@ -20,6 +20,9 @@ struct BsArgs {
   // the launch's work is the sequence of warp tiles g = b * ntiles + t
   // (block b, 1 KiB column tile t); CTA c takes tiles [cta_g[c], cta_g[c+1])
   uint32_t ntiles;
+  // repair kernels (bs_emit_projection / bs_emit_fused_repair): helpers in
+  // the launch, helper groups per tile, and warp tasks (tiles x groups)
+  uint32_t nh, ngroups, ntasks;
   uint32_t cta_g[kBsMaxCtas + 1];
   uint8_t *ptr[kBsMaxPtr];    // K input blocks, then the output blocks
 };
@@ -42,6 +45,30 @@ __device__ __forceinline__ void bs_zero(uint32_t (&acc)[8][8]) {
     for (int i = 0; i < 8; i++) acc[r][i] = 0;
 }
 
+// Three-input XOR and two-input XOR as single logic instructions (lop3 with
+// the truth table of a ^ b ^ c, 0x96), so that every accumulate of a
+// schedule is exactly one instruction whatever the compiler would otherwise
+// fuse or split.
+__device__ __forceinline__ uint32_t bs_x3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t bs_x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("xor.b32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Bit-field select (a & M) | (b & ~M) for a constant mask M: one lop3
+// (truth table 0xE4 with M as the third operand).
+template <uint32_t M>
+__device__ __forceinline__ uint32_t bs_sel(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(a), "r"(b), "n"(M));
+  return d;
+}
+
 // 8x8 bit transpose inside each byte lane of 8 words: afterwards word i
 // holds bit i of the 32 bytes (bit 8m+j = bit i of byte m of word j).  The
 // transform is an involution.  Each stage exchanges the bit fields `mask` of
@@ -52,34 +79,43 @@ __device__ __forceinline__ void bs_transpose(uint32_t (&w)[8], const BsArgs &a) 
 #pragma unroll
   for (int j = 0; j < 4; j++) {
     const uint32_t sl = __umulhi(w[j], a.hi28), sh = w[j + 4] * a.x16;
-    w[j + 4] = (sl & 0x0F0F0F0Fu) | (w[j + 4] & ~0x0F0F0F0Fu);
-    w[j] = (sh & 0xF0F0F0F0u) | (w[j] & ~0xF0F0F0F0u);
+    w[j + 4] = bs_sel<0x0F0F0F0Fu>(sl, w[j + 4]);
+    w[j] = bs_sel<0xF0F0F0F0u>(sh, w[j]);
   }
 #pragma unroll
   for (int j = 0; j < 8; j += 4)
 #pragma unroll
     for (int q = 0; q < 2; q++) {
       const uint32_t sl = __umulhi(w[j + q], a.hi30), sh = w[j + q + 2] * a.x4;
-      w[j + q + 2] = (sl & 0x33333333u) | (w[j + q + 2] & ~0x33333333u);
-      w[j + q] = (sh & 0xCCCCCCCCu) | (w[j + q] & ~0xCCCCCCCCu);
+      w[j + q + 2] = bs_sel<0x33333333u>(sl, w[j + q + 2]);
+      w[j + q] = bs_sel<0xCCCCCCCCu>(sh, w[j + q]);
     }
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
     const uint32_t sl = __umulhi(w[j], a.hi31), sh = w[j + 1] * a.x2;
-    w[j + 1] = (sl & 0x55555555u) | (w[j + 1] & ~0x55555555u);
-    w[j] = (sh & 0xAAAAAAAAu) | (w[j] & ~0xAAAAAAAAu);
+    w[j + 1] = bs_sel<0x55555555u>(sl, w[j + 1]);
+    w[j] = bs_sel<0xAAAAAAAAu>(sh, w[j]);
   }
 }
 
-// Asynchronous copy of this thread's 32 bytes of input `col` into ring slot
-// `slot` of the shared-memory staging area (cp.async, one commit group per
-// input).  Each thread reads back only what it copied, so no barrier is
-// needed; cp.async.wait_group orders the read after the copy.
-__device__ __forceinline__ void bs_prefetch(const BsCtx &x, int col, int slot) {
+// Shared-memory staging ring of the per-thread input copies: slot s of
+// thread t is at byte (s * kBsThreads + t) * kBsBytes of the dynamic shared
+// memory.  bs_ring_base() is this thread's slot 0 as a shared-space address;
+// the emitted loops advance a read and a write address by one slot per input
+// and wrap them, so no slot index is recomputed per input.
+constexpr uint32_t kBsSlotStep = kBsThreads * kBsBytes;
+
+__device__ __forceinline__ uint32_t bs_ring_base() {
   extern __shared__ __align__(16) uint8_t bs_smem[];
+  return (uint32_t)__cvta_generic_to_shared(bs_smem + threadIdx.x * kBsBytes);
+}
+
+// Asynchronous copy of this thread's 32 bytes of an input block into the
+// ring slot at shared address `dst` (cp.async, one commit group per input).
+// Each thread reads back only what it copied, so no barrier is needed;
+// cp.async.wait_group orders the read after the copy.
+__device__ __forceinline__ void bs_prefetch(const BsCtx &x, int col, uint32_t dst) {
   const uint8_t *src = x.a->ptr[col] + x.off;
-  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(
-      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16), "l"(src + 16)
                : "memory");
@@ -95,36 +131,61 @@ __device__ __forceinline__ void bs_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void bs_planes(const BsCtx &x, int slot, uint32_t (&Q)[16],
+// The 32 staged bytes at shared address `src`, as eight words.
+__device__ __forceinline__ void bs_load(uint32_t src, uint32_t (&w)[8]) {
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+               : "r"(src)
+               : "memory");
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+               : "r"(src + 16)
+               : "memory");
+}
+
+// Subset tables of eight bit planes: Q[s] is the XOR of the planes 0-3
+// selected by the bits of s, R[s] the same over planes 4-7.
+__device__ __forceinline__ void bs_tables(const uint32_t (&w)[8], uint32_t (&Q)[16],
                                           uint32_t (&R)[16]) {
-  extern __shared__ __align__(16) uint8_t bs_smem[];
-  const uint4 *p = reinterpret_cast<const uint4 *>(
-      bs_smem + ((size_t)slot * kBsThreads + threadIdx.x) * kBsBytes);
-  const uint4 u = p[0], v = p[1];
-  uint32_t w[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
-  bs_transpose(w, *x.a);
   Q[0] = 0;
   Q[1] = w[0];
   Q[2] = w[1];
-  Q[3] = w[0] ^ w[1];
+  Q[3] = bs_x2(w[0], w[1]);
   Q[4] = w[2];
-  Q[5] = w[2] ^ w[0];
-  Q[6] = w[2] ^ w[1];
-  Q[7] = w[2] ^ Q[3];
+  Q[5] = bs_x2(w[2], w[0]);
+  Q[6] = bs_x2(w[2], w[1]);
+  Q[7] = bs_x3(w[2], w[0], w[1]);
   Q[8] = w[3];
 #pragma unroll
-  for (int s = 9; s < 16; s++) Q[s] = w[3] ^ Q[s - 8];
+  for (int s = 9; s < 16; s++) Q[s] = bs_x2(w[3], Q[s - 8]);
   R[0] = 0;
   R[1] = w[4];
   R[2] = w[5];
-  R[3] = w[4] ^ w[5];
+  R[3] = bs_x2(w[4], w[5]);
   R[4] = w[6];
-  R[5] = w[6] ^ w[4];
-  R[6] = w[6] ^ w[5];
-  R[7] = w[6] ^ R[3];
+  R[5] = bs_x2(w[6], w[4]);
+  R[6] = bs_x2(w[6], w[5]);
+  R[7] = bs_x3(w[6], w[4], w[5]);
   R[8] = w[7];
 #pragma unroll
-  for (int s = 9; s < 16; s++) R[s] = w[7] ^ R[s - 8];
+  for (int s = 9; s < 16; s++) R[s] = bs_x2(w[7], R[s - 8]);
+}
+
+// The 32 staged bytes at shared address `src` as bit planes, and their
+// subset tables.
+__device__ __forceinline__ void bs_planes(const BsCtx &x, uint32_t src, uint32_t (&Q)[16],
+                                          uint32_t (&R)[16]) {
+  uint32_t w[8];
+  bs_load(src, w);
+  bs_transpose(w, *x.a);
+  bs_tables(w, Q, R);
+}
+
+// Barrier of the two warps of pair `pair` (named barrier 1 + pair, 64
+// threads); the fused repair kernels exchange partial sums through shared
+// memory between them.
+__device__ __forceinline__ void bs_pair_sync(uint32_t pair) {
+  asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
 }
 
 __device__ __forceinline__ void bs_store(const BsCtx &x, int slot, uint32_t (&planes)[8]) {

@@ -112,17 +112,23 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
     // one loop over the inputs: prefetch, transpose and subset tables are
     // emitted once; only the accumulate XORs differ per input (a switch),
     // which keeps a block's code at about half its fully unrolled size.
-    // Short blocks commit empty groups so the wait count stays kAhead - 1.
+    // The ring's read and write slots advance by one slot per input and wrap
+    // (no slot index arithmetic).  Short blocks commit empty groups so the
+    // wait count stays kAhead - 1.
     appendf(f, "  const uint8_t *in = %s_b%zu_in;\n", name.c_str(), b);
+    f += "  const uint32_t base = bs_ring_base(), end = base + kBsSlots * kBsSlotStep;\n";
     for (int i = 0; i < kAhead; i++)
       if (i < C)
-        appendf(f, "  bs_prefetch(x, %d, %d);\n", B.inputs[i], i % kSlots);
+        appendf(f, "  bs_prefetch(x, %d, base + %d * kBsSlotStep);\n", B.inputs[i], i % kSlots);
       else
         f += "  bs_commit_empty();\n";
+    appendf(f, "  uint32_t rd = base, wr = base + %d * kBsSlotStep;\n", kAhead % kSlots);
     appendf(f, "#pragma unroll 1\n  for (int i = 0; i < %d; i++) {\n", C);
-    appendf(f, "    bs_wait<%d>();\n    bs_planes(x, i %% %d, Q, R);\n", kAhead - 1, kSlots);
-    appendf(f, "    if (i + %d < %d) bs_prefetch(x, in[i + %d], (i + %d) %% %d); else bs_commit_empty();\n",
-            kAhead, C, kAhead, kAhead, kSlots);
+    appendf(f, "    bs_wait<%d>();\n    bs_planes(x, rd, Q, R);\n", kAhead - 1);
+    appendf(f, "    if (i + %d < %d) bs_prefetch(x, in[i + %d], wr); else bs_commit_empty();\n",
+            kAhead, C, kAhead);
+    f += "    rd += kBsSlotStep;\n    rd = rd == end ? base : rd;\n";
+    f += "    wr += kBsSlotStep;\n    wr = wr == end ? base : wr;\n";
     f += "    switch (i) {\n";
     for (int i = 0; i < C; i++) {
       appendf(f, "    case %d:\n", i);
@@ -140,16 +146,18 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
                 hi |= 1 << (j - 4);
             }
           }
+          // one logic instruction per (row, plane, input): acc ^ Q[lo] ^ R[hi]
           if (lo && hi) {
-            appendf(f, "      acc[%zu][%d] ^= Q[%d] ^ R[%d];\n", q, bit, lo, hi);
+            appendf(f, "      acc[%zu][%d] = bs_x3(acc[%zu][%d], Q[%d], R[%d]);\n", q, bit, q, bit,
+                    lo, hi);
             e.xors += 2;
             blk_ops[b]++;
           } else if (lo) {
-            appendf(f, "      acc[%zu][%d] ^= Q[%d];\n", q, bit, lo);
+            appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], Q[%d]);\n", q, bit, q, bit, lo);
             e.xors += 1;
             blk_ops[b]++;
           } else if (hi) {
-            appendf(f, "      acc[%zu][%d] ^= R[%d];\n", q, bit, hi);
+            appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], R[%d]);\n", q, bit, q, bit, hi);
             e.xors += 1;
             blk_ops[b]++;
           }
@@ -184,6 +192,183 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
   // transposes and subset tables, output transposes, accumulate XORs
   for (size_t b = 0; b < blks.size(); b++)
     e.cost.push_back((int)(blk_ops[b] + 100 * blks[b].inputs.size() + 70 * blks[b].rows.size()));
+  return e;
+}
+
+namespace {
+
+// dst[i] = (or ^=) the XOR of the planes src[jj] whose bit i of c * 2^jj is
+// set: output plane i of c * x, for a constant c != 0.  Terms fold into the
+// destination two at a time (3-input XOR).
+void emit_mul_planes(std::string &f, uint8_t c, const char *dst, const char *src, bool assign,
+                     const char *ind, long long &ops) {
+  for (int i = 0; i < 8; i++) {
+    std::vector<std::string> t;
+    for (int jj = 0; jj < 8; jj++)
+      if ((gf_mul_sr(c, (uint8_t)(1u << jj)) >> i) & 1)
+        t.push_back(std::string(src) + "[" + std::to_string(jj) + "]");
+    const std::string d = std::string(dst) + "[" + std::to_string(i) + "]";
+    size_t k = 0;
+    if (assign) {
+      if (t.empty()) {
+        f += ind + d + " = 0u;\n";
+        continue;
+      }
+      if (t.size() == 1) {
+        f += ind + d + " = " + t[0] + ";\n";
+        continue;
+      }
+      if (t.size() == 2) {
+        f += ind + d + " = bs_x2(" + t[0] + ", " + t[1] + ");\n";
+        ops++;
+        continue;
+      }
+      f += ind + d + " = bs_x3(" + t[0] + ", " + t[1] + ", " + t[2] + ");\n";
+      ops++;
+      k = 3;
+    }
+    for (; k < t.size(); k += 2) {
+      if (k + 1 < t.size())
+        f += ind + d + " = bs_x3(" + d + ", " + t[k] + ", " + t[k + 1] + ");\n";
+      else
+        f += ind + d + " = bs_x2(" + d + ", " + t[k] + ");\n";
+      ops++;
+    }
+  }
+}
+
+std::vector<int> nonzeros(const uint8_t *phi, int alpha) {
+  std::vector<int> nz;
+  for (int j = 0; j < alpha; j++)
+    if (phi[j]) nz.push_back(j);
+  return nz;
+}
+
+// The loop over helpers [h0, h1) of one warp task: each helper's blocks read
+// by phi (its non-zeros, in order) stream through the shared-memory ring, are
+// turned into planes and multiplied into p; `epilogue` follows each helper
+// with p holding its projection.  Input i of the task is block nz[i % NZ] of
+// helper h0 + i / NZ, prefetched kAhead inputs ahead across helpers.
+void emit_helper_loop(std::string &f, const uint8_t *phi, int alpha, const std::string &h0,
+                      const std::string &h1, const std::string &epilogue, long long &ops) {
+  const std::vector<int> nz = nonzeros(phi, alpha);
+  const int NZ = (int)nz.size();
+  f += "  const uint32_t base = bs_ring_base(), end = base + kBsSlots * kBsSlotStep;\n";
+  for (int i = 0; i < kAhead; i++)
+    appendf(f, "  if (%s + %d < %s) bs_prefetch(x, (%s + %d) * %d + %d, base + %d * kBsSlotStep); "
+               "else bs_commit_empty();\n",
+            h0.c_str(), i / NZ, h1.c_str(), h0.c_str(), i / NZ, alpha, nz[i % NZ], i % kSlots);
+  appendf(f, "  uint32_t rd = base, wr = base + %d * kBsSlotStep;\n", kAhead % kSlots);
+  appendf(f, "#pragma unroll 1\n  for (uint32_t h = %s; h < %s; h++) {\n", h0.c_str(), h1.c_str());
+  for (int jj = 0; jj < NZ; jj++) {
+    appendf(f, "    bs_wait<%d>();\n    bs_load(rd, w);\n    bs_transpose(w, *x.a);\n", kAhead - 1);
+    emit_mul_planes(f, phi[nz[jj]], "p", "w", jj == 0, "    ", ops);
+    const int t = jj + kAhead, dh = t / NZ, jn = nz[t % NZ];
+    appendf(f, "    if (h + %d < %s) bs_prefetch(x, (h + %d) * %d + %d, wr); else bs_commit_empty();\n",
+            dh, h1.c_str(), dh, alpha, jn);
+    f += "    rd += kBsSlotStep;\n    rd = rd == end ? base : rd;\n";
+    f += "    wr += kBsSlotStep;\n    wr = wr == end ? base : wr;\n";
+  }
+  f += epilogue;
+  f += "  }\n";
+}
+
+}  // namespace
+
+BsEmitted bs_emit_projection(const uint8_t *phi, int alpha, const std::string &name) {
+  BsEmitted e;
+  std::string &f = e.code;
+  appendf(f, "// %s: helper projections p_h = sum_j phi[j] Y[alpha h + j], alpha = %d\n",
+          name.c_str(), alpha);
+  appendf(f, "extern \"C\" __global__ void __launch_bounds__(kBsThreads, 1) %s(const __grid_constant__ BsArgs a) {\n",
+          name.c_str());
+  f += "  const uint32_t warps = gridDim.x * (kBsThreads / 32);\n";
+  f += "  for (uint32_t g = blockIdx.x * (kBsThreads / 32) + threadIdx.x / 32; g < a.ntasks; g += warps) {\n";
+  f += "    const uint32_t grp = g % a.ngroups, u = g / a.ngroups;\n";
+  appendf(f, "    const uint32_t h0 = grp * %d, h1 = h0 + %d < a.nh ? h0 + %d : a.nh;\n",
+          kBsHelpersPerTask, kBsHelpersPerTask, kBsHelpersPerTask);
+  f += "    BsCtx x;\n    const bool live = bs_ctx(a, x, u);\n";
+  f += "    if (!live) x.off = 0;  // lanes past the end read in-range bytes and store nothing\n";
+  f += "    uint32_t w[8], p[8];\n";
+  std::string body;
+  appendf(body, "    if (live) bs_store(x, (int)(a.nh * %d + h), p);\n", alpha);
+  std::string loop;
+  emit_helper_loop(loop, phi, alpha, "h0", "h1", body, e.xors);
+  // indent the loop one level into the task loop
+  for (size_t pos = 0; pos < loop.size();) {
+    const size_t nl = loop.find('\n', pos);
+    const std::string line = loop.substr(pos, nl - pos);
+    f += (line.rfind("#pragma", 0) == 0 ? "" : "  ") + line + "\n";
+    pos = nl + 1;
+  }
+  f += "  }\n}\n";
+  return e;
+}
+
+BsEmitted bs_emit_fused_repair(const uint8_t *phi, int alpha, const uint8_t *D, int d,
+                               const std::string &name) {
+  BsEmitted e;
+  std::string &f = e.code;
+  const int d0 = (d + 1) / 2;     // group 0: helpers [0, d0), group 1: [d0, d)
+  const int rs = (alpha + 1) / 2;  // group 0 stores rows [0, rs), group 1 rows [rs, alpha)
+  appendf(f, "// %s: fused repair, alpha = %d, d = %d\n", name.c_str(), alpha, d);
+  for (int g = 0; g < 2; g++) {
+    const int h0 = g ? d0 : 0, h1 = g ? d : d0;
+    appendf(f, "__device__ __forceinline__ void %s_g%d(const BsCtx &x, uint32_t (&acc)[%d][8]) {\n",
+            name.c_str(), g, alpha);
+    f += "  uint32_t Q[16], R[16], w[8], p[8];\n";
+    std::string epi = "    bs_tables(p, Q, R);\n    switch (h) {\n";
+    for (int q = h0; q < h1; q++) {
+      appendf(epi, "    case %d:\n", q);
+      for (int r = 0; r < alpha; r++) {
+        const uint8_t cf = D[(size_t)r * d + q];
+        if (!cf) continue;
+        for (int bit = 0; bit < 8; bit++) {
+          int lo = 0, hi = 0;  // row `bit` of M_cf, split in two nibbles
+          for (int j = 0; j < 8; j++)
+            if ((gf_mul_sr(cf, (uint8_t)(1u << j)) >> bit) & 1) {
+              if (j < 4)
+                lo |= 1 << j;
+              else
+                hi |= 1 << (j - 4);
+            }
+          if (lo && hi)
+            appendf(epi, "      acc[%d][%d] = bs_x3(acc[%d][%d], Q[%d], R[%d]);\n", r, bit, r, bit, lo, hi);
+          else if (lo)
+            appendf(epi, "      acc[%d][%d] = bs_x2(acc[%d][%d], Q[%d]);\n", r, bit, r, bit, lo);
+          else
+            appendf(epi, "      acc[%d][%d] = bs_x2(acc[%d][%d], R[%d]);\n", r, bit, r, bit, hi);
+          e.xors++;
+        }
+      }
+      epi += "      break;\n";
+    }
+    epi += "    default: break;\n    }\n";
+    emit_helper_loop(f, phi, alpha, std::to_string(h0), std::to_string(h1), epi, e.xors);
+    f += "}\n\n";
+  }
+  appendf(f, "extern \"C\" __global__ void __launch_bounds__(kBsThreads, 1) %s(const __grid_constant__ BsArgs a) {\n",
+          name.c_str());
+  f += "  extern __shared__ __align__(16) uint8_t bs_smem[];\n";
+  f += "  const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32, pair = warp / 2, grp = warp % 2;\n";
+  appendf(f, "  uint32_t *xs = reinterpret_cast<uint32_t *>(bs_smem + kBsSlots * kBsSlotStep) + pair * %d;\n",
+          alpha * 8 * 32);
+  f += "  const uint32_t pairs = gridDim.x * (kBsThreads / 64);\n";
+  f += "  for (uint32_t u = blockIdx.x * (kBsThreads / 64) + pair; u < a.ntiles; u += pairs) {\n";
+  f += "    BsCtx x;\n    const bool live = bs_ctx(a, x, u);\n";
+  f += "    if (!live) x.off = 0;  // lanes past the end read in-range bytes and store nothing\n";
+  appendf(f, "    uint32_t acc[%d][8];\n#pragma unroll\n    for (int r = 0; r < %d; r++)\n#pragma unroll\n"
+             "      for (int i = 0; i < 8; i++) acc[r][i] = 0;\n", alpha, alpha);
+  appendf(f, "    if (grp == 0) %s_g0(x, acc); else %s_g1(x, acc);\n", name.c_str(), name.c_str());
+  f += "    // each warp hands the other the partial sums of the rows that warp stores\n";
+  appendf(f, "#pragma unroll\n    for (int r = 0; r < %d; r++)\n      if ((r < %d) != (grp == 0))\n#pragma unroll\n"
+             "        for (int i = 0; i < 8; i++) xs[(r * 8 + i) * 32 + lane] = acc[r][i];\n", alpha, rs);
+  f += "    bs_pair_sync(pair);\n";
+  appendf(f, "#pragma unroll\n    for (int r = 0; r < %d; r++)\n      if ((r < %d) == (grp == 0)) {\n#pragma unroll\n"
+             "        for (int i = 0; i < 8; i++) acc[r][i] = bs_x2(acc[r][i], xs[(r * 8 + i) * 32 + lane]);\n"
+             "        if (live) bs_store(x, (int)(a.nh * %d + r), acc[r]);\n      }\n", alpha, rs, alpha);
+  f += "    bs_pair_sync(pair);  // the exchange area is reused by the next tile\n";
+  f += "  }\n}\n";
   return e;
 }
 

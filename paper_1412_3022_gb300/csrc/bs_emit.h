@@ -55,4 +55,28 @@ struct BsEmitted {
 BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
                          const std::string &name, bool extern_c);
 
+// Repair schedules, emitted at run time for one failed node's helper
+// coefficients phi (alpha entries, the projection each helper applies to its
+// alpha blocks, Sec. 2/3.3) and, for the fused kernel, the newcomer matrix D
+// (alpha x d, row-major).  Each helper block that phi reads is turned into
+// bit planes once and multiplied by its constant phi[j] as plain XORs of
+// planes (output plane i of c*x is the XOR of the input planes jj with bit i
+// of c*2^jj set); no subset tables are needed for a single row.
+//
+// Projection kernel: warp task = (1 KiB column tile, group of
+// kBsHelpersPerTask helpers); helper h's blocks at pointer slots
+// [h*alpha, h*alpha + alpha), its projection to slot nh*alpha + h.
+//
+// Fused repair kernel (alpha <= 8): the two warps of a pair take the same
+// tile, each the projections of half the helpers, which stay in registers
+// and go straight into the newcomer's apply (subset tables of the
+// projection, one 3-input XOR per output plane); the two partial sums are
+// combined through shared memory.  Output row r goes to slot d*alpha + r.
+constexpr int kBsHelpersPerTask = 2;
+constexpr int kBsFusedMaxAlpha = 8;
+
+BsEmitted bs_emit_projection(const uint8_t *phi, int alpha, const std::string &name);
+BsEmitted bs_emit_fused_repair(const uint8_t *phi, int alpha, const uint8_t *D, int d,
+                               const std::string &name);
+
 }  // namespace pmrc

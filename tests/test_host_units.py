@@ -64,7 +64,8 @@ def _evaluate_schedule(text, cols, X):
                  for s in range(16)]
             R = [np.bitwise_xor.reduce([p[4 + j] for j in range(4) if s >> j & 1] or [np.zeros(T, np.uint8)])
                  for s in range(16)]
-            for q, bit, terms in re.findall(r"acc\[(\d+)\]\[(\d+)\] \^= ([^;]*);", case):
+            for q, bit, terms in re.findall(
+                    r"acc\[(\d+)\]\[(\d+)\] = bs_x[23]\(acc\[\1\]\[\2\], ([^;]*)\);", case):
                 for name, idx in re.findall(r"([QR])\[(\d+)\]", terms):
                     acc[int(q), int(bit)] ^= (Q if name == "Q" else R)[int(idx)]
         kernel_case = re.search(r"case %d: \{\s*k_b%d\(x, acc\);(.*?)\} break;" % (b, b), text, re.S)
@@ -106,6 +107,140 @@ def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed):
             if M[row, c]:
                 want ^= np.array([_gf_mul(int(M[row, c]), int(x)) for x in X[c]], np.uint8)
         assert np.array_equal(got[row], want), row
+
+
+def _run_statements(env, lines):
+    """Executes emitted assignments (x = y; x = 0u; x = bs_x2(a, b);
+    x = bs_x3(a, b, c);) on integer bit vectors."""
+    import re
+    for ln in lines:
+        m = re.match(r"\s*([\w\[\]]+) = (.*);$", ln)
+        if not m or "(" in m.group(1):
+            continue
+        lhs, rhs = m.groups()
+        if rhs == "0u":
+            env[lhs] = 0
+        elif rhs.startswith("bs_x"):
+            v = 0
+            for name in rhs[rhs.index("(") + 1:-1].split(", "):
+                v ^= env[name]
+            env[lhs] = v
+        elif re.fullmatch(r"[\w\[\]]+", rhs):
+            env[lhs] = env[rhs]
+
+
+def _planes(block):
+    """Bit planes of a byte block as integers (bit t = bit j of byte t)."""
+    return [sum(((int(x) >> j) & 1) << t for t, x in enumerate(block)) for j in range(8)]
+
+
+def _bytes(planes, T):
+    import numpy as np
+    return np.array([sum(((planes[i] >> t) & 1) << i for i in range(8)) for t in range(T)], np.uint8)
+
+
+def _helper_sections(body):
+    """Splits a helper-loop body into the per-input sections (each starts at
+    bs_load) and the statements after the last one (the epilogue)."""
+    secs, cur, pre = [], None, []
+    for ln in body.splitlines():
+        if "bs_load(rd, w)" in ln:
+            cur = []
+            secs.append(cur)
+        elif cur is not None:
+            cur.append(ln)
+        else:
+            pre.append(ln)
+    return secs
+
+
+@pytest.mark.parametrize("alpha,d,seed,zeros,single", [(7, 14, 1, 1, None), (7, 14, 2, 0, None),
+                                                        (3, 4, 3, 1, None), (8, 16, 4, 1, None),
+                                                        (7, 14, 5, 0, 3), (1, 8, 6, 0, None),
+                                                        (2, 5, 7, 1, None)])
+def test_repair_schedules_compute_projection_and_newcomer(alpha, d, seed, zeros, single):
+    """The run-time repair schedules, evaluated on the CPU: the projection
+    kernel's helper loop gives sum_j phi[j] Y_hj, and the fused kernel's two
+    helper groups, tables and per-helper newcomer terms give D applied to the
+    projections (independent GF(2^8) multiply)."""
+    import re
+    import numpy as np
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("g++ not found")
+    exe = os.path.join(ROOT, "_build", "test_emit_repair_dump")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", exe,
+                        os.path.join(ROOT, "tests", "host", "emit_repair_dump.cpp"),
+                        os.path.join(CSRC, "bs_emit.cpp")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    args = [exe, str(alpha), str(d), str(seed), str(zeros)] + ([str(single)] if single is not None else [])
+    out = subprocess.run(args, capture_output=True, text=True, timeout=60).stdout
+    head, rest = out.split("PROJ\n", 1)
+    proj, fused = rest.split("FUSED\n", 1)
+    lines = head.strip().splitlines()
+    phi = [int(v) for v in lines[0].split()[1:]]
+    D = np.array([[int(v) for v in ln.split()] for ln in lines[2:2 + alpha]], np.uint8)
+    nz = [j for j in range(alpha) if phi[j]]
+    T = 48
+    Y = np.random.default_rng(seed).integers(0, 256, (d, alpha, T), dtype=np.uint8)
+
+    def gfvec(c, v):
+        return np.array([_gf_mul(int(c), int(x)) for x in v], np.uint8)
+
+    want_p = []
+    for h in range(d):
+        acc = np.zeros(T, np.uint8)
+        for j in nz:
+            acc ^= gfvec(phi[j], Y[h, j])
+        want_p.append(acc)
+
+    def projection_of(body, h):
+        env = {}
+        for jj, sec in enumerate(_helper_sections(body)):
+            for i, pl in enumerate(_planes(Y[h, nz[jj]])):
+                env["w[%d]" % i] = pl
+            _run_statements(env, sec)
+        return env
+
+    # projection kernel: one loop body, run per helper
+    body = proj[proj.index("for (uint32_t h = h0; h < h1; h++) {"):]
+    assert len(_helper_sections(body)) == len(nz)
+    for h in range(d):
+        env = projection_of(body, h)
+        assert np.array_equal(_bytes([env["p[%d]" % i] for i in range(8)], T), want_p[h]), h
+    # fused kernel: both helper groups, tables of the projection, D terms
+    acc = {}
+    for g in (0, 1):
+        fn = fused[fused.index("void kf_g%d(" % g):]
+        fn = fn[:fn.index("\n}\n")]
+        h0, h1 = map(int, re.search(r"for \(uint32_t h = (\d+); h < (\d+); h\+\+\)", fn).groups())
+        loop = fn[fn.index("h++) {"):]
+        head_part, cases = loop.split("bs_tables(p, Q, R);", 1)
+        for h in range(h0, h1):
+            env = projection_of(head_part, h)
+            p = [env["p[%d]" % i] for i in range(8)]
+            for s in range(16):
+                env["Q[%d]" % s] = 0
+                env["R[%d]" % s] = 0
+                for i in range(4):
+                    if s >> i & 1:
+                        env["Q[%d]" % s] ^= p[i]
+                        env["R[%d]" % s] ^= p[4 + i]
+            for key, v in acc.items():
+                env[key] = v
+            for r_ in range(alpha):
+                for i in range(8):
+                    env.setdefault("acc[%d][%d]" % (r_, i), 0)
+            m = re.search(r"case %d:(.*?)break;" % h, cases, re.S)
+            _run_statements(env, m.group(1).splitlines() if m else [])
+            acc = {k: v for k, v in env.items() if k.startswith("acc[")}
+    for r_ in range(alpha):
+        want = np.zeros(T, np.uint8)
+        for q in range(d):
+            want ^= gfvec(D[r_, q], want_p[q])
+        got = _bytes([acc.get("acc[%d][%d]" % (r_, i), 0) for i in range(8)], T)
+        assert np.array_equal(got, want), r_
 
 
 def test_kernel_cache_on_disk():
