@@ -14,7 +14,8 @@ uniform random bytes.  One step runs every operation of the hot path once:
 
 Throughput is user data / time (the paper's Sec. 4 definition: k*alpha
 blocks for encode and decode, alpha blocks for repair), GB = 1e9 B.  L2 is
-flushed (512 MiB write) before every operation, outside the timed events.
+flushed before every operation, outside the timed events (a 512 MiB write,
+then a 512 MiB read sweep so the lines left in L2 are clean).
 Each operation is timed with CUDA events on the launch stream.
 
 --impl reference times the CPU oracle (plain C, one core) on a bounded
@@ -127,8 +128,11 @@ def parse():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the rows outside the step (fused repair, specific algorithms, "
                         "PM-MBR, Reed-Solomon), e.g. for a launch list of the step alone")
-    p.add_argument("--serve-requests", type=int, default=400,
+    p.add_argument("--serve-requests", type=int, default=10000,
                    help="requests per offered-load level")
+    p.add_argument("--cfg1-reps", type=int, default=2000,
+                   help="timed calls per operation of the n=6 k=3 4 KiB latency section")
+    p.add_argument("--no-cfg1", action="store_true")
     return p.parse_args()
 
 
@@ -182,6 +186,27 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ peaks
+class L2Flush:
+    """Evicts the timed operation's data from L2 before each timed call: a
+    512 MiB write (larger than the 126 MB L2), then a read sweep of another
+    512 MiB buffer (one 4-byte load per 128-byte line, gathered into a small
+    buffer) so that the lines left in L2 are clean and the next call does
+    not pay for writing the flush's dirty lines back.  Both are single
+    kernels queued ahead of the timed call (no idle gap before it)."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        self.r = torch.ones(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        self.g = torch.empty(FLUSH_BYTES // 128, dtype=torch.int32, device=dev)
+
+    def __call__(self, v=7):
+        self.w.fill_(v)
+        self.g.copy_(self.r.view(-1, 32)[:, 0])
+
+    def fill_(self, v):  # the call sites' former flush.fill_(v)
+        self(v)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -310,7 +335,7 @@ def run_ours(args, rank, world, local_rank):
     B = args.block_bytes
     W = Workload(torch, P, inputs, B, rank_seed(args.seed, rank), dev)
     ops = W.ops()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush = L2Flush(torch, dev)
     stream = torch.cuda.current_stream()
     names = [n for n, _ in ops]
     ev = {n: [] for n in names}
@@ -437,6 +462,7 @@ def run_ours(args, rank, world, local_rank):
     ksweep = None if (args.no_sweep or args.no_extra) else run_ksweep(torch, P, inputs, args, flush,
                                                                       stream, dev)
     init = None if args.no_extra else run_init(torch, P, inputs, args, dev)
+    cfg1 = None if args.no_cfg1 else run_cfg1(torch, P, inputs, args, dev, stream)
     batched = None if args.no_batched else run_batched(torch, P, inputs, args, dev, stream)
     serving = None if args.no_serving else run_serving(torch, P, inputs, args)
     result = {
@@ -446,8 +472,8 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded uniform random bytes, generated on device)",
         "config": {"workload": WORKLOAD, "block_bytes": B, "stripe_bytes": K_ * A_ * B,
-                   "user_bytes_per_step": user_step, "l2": "flushed before every op "
-                   "(512 MiB write, outside the timed events)",
+                   "user_bytes_per_step": user_step, "l2": "flushed before every op, outside the timed events: "
+                   "512 MiB write, then a 512 MiB read sweep (clean lines left in L2)",
                    "parallelism": f"replicas x{world} (independent stripes, no collective)"},
         "roofline": roofline,
         "per_op": per_op,
@@ -464,6 +490,8 @@ def run_ours(args, rank, world, local_rank):
         result["k_sweep"] = ksweep
     if init:
         result["init"] = init
+    if cfg1:
+        result["cfg1_latency"] = cfg1
     if degraded:
         result["degraded_read"] = degraded
     if batched:
@@ -475,6 +503,73 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def run_cfg1(torch, P, inputs, args, dev, stream):
+    """The n=6, k=3, d=4 code of the small configuration: vanilla generator
+    (non-systematic) encode of 6 data blocks of 4 KiB into 12, repair of node
+    0 from helpers {1, 2, 3, 4} (projections + newcomer, and fused), and
+    reconstruction from nodes {1, 2, 3}.  Latency-bound: each call is timed
+    on its own over `args.cfg1_reps` repetitions, as device time between CUDA
+    events around the call and as host time from the call to its completion
+    (synchronized); p50 / p99 of both.  Results are checked on the device
+    against the stored codeword and the data."""
+    n, k, a, B = 6, 3, 2, 4096
+    c = P.Code(n, k, P.PMRC_VANILLA, P.PMRC_NONSYSTEMATIC)
+    X = inputs.device_blocks(k * a, B, args.seed + 11, device=dev)
+    Y = torch.empty((n * a, B), dtype=torch.uint8, device=dev)
+    f, H, S = 0, [1, 2, 3, 4], [1, 2, 3]
+    recv = torch.empty((len(H), B), dtype=torch.uint8, device=dev)
+    node = torch.empty((a, B), dtype=torch.uint8, device=dev)
+    fused = torch.empty((a, B), dtype=torch.uint8, device=dev)
+    Xd = torch.empty_like(X)
+    st = int(stream.cuda_stream)
+    x_p = P.ptr_array([X[i] for i in range(k * a)])
+    y_p = P.ptr_array([Y[i] for i in range(n * a)])
+    hb = P.ptr_array([Y[a * h + j] for h in H for j in range(a)])
+    r_p = P.ptr_array([recv[i] for i in range(len(H))])
+    n_p = P.ptr_array([node[j] for j in range(a)])
+    f_p = P.ptr_array([fused[j] for j in range(a)])
+    d_in = P.ptr_array([Y[a * i + j] for i in S for j in range(a)])
+    d_out = P.ptr_array([Xd[r] for r in range(k * a)])
+    cH, cS = P.int_array(H), P.int_array(S)
+    ops = {
+        "encode": lambda: c.encode(x_p, y_p, B, st),
+        "repair": lambda: (c.repair_helpers(f, cH, hb, r_p, B, st),
+                           c.repair_newcomer(f, cH, r_p, n_p, B, st)),
+        "repair_fused": lambda: c.repair(f, cH, hb, f_p, B, st),
+        "decode": lambda: c.decode(cS, d_in, d_out, B, st),
+    }
+    out = {"workload": "PM-MSR n=6 k=3 d=4 alpha=2, vanilla generator form, 4 KiB blocks: "
+                       "encode 6 -> 12 blocks, repair of node 0 from {1,2,3,4}, "
+                       "reconstruction from {1,2,3}",
+           "reps": args.cfg1_reps}
+    for name, fn in ops.items():
+        for _ in range(20):
+            fn()
+        torch.cuda.synchronize()
+        dev_ms, host_ms = [], []
+        for _ in range(args.cfg1_reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            host_ms.append((time.perf_counter() - t0) * 1e3)
+            dev_ms.append(e0.elapsed_time(e1))
+        dev_ms.sort()
+        host_ms.sort()
+        q = lambda v, p: v[min(len(v) - 1, int(p * len(v)))]
+        user = (k * a if name in ("encode", "decode") else a) * B
+        out[name] = {"device_p50_ms": round(q(dev_ms, 0.5), 4), "device_p99_ms": round(q(dev_ms, 0.99), 4),
+                     "host_p50_ms": round(q(host_ms, 0.5), 4), "host_p99_ms": round(q(host_ms, 0.99), 4),
+                     "user_GBps_p50": round(user / (q(dev_ms, 0.5) * 1e-3) / 1e9, 3)}
+    torch.cuda.synchronize()
+    out["checked"] = bool(torch.equal(node, Y[a * f:a * f + a]) and torch.equal(fused, node)
+                          and torch.equal(Xd, X))
+    return out
 
 
 def run_sweep(torch, P, inputs, args, flush, stream, dev, hbm):
@@ -871,17 +966,20 @@ def run_batched(torch, P, inputs, args, dev, stream):
         if m["op"] == "encode":
             ins = [base + off + i * nb for i in range(k * a)]
             outs = [base + off + (k * a + i) * nb for i in range(k * a)]
+            span = (off + k * a * nb, k * a * nb)
             off += 2 * k * a * nb
-            ops.append(("encode", c, ins, outs, nb, m))
+            ops.append(("encode", c, ins, outs, nb, dict(m, span=span, alg=2 * k * a * nb)))
         else:
             Y = [base + off + i * nb for i in range(2 * k * a)]
             outs = [base + off + (2 * k * a + j) * nb for j in range(a)]
+            span = (off + 2 * k * a * nb, a * nb)
             off += (2 * k * a + a) * nb
             c.encode(Y[:k * a], Y[k * a:], nb)  # stored codeword
             f = m["failed"]
             H = c.default_helpers(f)
+            reads = int((c.helper_coefficients(f) != 0).sum())
             ops.append(("repair", c, [Y[a * h + j] for h in H for j in range(a)], outs, nb,
-                        dict(m, H=H)))
+                        dict(m, H=H, span=span, alg=(len(H) * reads + a) * nb)))
     torch.cuda.synchronize()
     user = sum((m["k"] * (m["k"] - 1) if op == "encode" else m["k"] - 1) * m["block_bytes"]
                for op, _, _, _, _, m in ops)
@@ -920,9 +1018,32 @@ def run_batched(torch, P, inputs, args, dev, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         res[name] = (e0.elapsed_time(e1) / reps, (time.perf_counter() - t0) * 1e3 / reps)
+    # every stripe of the batched launch equals the same stripe run through
+    # the plain call (compared on the device, one stripe at a time)
+    b.launch(stream)
+    torch.cuda.synchronize()
+    mismatches = 0
+    scratch = torch.empty(max(m["span"][1] for _, _, _, _, _, m in ops), dtype=torch.uint8,
+                          device=dev)
+    for op, c, ins, outs, nb, m in ops:
+        o, ln = m["span"]
+        view = arena[o:o + ln]
+        scratch[:ln].copy_(view)
+        if op == "encode":
+            c.encode(ins, outs, nb, stream)
+        else:
+            c.repair(m["failed"], m["H"], ins, outs, nb, stream)
+        mismatches += int(not torch.equal(scratch[:ln], view))
+    del scratch
+    alg = sum(m["alg"] for _, _, _, _, _, m in ops)
+    hbm, peak_src = measured_peaks()
     out = {
         "workload": f"{len(ops)} stripes, k uniform on {{4,8,16}} (n=2k, sparse systematic), "
                     "block sizes log-uniform 4 KiB-1 MiB, 50% encode / 50% fused repair",
+        "checked": mismatches == 0, "stripes_differing_from_plain_calls": mismatches,
+        "alg_GB": round(alg / 1e9, 3),
+        "batched_frac_hbm": round(alg / (res["batched"][0] * 1e-3) / 1e9 / hbm, 4),
+        "plain_frac_hbm": round(alg / (res["plain"][0] * 1e-3) / 1e9 / hbm, 4),
         "user_GB": round(user / 1e9, 3),
         "batched_GBps": round(user / (res["batched"][0] * 1e-3) / 1e9, 1),
         "batched_ms": round(res["batched"][0], 3),
@@ -948,9 +1069,21 @@ def run_serving(torch, P, inputs, args):
     systematic), stripes log-uniform on [64 KiB, 64 MiB] split into k*alpha
     blocks (the last one zero-padded), host buffers pinned.  First the
     saturated rate (all requests submitted at once), then offered loads of
-    25/50/75/90% of it; latency is submit to completion seen by the host."""
+    25/50/75/90% of it; latency is submit (arrival) to completion seen by
+    the host.  Three arms on the same requests and arrival times:
+
+      served          the continuous-batching server, host buffers (inputs
+                      copied in, results copied out, per request);
+      device_resident the same server with every request's blocks already in
+                      device memory (PMRC_REQ_DEVICE: no copies), at
+                      saturation: the GPU side of continuous batching;
+      plain           one request at a time through the single-stripe calls
+                      in arrival order (copy in, call, copy out, wait), on one
+                      stream: the per-stripe launches without batching."""
     import numpy as np
-    reqs_all = inputs.serve_requests(args.serve_requests * 5, seed=args.seed + 6)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.serve_requests
+    reqs_all = inputs.serve_requests(n * 5, seed=args.seed + 6)
     codes = {k: P.Code(2 * k, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC) for k in (4, 8, 12, 16)}
 
     def sizes(q):
@@ -969,63 +1102,138 @@ def run_serving(torch, P, inputs, args):
     g.manual_seed(args.seed + 7)
     hin = torch.randint(0, 256, (max_in,), dtype=torch.uint8, generator=g).pin_memory()
     hout = torch.empty(max_out, dtype=torch.uint8).pin_memory()
+    din = torch.empty(max_in, dtype=torch.uint8, device=dev)
+    din.copy_(hin)
+    dout = torch.empty(max_out, dtype=torch.uint8, device=dev)
     helpers = {}
     for k, c in codes.items():
         for f in range(2 * k):
             helpers[(k, f)] = c.default_helpers(f)
-    srv = P.Server(budget_bytes=16 << 30, max_slots=64)
+    budget = 16 << 30
+    srv = P.Server(budget_bytes=budget, max_slots=64)
     opcode = {"encode": P.PMRC_OP_ENCODE, "repair": P.PMRC_OP_REPAIR,
               "decode": P.PMRC_OP_DECODE}
 
-    def submit(q):
+    def submit(q, device):
         k = q["k"]
-        return srv.submit(opcode[q["op"]], codes[k], q["block_bytes"], hin, hout,
-                          failed=q["failed"], helpers=helpers[(k, q["failed"])],
-                          nodes=q["nodes"])
+        op = opcode[q["op"]] | (P.PMRC_REQ_DEVICE if device else 0)
+        return srv.submit(op, codes[k], q["block_bytes"], din if device else hin,
+                          dout if device else hout, failed=q["failed"],
+                          helpers=helpers[(k, q["failed"])], nodes=q["nodes"])
 
-    def run(batch, rate):
+    def arrivals(batch, rate):
+        rng = np.random.default_rng(args.seed + 8)
+        t, out = 0.0, []
+        for _ in batch:
+            if rate:
+                t += rng.exponential(1.0 / rate)
+            out.append(t)
+        return out
+
+    def summary(batch, lats, wall):
+        user = sum(sizes(q)[2] for q in batch)
+        lat = np.array(lats)
+        ub = np.array([sizes(q)[2] for q in batch])
+        by_size = {}
+        for name, lo, hi in (("<1MiB", 0, 1 << 20), ("1-8MiB", 1 << 20, 8 << 20),
+                             (">8MiB", 8 << 20, 1 << 62)):
+            m = (ub >= lo) & (ub < hi)
+            if m.any():
+                by_size[name] = {"requests": int(m.sum()),
+                                 "p50_ms": round(float(np.percentile(lat[m], 50)), 3),
+                                 "p99_ms": round(float(np.percentile(lat[m], 99)), 3)}
+        return {"requests": len(batch), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "max_ms": round(float(lat.max()), 3), "GBps": round(user / wall / 1e9, 2),
+                "by_size": by_size}
+
+    def run(batch, rate, device=False):
         srv.reset_stats()
         ids = []
+        when = arrivals(batch, rate)
         t0 = time.perf_counter()
-        tq = 0.0
-        rng = np.random.default_rng(args.seed + 8)
-        for q in batch:
-            if rate:
-                tq += rng.exponential(1.0 / rate)
-                dt = t0 + tq - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-            ids.append(submit(q))
-        lost = 0
+        for q, tq in zip(batch, when):
+            dt = t0 + tq - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(submit(q, device))
+        lats, lost = [], 0
         for rid in ids:
             try:
-                srv.wait(rid, timeout_ms=60000)
+                lats.append(srv.wait(rid, timeout_ms=120000)[1])
             except P.PMRCError:
                 lost += 1
         wall = time.perf_counter() - t0
         st = srv.stats()
         if lost or st["failed"]:
             raise RuntimeError(f"serving: {lost} requests timed out, {int(st['failed'])} failed")
-        user = sum(sizes(q)[2] for q in batch)
-        return {"requests": len(batch), "p50_ms": round(st["p50_ms"], 3),
-                "p99_ms": round(st["p99_ms"], 3), "max_ms": round(st["max_ms"], 3),
-                "GBps": round(user / wall / 1e9, 2), "iterations": int(st["iterations"]),
-                "peak_GB": round(st["peak_bytes"] / 1e9, 2)}
+        out = summary(batch, lats, wall)
+        out.update({"iterations": int(st["iterations"]), "peak_GB": round(st["peak_bytes"] / 1e9, 2)})
+        return out
 
-    n = args.serve_requests
-    run(reqs_all[:min(32, n)], 0)  # warm-up: plans, pools
+    stream = torch.cuda.Stream(device=dev)
+    st_handle = int(stream.cuda_stream)
+
+    def plain_call(q):
+        k, B = q["k"], q["block_bytes"]
+        a = k - 1
+        c = codes[k]
+        nin, nout = sizes(q)[0] // B, sizes(q)[1] // B
+        ib, ob = din.data_ptr(), dout.data_ptr()
+        ins = P.ptr_array([ib + i * B for i in range(nin)])
+        outs = P.ptr_array([ob + j * B for j in range(nout)])
+        with torch.cuda.stream(stream):
+            din[:nin * B].copy_(hin[:nin * B], non_blocking=True)
+        if q["op"] == "encode":
+            c.encode(ins, outs, B, st_handle)
+        elif q["op"] == "repair":
+            c.repair(q["failed"], helpers[(k, q["failed"])], ins, outs, B, st_handle)
+        else:
+            c.decode(q["nodes"], ins, outs, B, st_handle)
+        with torch.cuda.stream(stream):
+            hout[:nout * B].copy_(dout[:nout * B], non_blocking=True)
+        stream.synchronize()
+        del a
+
+    def run_plain(batch, rate):
+        when = arrivals(batch, rate)
+        lats = []
+        t0 = time.perf_counter()
+        for q, tq in zip(batch, when):
+            dt = t0 + tq - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            plain_call(q)
+            lats.append((time.perf_counter() - t0 - tq) * 1e3)
+        return summary(batch, lats, time.perf_counter() - t0)
+
+    warm = reqs_all[:min(64, n)]
+    run(warm, 0)             # plans, pools, kernels
+    run(warm, 0, device=True)
+    for q in warm:
+        plain_call(q)
+    P.wait_kernels()
     sat = run(reqs_all[:n], 0)
     mean_user = sum(sizes(q)[2] for q in reqs_all[:n]) / n
     out = {"workload": "Poisson arrivals; encode/repair/reconstruct 60/25/15; k in {4,8,12,16} "
                        "(n=2k, sparse systematic); stripes log-uniform 64 KiB-64 MiB; pinned "
                        "host buffers; HBM budget 16 GiB, 64 slots",
-           "saturated": sat, "loads": {}}
+           "requests_per_level": n,
+           "saturated": sat, "loads": {},
+           "device_resident": {"saturated": run(reqs_all[:n], 0, device=True)},
+           "plain": {"saturated": run_plain(reqs_all[:n], 0), "loads": {}}}
     for i, load in enumerate((0.25, 0.5, 0.75, 0.9)):
         rate = load * sat["GBps"] * 1e9 / mean_user
         batch = reqs_all[(i + 1) * n:(i + 2) * n]
         r = run(batch, rate)
         r["offered_GBps"] = round(load * sat["GBps"], 2)
         out["loads"][f"{int(load * 100)}%"] = r
+        rp = run_plain(batch, rate)
+        rp["offered_GBps"] = r["offered_GBps"]
+        out["plain"]["loads"][f"{int(load * 100)}%"] = rp
+    out["served_over_plain_saturated"] = round(sat["GBps"] / out["plain"]["saturated"]["GBps"], 3)
+    out["device_resident_over_host_saturated"] = round(
+        out["device_resident"]["saturated"]["GBps"] / sat["GBps"], 3)
     srv.close()
     del np
     return out
@@ -1194,47 +1402,104 @@ def calibrate_cols(seconds, seed):
     return max(4096, min(want // 4096 * 4096, 1 << 20))
 
 
+def host_cores():
+    """Threads this process may run on, and the host CPU's model name."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+            for ln in r.stdout.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return max(1, int(cores or 1)), model or "unknown"
+
+
+def oracle_parallel_step(O, parts, pool):
+    """One step of the oracle over column slices of the stripe, one slice per
+    thread (the oracle's calls release the interpreter lock); returns the
+    wall time."""
+    t0 = time.perf_counter()
+    list(pool.map(lambda pt: oracle_step(O, *pt), parts))
+    return time.perf_counter() - t0
+
+
+def oracle_parts(cols, threads, seed):
+    """`threads` independent column slices of `cols` bytes each (the same
+    code, failed node, helpers and node subset), for the all-cores oracle."""
+    O, X, Y, f, H, S = oracle_sample(cols * threads, seed)
+    parts = []
+    for t in range(threads):
+        cs = slice(t * cols, (t + 1) * cols)
+        parts.append((np.ascontiguousarray(X[:, cs]), np.ascontiguousarray(Y[:, cs]), f, H, S))
+    return O, parts
+
+
 def cpu_baseline(args, W, torch):
+    """The oracle on the host cores: one thread, and every core this process
+    may use (a thread per column slice), on a bounded sample of the stripe."""
+    import concurrent.futures as cf
     seed = args.seed
-    cols = calibrate_cols(args.cpu_seconds, seed)
+    cores, model = host_cores()
+    cols = calibrate_cols(args.cpu_seconds / 2, seed)
     O, X, Y, f, H, S = oracle_sample(cols, seed)
     t0 = time.perf_counter()
     oracle_step(O, X, Y, f, H, S)
-    dt = time.perf_counter() - t0
-    user = (2 * K_ * A_ + A_ + K_ * A_) * cols
-    return {"value": round(user / dt / 1e9, 5), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "seconds": round(dt, 2),
-            "sample": f"one step (all four operations) on {cols}-byte column slices of the "
-                      f"n=16 k=8 stripe (56 blocks x {cols} B), plain C oracle, one thread"}
+    dt1 = time.perf_counter() - t0
+    user1 = (2 * K_ * A_ + A_ + K_ * A_) * cols
+    one = {"value": round(user1 / dt1 / 1e9, 5), "seconds": round(dt1, 2), "cols": cols}
+    O, parts = oracle_parts(cols, cores, seed)
+    with cf.ThreadPoolExecutor(cores) as pool:
+        dtn = oracle_parallel_step(O, parts, pool)
+    usern = user1 * cores
+    return {"value": round(usern / dtn / 1e9, 5), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "cpu_model": model, "seconds": round(dtn, 2),
+            "sample": f"one step (all four operations) on {cores} column slices of {cols} bytes of "
+                      f"the n=16 k=8 stripe (56 blocks each), plain C oracle, one thread per slice",
+            "one_thread": one,
+            "parallel_efficiency": round((usern / dtn) / (user1 / dt1) / cores, 3)}
 
 
 def run_reference(args, rank):
+    """The oracle as it stands on every host core this process may use, a
+    bounded sample of the stripe per step."""
     if rank != 0:
         return None
+    import concurrent.futures as cf
+    cores, model = host_cores()
     # size each step so that warmup+steps stay within a few minutes
     budget = 150.0 / max(1, args.steps + args.warmup)
     cols = calibrate_cols(min(budget, args.ref_seconds), args.seed)
-    O, X, Y, f, H, S = oracle_sample(cols, args.seed)
-    for _ in range(args.warmup):
-        oracle_step(O, X, Y, f, H, S)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(O, X, Y, f, H, S)
-        times.append(time.perf_counter() - t0)
+    O, parts = oracle_parts(cols, cores, args.seed)
+    with cf.ThreadPoolExecutor(cores) as pool:
+        for _ in range(args.warmup):
+            oracle_parallel_step(O, parts, pool)
+        times = [oracle_parallel_step(O, parts, pool) for _ in range(args.steps)]
     dt = sum(times) / len(times)
-    user = (2 * K_ * A_ + A_ + K_ * A_) * cols
+    user = (2 * K_ * A_ + A_ + K_ * A_) * cols * cores
     value = round(user / dt / 1e9, 5)
-    sample = (f"each step: all four operations on {cols}-byte column slices of the n=16 k=8 "
-              f"stripe, plain C oracle, one thread")
+    sample = (f"each step: all four operations on {cores} column slices of {cols} bytes of the "
+              f"n=16 k=8 stripe, plain C oracle, one thread per slice")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD + f" (oracle on {cols}-byte column slices)",
+            "config": {"workload": WORKLOAD + f" (oracle on {cores} x {cols}-byte column slices)",
                        "block_bytes": cols},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": model, "sample": sample},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -383,12 +383,21 @@ int pmrc_batch_info(const pmrc_batch *batch, int64_t *info_out);
  * the previous iteration computes, runs every request whose inputs have
  * landed in one persistent launch (the batched kernel), and copies results
  * back, recording submit-to-completion latency.  Each request gives the same
- * bytes as the corresponding single call.  Requests use HOST buffers; make
- * them pinned (cudaMallocHost / cudaHostRegister) so the copies run
- * asynchronously, and keep them alive until the request is finished. */
+ * bytes as the corresponding single call.  Requests use HOST buffers (make
+ * them pinned, cudaMallocHost / cudaHostRegister, so the copies run
+ * asynchronously, and keep them alive until the request is finished), or
+ * device blocks with PMRC_REQ_DEVICE. */
 typedef struct pmrc_server pmrc_server;
 
 enum { PMRC_OP_ENCODE = 0, PMRC_OP_REPAIR = 1, PMRC_OP_DECODE = 2 };
+
+/* OR'ed into pmrc_request.op: `in` and `out` are DEVICE blocks of the
+ * server's device (the same layout as the host buffers below, 16-byte
+ * aligned, B a multiple of 16), owned by the caller and alive until the
+ * request is finished.  The request takes a slot but no arena space, its
+ * blocks are neither copied in nor out, and the batched kernel reads and
+ * writes them in place: stripe state kept resident in HBM. */
+enum { PMRC_REQ_DEVICE = 0x100 };
 
 typedef struct {
   int op;                 /* PMRC_OP_*                                          */

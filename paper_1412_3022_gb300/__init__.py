@@ -37,6 +37,7 @@ PMRC_KERNEL_BITSLICED = 2
 PMRC_OP_ENCODE = 0
 PMRC_OP_REPAIR = 1
 PMRC_OP_DECODE = 2
+PMRC_REQ_DEVICE = 0x100   # OR'ed into op: in/out are device blocks, used in place
 
 PMRC_VANILLA = 0
 PMRC_SPARSE = 1

@@ -99,6 +99,7 @@ struct Req {
   size_t B = 0;
   const uint8_t *in = nullptr;
   uint8_t *out = nullptr;
+  bool device = false;  // in/out are the caller's device blocks (no arena, no copies)
   int failed = -1;
   std::vector<int> helpers, nodes;
   size_t in_bytes = 0, out_bytes = 0, nin = 0, nout = 0;
@@ -171,14 +172,16 @@ void forget(pmrc_server *s, std::map<uint64_t, std::unique_ptr<Req>>::iterator i
   s->reqs.erase(it);
 }
 
-// Device pointers of a request's blocks inside the arena.
+// Device pointers of a request's blocks: inside the arena, or the caller's
+// device blocks for a device-resident request.
 void block_ptrs(pmrc_server *s, Req *r, std::vector<const uint8_t *> &in,
                 std::vector<uint8_t *> &out) {
-  uint8_t *base = s->arena_base + r->off;
+  const uint8_t *ib = r->device ? r->in : s->arena_base + r->off;
+  uint8_t *ob = r->device ? r->out : s->arena_base + r->off + r->in_span;
   in.resize(r->nin);
   out.resize(r->nout);
-  for (size_t i = 0; i < r->nin; i++) in[i] = base + i * r->B;
-  for (size_t j = 0; j < r->nout; j++) out[j] = base + r->in_span + j * r->B;
+  for (size_t i = 0; i < r->nin; i++) in[i] = ib + i * r->B;
+  for (size_t j = 0; j < r->nout; j++) out[j] = ob + j * r->B;
 }
 
 }  // namespace
@@ -260,8 +263,9 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
   // outputs go back as soon as the iteration's kernel is done
   cudaStreamWaitEvent(s_out, it.done, 0);
   for (Req *r : ok) {
-    cudaMemcpyAsync(r->out, arena_base + r->off + r->in_span, r->out_bytes,
-                    cudaMemcpyDeviceToHost, s_out);
+    if (!r->device)
+      cudaMemcpyAsync(r->out, arena_base + r->off + r->in_span, r->out_bytes,
+                      cudaMemcpyDeviceToHost, s_out);
     cudaEventRecord(r->ev_out, s_out);
     r->state = kRunning;
   }
@@ -281,6 +285,13 @@ void pmrc_server::run() {
     // 1. admit
     while (!queue.empty() && (int)active.size() < max_slots) {
       Req *r = queue.front();
+      if (r->device) {  // its blocks are already on the device: ready at once
+        queue.pop_front();
+        r->state = kReady;
+        active.push_back(r);
+        progress = true;
+        continue;
+      }
       size_t off;
       if (!arena->alloc(r->in_span + r->out_bytes, off)) break;
       queue.pop_front();
@@ -318,7 +329,7 @@ void pmrc_server::run() {
                        r->state == kFailed;
       if (fin) {
         if (r->state == kRunning) r->state = kDone;
-        arena->release(r->off, r->in_span + r->out_bytes);
+        if (!r->device) arena->release(r->off, r->in_span + r->out_bytes);
         r->t_done = Clock::now();
         if (r->state == kDone) {
           lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit)
@@ -425,7 +436,8 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   if (c->m.w != 8) return sfail(PMRC_EUNSUPPORTED, "the server takes GF(2^8) codes");
   std::unique_ptr<Req> r(new (std::nothrow) Req());
   if (!r) return sfail(PMRC_ENOMEM, "out of host memory");
-  r->op = q->op;
+  r->op = q->op & ~PMRC_REQ_DEVICE;
+  r->device = (q->op & PMRC_REQ_DEVICE) != 0;
   r->code = c;
   r->B = q->block_bytes;
   r->in = q->in;
@@ -441,7 +453,7 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != s->device) cudaSetDevice(s->device);
-  switch (q->op) {
+  switch (r->op) {
     case PMRC_OP_ENCODE:
       r->nin = K;
       r->nout = c->m.systematic ? N - KA : N;
@@ -504,8 +516,12 @@ int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) 
   r->in_bytes = r->nin * r->B;
   r->out_bytes = r->nout * r->B;
   r->in_span = (r->in_bytes + kAlign - 1) & ~(kAlign - 1);
-  if (r->in_span + r->out_bytes > s->arena->size())
+  if (!r->device && r->in_span + r->out_bytes > s->arena->size())
     return sfail(PMRC_ENOMEM, "request larger than the server's HBM budget");
+  if (r->device) {  // the kernel reads and writes the caller's blocks in place
+    bool aligned = ((uintptr_t)r->in % 16 == 0) && ((uintptr_t)r->out % 16 == 0) && r->B % 16 == 0;
+    if (!aligned) return sfail(PMRC_EINVAL, "device-resident blocks must be 16-byte aligned");
+  }
   if (cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return sfail(PMRC_ECUDA, "cudaEventCreate");

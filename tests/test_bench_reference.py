@@ -1,6 +1,7 @@
-"""The benchmark's reference arm (the CPU oracle timed on the host cores,
-`bench.py --impl reference`) runs without a GPU and prints one JSON line
-with the contract's keys, for the same metric and unit as the GPU arm."""
+"""The benchmark's reference arm (the CPU oracle timed on every host core
+the process may use, one thread per column slice, `bench.py --impl
+reference`) runs without a GPU and prints one JSON line with the contract's
+keys, for the same metric and unit as the GPU arm."""
 import json
 import os
 import subprocess
@@ -23,7 +24,9 @@ def test_reference_arm_prints_one_json_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cores = len(os.sched_getaffinity(0))
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == cores
+    assert d["cpu_baseline"]["cpu_model"]
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}

@@ -174,3 +174,40 @@ def test_serving_many_small_requests_all_complete():
     for o in outs:
         assert np.array_equal(o.numpy(), want)
     srv.close()
+
+
+def test_serving_device_resident_requests_in_place():
+    """Requests whose blocks already live in device memory (PMRC_REQ_DEVICE):
+    no arena space and no copies; results equal the oracle's and the host
+    requests' in the same mix."""
+    w = Workload(24, seed=23, max_stripe=400_000)
+    for q in w.reqs:                 # device-resident blocks need 16-byte sizes
+        if q["B"] % 16:
+            q["skip"] = True
+    srv = P.Server(budget_bytes=64 << 20, max_slots=16)
+    ids, dev = [], []
+    for q in w.reqs:
+        if q.get("skip"):
+            continue
+        din = q["in"].cuda()
+        dout = torch.full(q["want"].shape, 0xA5, dtype=torch.uint8, device="cuda")
+        op = {"encode": P.PMRC_OP_ENCODE, "repair": P.PMRC_OP_REPAIR,
+              "decode": P.PMRC_OP_DECODE}[q["op"]]
+        ids.append(srv.submit(op | P.PMRC_REQ_DEVICE, q["code"], q["B"], din, dout,
+                              failed=q.get("f", -1), helpers=q.get("H"), nodes=q.get("S")))
+        dev.append((q, din, dout))
+        ids.append(Workload.submit(srv, q))           # the same request from host buffers
+    for rid in ids:
+        st, lat = srv.wait(rid, timeout_ms=30000)
+        assert st == P.PMRC_OK and lat >= 0
+    assert srv.stats()["peak_bytes"] <= srv.stats()["budget_bytes"]
+    torch.cuda.synchronize()
+    for q, din, dout in dev:
+        assert np.array_equal(dout.cpu().numpy(), q["want"]), (q["op"], q["k"], q["B"])
+        assert np.array_equal(q["out"].numpy(), q["want"]), (q["op"], q["k"], q["B"])
+    with pytest.raises(P.PMRCError) as e:            # misaligned device blocks are refused
+        q, din, dout = dev[0]
+        srv.submit(P.PMRC_OP_ENCODE | P.PMRC_REQ_DEVICE, q["code"], q["B"], din.data_ptr() + 1,
+                   dout)
+    assert e.value.rc == P.PMRC_EINVAL
+    srv.close()
