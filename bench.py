@@ -321,6 +321,13 @@ class Workload:
 
 
 def run_ours(args, rank, world, local_rank):
+    # an empty on-disk kernel cache of this run's own: the initialization
+    # section measures cold compilations whatever earlier processes cached
+    import atexit
+    import shutil
+    cache = tempfile.mkdtemp(prefix="pmrc-bench-kernels-")
+    os.environ["PMRC_KERNEL_CACHE"] = cache
+    atexit.register(shutil.rmtree, cache, True)
     import torch
 
     import paper_1412_3022_gb300 as P
@@ -685,6 +692,16 @@ def run_init(torch, P, inputs, args, dev):
     out["decode_pattern_first_call_ms"] = round(first, 2)
     out["decode_pattern_kernel_ready_ms"] = round(ready, 2)
     out["decode_pattern_init_ms"] = round(first - again, 2)
+    # a new handle (as in a new process) has none of these kernels loaded:
+    # its first reconstruction of the same node set finds the compiled
+    # kernel in the on-disk cache instead of running NVRTC again
+    c2 = P.Code(N_, K_, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    first2 = wall(lambda: c2.decode(S, din, [Xr[r] for r in range(K)], B))
+    t = time.perf_counter()
+    c2.wait_kernels()
+    out["decode_pattern_kernel_ready_from_disk_cache_ms"] = round(
+        first2 + (time.perf_counter() - t) * 1e3, 2)
+    del c2
     first = wall(rep)                    # plans; the newcomer's kernel compiling
     t = time.perf_counter()
     c.wait_kernels()                     # (no compilation outlives this section)
@@ -694,9 +711,10 @@ def run_init(torch, P, inputs, args, dev):
     out["repair_pattern_init_ms"] = round(first - again, 2)
     out["repair_pattern_kernel_ready_ms"] = round(ready, 2)
     out["note"] = ("host wall clock; a pattern's first call builds its plans and starts "
-                   "compiling its bitsliced kernel (NVRTC: the reconstruction's, the newcomer's) "
-                   "in the background, running the split-table kernel meanwhile; kernel_ready is "
-                   "when the compilation ended")
+                   "compiling its bitsliced kernel (NVRTC: the reconstruction's, the newcomer's, "
+                   "the helper projections') in the background, running the split-table kernel "
+                   "meanwhile; kernel_ready is when the compilation ended; the bench runs with an "
+                   "empty on-disk kernel cache of its own, so the first compilations are cold")
     del Y, Xr, recv, node, c
     torch.cuda.synchronize()
     return out

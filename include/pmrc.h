@@ -207,12 +207,16 @@ int pmrc_read_degraded(const pmrc_code *code, int node, const int *helpers,
  * 64 KiB is rejected with PMRC_EUNSUPPORTED (no code with alpha <= 16 comes
  * close: k = 16 needs about 10 KiB).
  *
- * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
+ * Every call looks up the array's device address on the calling thread's
+ * current device (cudaGetSymbolAddress, a host-side query; the array's
+ * host-side name is not a device address).  The first call on a device also
+ * loads the library's device code there, so make that first call before any
  * stream capture.  Every call uses the same array and it keeps the last
  * call's contents, so calls that overlap on the GPU (other streams, other
  * host threads) race and corrupt each other's results: issue them one after
- * another on one stream. */
+ * another on one stream.  For PMRC_RS codes (one block per node, helper
+ * coefficient 1) the fused kernel applies the newcomer's 1 x k row to the
+ * helper blocks read in place. */
 int pmrc_repair_noalloc(const pmrc_code *code, int failed, const int *helpers,
                         const uint8_t *const *helper_blocks, uint8_t *const *out,
                         size_t block_bytes, pmrc_stream_t stream);
@@ -310,17 +314,23 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * PMRC_KERNEL_BITSLICED falls back to the split-table kernel rather than
  * failing.
  *
- * Under PMRC_KERNEL_AUTO the run-time compilations (encode, reconstruction,
- * newcomer) run on background threads: the call that needs one starts it
- * and runs the split-table kernel, as do later calls until it has finished
- * (pmrc_wait_kernels waits for it); the first call after that loads it.
- * Under PMRC_KERNEL_BITSLICED the call compiles before it launches.
+ * The same policy governs the repair kernels compiled at run time: the
+ * helper projections (pmrc_repair_helper(s), one kernel per failed node) and
+ * the fused repair (pmrc_repair, one kernel per failed node and helper set,
+ * alpha <= 8), which AUTO takes from 256 KiB blocks.
  *
- * Kernels compiled at run time can be kept across handles and processes:
- * when the environment variable PMRC_KERNEL_CACHE names a writable
- * directory, each compiled cubin is stored there under a hash of its
- * source, and a later compilation of the same schedule reads the file
- * instead of running NVRTC. */
+ * Under PMRC_KERNEL_AUTO the run-time compilations (encode, reconstruction,
+ * newcomer, repair) run on background threads: the call that needs one
+ * starts it and runs the split-table kernel, as do later calls until it has
+ * finished (pmrc_wait_kernels waits for it); the first call after that loads
+ * it.  Under PMRC_KERNEL_BITSLICED the call compiles before it launches.
+ *
+ * Kernels compiled at run time are kept across handles and processes: each
+ * compiled cubin is stored on disk under a hash of its source, and a later
+ * compilation of the same schedule reads the file instead of running NVRTC.
+ * The directory is the environment variable PMRC_KERNEL_CACHE when it is
+ * set (empty, "0" or "off" turns the cache off), else $XDG_CACHE_HOME/pmrc,
+ * else $HOME/.cache/pmrc (created, mode 0700), read at each compilation. */
 int pmrc_set_decode_kernel(pmrc_code *code, int which);
 
 /* Waits until the handle's background compilations have finished, at most

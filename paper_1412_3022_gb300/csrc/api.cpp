@@ -18,6 +18,7 @@
 #include "jit.h"
 #include "plan.h"
 #include "region.h"
+#include "trace.h"
 
 using namespace pmrc;
 
@@ -239,6 +240,7 @@ int pmrc_create(int n, int k, int d, int construction, int form, pmrc_code **out
 
 int pmrc_create_field(int n, int k, int d, int construction, int form, int field_bits,
                       pmrc_code **out) {
+  PMRC_TRACE("pmrc_create_field");
   if (!out) return fail(PMRC_EINVAL, "out is NULL");
   *out = nullptr;
   if (field_bits != 8 && field_bits != 16) return fail(PMRC_EINVAL, "field_bits must be 8 or 16");
@@ -422,6 +424,7 @@ int pmrc_set_encode_kernel(pmrc_code *c, int which) {
 
 int pmrc_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
                 size_t nbytes, pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_encode");
   if (!c || !data || !out) return fail(PMRC_EINVAL, "NULL argument");
   if (is16(c)) {
     if (nbytes % 2) return fail(PMRC_EINVAL, "GF(2^16) blocks hold whole 2-byte symbols");
@@ -595,6 +598,7 @@ extern "C" {
 int pmrc_repair_helpers(const pmrc_code *c, int f, int nh, const int *helpers,
                         const uint8_t *const *blocks, uint8_t *const *out, size_t nbytes,
                         pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_repair_helpers");
   if (!c || !blocks || !out || nh <= 0 || (nh > 1 && !helpers))
     return fail(PMRC_EINVAL, "NULL argument or nhelpers <= 0");
   if (f < 0 || f >= c->m.n) return fail(PMRC_EINVAL, "failed node out of range");
@@ -622,6 +626,7 @@ int pmrc_repair_helper(const pmrc_code *c, int f, int helper, const uint8_t *con
 int pmrc_repair_newcomer(const pmrc_code *c, int f, const int *helpers,
                          const uint8_t *const *received, uint8_t *const *out, size_t nbytes,
                          pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_repair_newcomer");
   if (!c || !helpers || !received || !out) return fail(PMRC_EINVAL, "NULL argument");
   if (is16(c)) {
     if (nbytes % 2) return fail(PMRC_EINVAL, "GF(2^16) blocks hold whole 2-byte symbols");
@@ -636,6 +641,7 @@ int pmrc_repair_newcomer(const pmrc_code *c, int f, const int *helpers,
 
 int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
                 uint8_t *const *out, size_t nbytes, pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_repair");
   if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
   if (is16(c)) return not_for16("pmrc_repair (fused)");
   if (c->m.alpha > 16) return fail(PMRC_EUNSUPPORTED, "pmrc_repair needs alpha <= 16");
@@ -693,6 +699,7 @@ int pmrc_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *co
 int pmrc_read_degraded(const pmrc_code *c, int node, const int *helpers,
                        const uint8_t *const *blocks, uint8_t *const *out, size_t offset,
                        size_t length, pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_read_degraded");
   if (!c || !helpers || !blocks || !out) return fail(PMRC_EINVAL, "NULL argument");
   if (!c->m.systematic) return fail(PMRC_EINVAL, "degraded reads need a systematic handle");
   if (node < 0 || node >= c->m.k) return fail(PMRC_EINVAL, "node is not a systematic node");
@@ -718,6 +725,7 @@ int pmrc_repair_noalloc(const pmrc_code *c, int f, const int *helpers,
 
 int pmrc_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                 uint8_t *const *data_out, size_t nbytes, pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_decode");
   if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
   {
     std::vector<char> seen(c->m.n, 0);
@@ -1055,6 +1063,7 @@ extern "C" {
 int pmrc_decode_specific(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                          uint8_t *const *data_out, size_t nbytes, void *workspace,
                          size_t workspace_bytes, pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_decode_specific");
   if (!c || !nodes || !node_blocks || !data_out) return fail(PMRC_EINVAL, "NULL argument");
   if (c->m.construction > 1)
     return fail(PMRC_EUNSUPPORTED, "the data collector of this library is the PM-MSR one");
@@ -1093,6 +1102,7 @@ int pmrc_decode_specific(const pmrc_code *c, const int *nodes, const uint8_t *co
 int pmrc_encode_precode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *parity,
                         size_t nbytes, void *workspace, size_t workspace_bytes,
                         pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_encode_precode");
   if (!c || !data || !parity) return fail(PMRC_EINVAL, "NULL argument");
   if (c->m.construction > 1)
     return fail(PMRC_EUNSUPPORTED, "precode encode is the PM-MSR systematic construction");

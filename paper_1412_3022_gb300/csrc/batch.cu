@@ -26,6 +26,7 @@
 #include "api_internal.h"
 #include "batch_internal.h"
 #include "device_info.h"
+#include "trace.h"
 #include "gf256.h"
 
 namespace pmrc {
@@ -482,6 +483,7 @@ int pmrc_batch_add_decode(pmrc_batch *b, const pmrc_code *c, const int *nodes,
 }
 
 int pmrc_batch_build(pmrc_batch *b, int work_bytes, int ctas_per_sm) {
+  PMRC_TRACE("pmrc_batch_build");
   if (!b) return bfail(PMRC_EINVAL, "NULL batch");
   if (b->stripes.empty()) return bfail(PMRC_EINVAL, "empty batch");
   if (work_bytes <= 0 || ctas_per_sm <= 0) {
@@ -498,6 +500,7 @@ int pmrc_batch_build(pmrc_batch *b, int work_bytes, int ctas_per_sm) {
 }
 
 int pmrc_batch_launch(pmrc_batch *b, pmrc_stream_t stream) {
+  PMRC_TRACE("pmrc_batch_launch");
   if (!b || !b->built) return bfail(PMRC_EINVAL, "batch not built");
   cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
   if (e != cudaSuccess)
@@ -506,6 +509,7 @@ int pmrc_batch_launch(pmrc_batch *b, pmrc_stream_t stream) {
 }
 
 int pmrc_batch_tune(pmrc_batch *b, pmrc_stream_t stream, int *best_out) {
+  PMRC_TRACE("pmrc_batch_tune");
   if (!b || b->stripes.empty()) return bfail(PMRC_EINVAL, "empty batch");
   const int work[] = {16 << 10, 64 << 10, 256 << 10};
   const int ctas[] = {1, 2};

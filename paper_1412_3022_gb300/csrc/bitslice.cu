@@ -91,7 +91,7 @@ namespace {
 cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs, int noutputs,
                       const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
                       cudaStream_t stream, std::atomic<uint64_t> (&smem_set)[kMaxDevices],
-                      int slot) {
+                      int slot, size_t extra_smem = 0) {
   BsArgs a;
   a.nbytes = nbytes;
   a.hi28 = 1u << 28;
@@ -104,7 +104,7 @@ cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs,
   for (int i = 0; i < ninputs; i++) a.ptr[i] = const_cast<uint8_t *>(in[i]);
   for (int j = 0; j < noutputs; j++) a.ptr[ninputs + j] = out[j];
   const int sms = current_sm_count();
-  const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes;  // 80 KiB
+  const size_t smem = (size_t)kBsSlots * kBsThreads * kBsBytes + extra_smem;  // 80 KiB ring
   {
     const cudaError_t e = allow_max_smem(fn, smem_set, slot);
     if (e != cudaSuccess) return e;
@@ -142,6 +142,7 @@ struct BsRuntimeKernel {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t fn = nullptr;
   int kind = kBsMatrix;
+  int pairs = 0;  // warp pairs split each item's inputs (bs_emit_kernel)
   int nblocks = 0, ninputs = 0, noutputs = 0;
   int alpha = 0, d = 0;
   std::vector<int> cost;
@@ -198,7 +199,11 @@ int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool 
   if (rc) return rc;
   out.name = std::string("bs_rt_") + role;
   const char *kname = out.name.c_str();
-  const BsEmitted em = bs_emit_kernel(M, rows, cols, blks, kname, true);
+  // matrices cut into consecutive rows (reconstruction rows, newcomer
+  // applies) are few blocks over many inputs: their launches have about one
+  // tile per warp, so warp pairs split each item's inputs
+  const bool pairs = !by_support;
+  const BsEmitted em = bs_emit_kernel(M, rows, cols, blks, kname, true, pairs);
   const std::string src =
       "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\n"
       "typedef unsigned int uint32_t;\ntypedef unsigned long long uint64_t;\n" +
@@ -206,6 +211,7 @@ int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool 
   rc = jit_compile(src, kname, out.cubin, err);
   if (rc) return rc;
   out.kind = kBsMatrix;
+  out.pairs = pairs ? 1 : 0;
   out.nblocks = (int)blks.size();
   out.ninputs = cols;
   out.noutputs = rows;
@@ -218,6 +224,7 @@ int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, st
   const int rc = jit_load(c.cubin, c.name.c_str(), &k->lib, &k->fn, err);
   if (rc) return rc;
   k->kind = c.kind;
+  k->pairs = c.pairs;
   k->nblocks = c.nblocks;
   k->ninputs = c.ninputs;
   k->noutputs = c.noutputs;
@@ -238,7 +245,8 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by
 cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,
                                     uint8_t *const *out, size_t nbytes, cudaStream_t stream) {
   return bs_launch(reinterpret_cast<const void *>(k.fn), k.nblocks, k.cost.data(), k.ninputs,
-                   k.noutputs, in, out, nbytes, stream, k.smem_set, 0);
+                   k.noutputs, in, out, nbytes, stream, k.smem_set, 0,
+                   k.pairs ? (size_t)kBsPairExchangeBytes : 0);
 }
 
 int bitslice_max_pointers() { return kBsMaxPtr; }
@@ -345,9 +353,7 @@ cudaError_t bitslice_launch_fused_repair(BsRuntimeKernel &k, const uint8_t *cons
                       (size_t)(kBsThreads / 64) * k.alpha * 8 * 32 * 4;
   cudaError_t e = allow_max_smem(fn, k.smem_set, 0);
   if (e != cudaSuccess) return e;
-  const uint64_t pairs = kBsThreads / 64;
-  const int ncta = (int)std::max<uint64_t>(
-      1, std::min<uint64_t>(current_sm_count(), (a.ntiles + pairs - 1) / pairs));
+  const int ncta = (int)std::max<uint64_t>(1, std::min<uint64_t>(current_sm_count(), a.ntiles));
   void *args[] = {&a};
   return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);
 }

@@ -55,6 +55,7 @@ struct BsCompiled {
   std::string name;  // kernel name: bs_rt_<role>
   std::vector<char> cubin;
   int kind = kBsMatrix;
+  int pairs = 0;  // warp pairs split each item's inputs (matrix kernels of consecutive rows)
   int nblocks = 0, ninputs = 0, noutputs = 0;
   int alpha = 0, d = 0;  // repair kernels: blocks per node, helpers
   std::vector<int> cost;

@@ -87,8 +87,89 @@ void bs_cta_ranges(int nblocks, const int *cost, uint64_t ntiles, int ncta, uint
   cta_g[ncta] = (uint32_t)items;
 }
 
+namespace {
+
+// One block function: the loop over `ins` (a block's inputs, or half of
+// them) accumulating M's coefficients of the block's rows into acc.  Returns
+// the accumulate instructions emitted.
+int emit_block_fn(std::string &f, const uint8_t *M, int K, const BsBlock &B,
+                  const std::vector<int> &ins, const std::string &fname, long long &xors) {
+  int ops = 0;
+  {  // the inputs' columns, read by the prefetch in the loop below
+    std::string colsl;
+    for (size_t i = 0; i < ins.size(); i++) colsl += (i ? ", " : "") + std::to_string(ins[i]);
+    f += "__constant__ uint8_t " + fname + "_in[" + std::to_string(std::max<size_t>(ins.size(), 1)) +
+         "] = {" + (colsl.empty() ? std::string("0") : colsl) + "};\n";
+  }
+  appendf(f, "__device__ __forceinline__ void %s(const BsCtx &x, uint32_t (&acc)[8][8]) {\n",
+          fname.c_str());
+  f += "  uint32_t Q[16], R[16];\n";
+  const int C = (int)ins.size();
+  // one loop over the inputs: prefetch, transpose and subset tables are
+  // emitted once; only the accumulate XORs differ per input (a switch),
+  // which keeps a block's code at about half its fully unrolled size.
+  // The ring's read and write slots advance by one slot per input and wrap
+  // (no slot index arithmetic).  Short blocks commit empty groups so the
+  // wait count stays kAhead - 1.
+  appendf(f, "  const uint8_t *in = %s_in;\n", fname.c_str());
+  f += "  const uint32_t base = bs_ring_base(), end = base + kBsSlots * kBsSlotStep;\n";
+  for (int i = 0; i < kAhead; i++)
+    if (i < C)
+      appendf(f, "  bs_prefetch(x, %d, base + %d * kBsSlotStep);\n", ins[i], i % kSlots);
+    else
+      f += "  bs_commit_empty();\n";
+  appendf(f, "  uint32_t rd = base, wr = base + %d * kBsSlotStep;\n", kAhead % kSlots);
+  appendf(f, "#pragma unroll 1\n  for (int i = 0; i < %d; i++) {\n", C);
+  appendf(f, "    bs_wait<%d>();\n    bs_planes(x, rd, Q, R);\n", kAhead - 1);
+  appendf(f, "    if (i + %d < %d) bs_prefetch(x, in[i + %d], wr); else bs_commit_empty();\n",
+          kAhead, C, kAhead);
+  f += "    rd += kBsSlotStep;\n    rd = rd == end ? base : rd;\n";
+  f += "    wr += kBsSlotStep;\n    wr = wr == end ? base : wr;\n";
+  f += "    switch (i) {\n";
+  for (int i = 0; i < C; i++) {
+    appendf(f, "    case %d:\n", i);
+    const int col = ins[i];
+    for (size_t q = 0; q < B.rows.size(); q++) {
+      const uint8_t cf = M[(size_t)B.rows[q] * K + col];
+      for (int bit = 0; bit < 8; bit++) {
+        int lo = 0, hi = 0;  // row `bit` of M_cf, split in two nibbles
+        for (int j = 0; j < 8; j++) {
+          const uint8_t colj = gf_mul_sr(cf, (uint8_t)(1u << j));
+          if ((colj >> bit) & 1) {
+            if (j < 4)
+              lo |= 1 << j;
+            else
+              hi |= 1 << (j - 4);
+          }
+        }
+        // one logic instruction per (row, plane, input): acc ^ Q[lo] ^ R[hi]
+        if (lo && hi) {
+          appendf(f, "      acc[%zu][%d] = bs_x3(acc[%zu][%d], Q[%d], R[%d]);\n", q, bit, q, bit,
+                  lo, hi);
+          xors += 2;
+          ops++;
+        } else if (lo) {
+          appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], Q[%d]);\n", q, bit, q, bit, lo);
+          xors += 1;
+          ops++;
+        } else if (hi) {
+          appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], R[%d]);\n", q, bit, q, bit, hi);
+          xors += 1;
+          ops++;
+        }
+      }
+    }
+    f += "      break;\n";
+  }
+  f += "    default: break;\n    }\n  }\n";
+  f += "}\n\n";
+  return ops;
+}
+
+}  // namespace
+
 BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
-                         const std::string &name, bool extern_c) {
+                         const std::string &name, bool extern_c, bool pair_split) {
   BsEmitted e;
   std::string &f = e.code;
   const int K = cols;
@@ -98,96 +179,71 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
     const BsBlock &B = blks[b];
     appendf(f, "// %s block %zu: %zu rows x %zu inputs\n", name.c_str(), b, B.rows.size(),
             B.inputs.size());
-    {  // the block's input columns, read by the prefetch in the loop below
-      std::string colsl;
-      for (size_t i = 0; i < B.inputs.size(); i++) colsl += (i ? ", " : "") + std::to_string(B.inputs[i]);
-      f += "__constant__ uint8_t " + name + "_b" + std::to_string(b) + "_in[" +
-           std::to_string(std::max<size_t>(B.inputs.size(), 1)) + "] = {" +
-           (colsl.empty() ? std::string("0") : colsl) + "};\n";
+    const std::string fn = name + "_b" + std::to_string(b);
+    if (!pair_split) {
+      blk_ops[b] = emit_block_fn(f, M, K, B, B.inputs, fn, e.xors);
+    } else {  // the inputs cut in two halves, one per warp of a pair
+      const size_t h = (B.inputs.size() + 1) / 2;
+      const std::vector<int> i0(B.inputs.begin(), B.inputs.begin() + h), i1(B.inputs.begin() + h,
+                                                                           B.inputs.end());
+      blk_ops[b] = emit_block_fn(f, M, K, B, i0, fn + "_h0", e.xors);
+      blk_ops[b] += emit_block_fn(f, M, K, B, i1, fn + "_h1", e.xors);
     }
-    appendf(f, "__device__ __forceinline__ void %s_b%zu(const BsCtx &x, uint32_t (&acc)[8][8]) {\n",
-            name.c_str(), b);
-    f += "  uint32_t Q[16], R[16];\n";
-    const int C = (int)B.inputs.size();
-    // one loop over the inputs: prefetch, transpose and subset tables are
-    // emitted once; only the accumulate XORs differ per input (a switch),
-    // which keeps a block's code at about half its fully unrolled size.
-    // The ring's read and write slots advance by one slot per input and wrap
-    // (no slot index arithmetic).  Short blocks commit empty groups so the
-    // wait count stays kAhead - 1.
-    appendf(f, "  const uint8_t *in = %s_b%zu_in;\n", name.c_str(), b);
-    f += "  const uint32_t base = bs_ring_base(), end = base + kBsSlots * kBsSlotStep;\n";
-    for (int i = 0; i < kAhead; i++)
-      if (i < C)
-        appendf(f, "  bs_prefetch(x, %d, base + %d * kBsSlotStep);\n", B.inputs[i], i % kSlots);
-      else
-        f += "  bs_commit_empty();\n";
-    appendf(f, "  uint32_t rd = base, wr = base + %d * kBsSlotStep;\n", kAhead % kSlots);
-    appendf(f, "#pragma unroll 1\n  for (int i = 0; i < %d; i++) {\n", C);
-    appendf(f, "    bs_wait<%d>();\n    bs_planes(x, rd, Q, R);\n", kAhead - 1);
-    appendf(f, "    if (i + %d < %d) bs_prefetch(x, in[i + %d], wr); else bs_commit_empty();\n",
-            kAhead, C, kAhead);
-    f += "    rd += kBsSlotStep;\n    rd = rd == end ? base : rd;\n";
-    f += "    wr += kBsSlotStep;\n    wr = wr == end ? base : wr;\n";
-    f += "    switch (i) {\n";
-    for (int i = 0; i < C; i++) {
-      appendf(f, "    case %d:\n", i);
-      const int col = B.inputs[i];
-      for (size_t q = 0; q < B.rows.size(); q++) {
-        const uint8_t cf = M[(size_t)B.rows[q] * K + col];
-        for (int bit = 0; bit < 8; bit++) {
-          int lo = 0, hi = 0;  // row `bit` of M_cf, split in two nibbles
-          for (int j = 0; j < 8; j++) {
-            const uint8_t colj = gf_mul_sr(cf, (uint8_t)(1u << j));
-            if ((colj >> bit) & 1) {
-              if (j < 4)
-                lo |= 1 << j;
-              else
-                hi |= 1 << (j - 4);
-            }
-          }
-          // one logic instruction per (row, plane, input): acc ^ Q[lo] ^ R[hi]
-          if (lo && hi) {
-            appendf(f, "      acc[%zu][%d] = bs_x3(acc[%zu][%d], Q[%d], R[%d]);\n", q, bit, q, bit,
-                    lo, hi);
-            e.xors += 2;
-            blk_ops[b]++;
-          } else if (lo) {
-            appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], Q[%d]);\n", q, bit, q, bit, lo);
-            e.xors += 1;
-            blk_ops[b]++;
-          } else if (hi) {
-            appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], R[%d]);\n", q, bit, q, bit, hi);
-            e.xors += 1;
-            blk_ops[b]++;
-          }
-        }
-      }
-      f += "      break;\n";
-    }
-    f += "    default: break;\n    }\n  }\n";
-    f += "}\n\n";
   }
-  // persistent kernel, one CTA per SM: the host splits the sequence of
-  // (block, 1 KiB column tile) items into equal-cost ranges, one per CTA, so
-  // an SM runs one block's straight-line code (two at a range boundary),
-  // fetched into its instruction caches once and then re-executed; the
-  // warps take the range's tiles in turn
   appendf(f, "%s__global__ void __launch_bounds__(kBsThreads, 1) %s(const __grid_constant__ BsArgs a) {\n",
           extern_c ? "extern \"C\" " : "", name.c_str());
   f += "  const uint32_t g1 = a.cta_g[blockIdx.x + 1];\n";
-  f += "  for (uint32_t g = a.cta_g[blockIdx.x] + threadIdx.x / 32; g < g1; g += kBsThreads / 32) {\n";
-  f += "    const uint32_t b = g / a.ntiles, u = g - b * a.ntiles;\n";
-  f += "    BsCtx x;\n    if (!bs_ctx(a, x, u)) continue;\n    uint32_t acc[8][8];\n";
-  f += "    bs_zero(acc);\n    switch (b) {\n";
-  for (size_t b = 0; b < blks.size(); b++) {
-    const BsBlock &B = blks[b];
-    appendf(f, "      case %zu: {\n        %s_b%zu(x, acc);\n", b, name.c_str(), b);
-    for (size_t q = 0; q < B.rows.size(); q++)
-      appendf(f, "        bs_store(x, %d, acc[%zu]);\n", K + B.rows[q], q);
-    f += "      } break;\n";
+  if (!pair_split) {
+    // persistent kernel, one CTA per SM: the host splits the sequence of
+    // (block, 1 KiB column tile) items into equal-cost ranges, one per CTA,
+    // so an SM runs one block's straight-line code (two at a range
+    // boundary), fetched into its instruction caches once and then
+    // re-executed; the warps take the range's tiles in turn
+    f += "  for (uint32_t g = a.cta_g[blockIdx.x] + threadIdx.x / 32; g < g1; g += kBsThreads / 32) {\n";
+    f += "    const uint32_t b = g / a.ntiles, u = g - b * a.ntiles;\n";
+    f += "    BsCtx x;\n    if (!bs_ctx(a, x, u)) continue;\n    uint32_t acc[8][8];\n";
+    f += "    bs_zero(acc);\n    switch (b) {\n";
+    for (size_t b = 0; b < blks.size(); b++) {
+      const BsBlock &B = blks[b];
+      appendf(f, "      case %zu: {\n        %s_b%zu(x, acc);\n", b, name.c_str(), b);
+      for (size_t q = 0; q < B.rows.size(); q++)
+        appendf(f, "        bs_store(x, %d, acc[%zu]);\n", K + B.rows[q], q);
+      f += "      } break;\n";
+    }
+    f += "      default: break;\n    }\n  }\n}\n\n";
+  } else {
+    // the same ranges, taken by warp pairs: both warps of a pair work on the
+    // same item, each over half of the block's inputs; the partial sums meet
+    // in shared memory (one exchange area of 8 rows x 8 planes x 32 lanes
+    // per pair) and each warp stores half of the block's rows
+    f += "  extern __shared__ __align__(16) uint8_t bs_smem[];\n";
+    f += "  const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32, pair = warp / 2, half = warp % 2;\n";
+    f += "  uint32_t *xs = reinterpret_cast<uint32_t *>(bs_smem + kBsSlots * kBsSlotStep) + pair * 8 * 8 * 32;\n";
+    f += "  for (uint32_t g = a.cta_g[blockIdx.x] + pair; g < g1; g += kBsThreads / 64) {\n";
+    f += "    const uint32_t b = g / a.ntiles, u = g - b * a.ntiles;\n";
+    f += "    BsCtx x;\n    const bool live = bs_ctx(a, x, u);\n";
+    f += "    if (!live) x.off = 0;  // lanes past the end read in-range bytes and store nothing\n";
+    f += "    uint32_t acc[8][8];\n    bs_zero(acc);\n    switch (b) {\n";
+    for (size_t b = 0; b < blks.size(); b++) {
+      const BsBlock &B = blks[b];
+      const int R = (int)B.rows.size(), rs = (R + 1) / 2;
+      appendf(f, "      case %zu: {\n        if (half == 0) %s_b%zu_h0(x, acc); else %s_b%zu_h1(x, acc);\n",
+              b, name.c_str(), b, name.c_str(), b);
+      appendf(f, "#pragma unroll\n        for (int r = 0; r < %d; r++)\n          if ((r < %d) != (half == 0))\n"
+                 "#pragma unroll\n            for (int i = 0; i < 8; i++) xs[(r * 8 + i) * 32 + lane] = acc[r][i];\n",
+              R, rs);
+      f += "        bs_pair_sync(pair);\n";
+      for (int q = 0; q < R; q++) {
+        appendf(f, "        if ((%d < %d) == (half == 0)) {\n", q, rs);
+        appendf(f, "#pragma unroll\n          for (int i = 0; i < 8; i++) acc[%d][i] = bs_x2(acc[%d][i], xs[(%d * 8 + i) * 32 + lane]);\n",
+                q, q, q);
+        appendf(f, "          if (live) bs_store(x, %d, acc[%d]);\n        }\n", K + B.rows[q], q);
+      }
+      f += "        bs_pair_sync(pair);  // the exchange area is reused by the next item\n";
+      f += "      } break;\n";
+    }
+    f += "      default: break;\n    }\n  }\n}\n\n";
   }
-  f += "      default: break;\n    }\n  }\n}\n\n";
   // relative cost of each block (instructions per tile, roughly): input
   // transposes and subset tables, output transposes, accumulate XORs
   for (size_t b = 0; b < blks.size(); b++)
@@ -353,8 +409,9 @@ BsEmitted bs_emit_fused_repair(const uint8_t *phi, int alpha, const uint8_t *D, 
   f += "  const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32, pair = warp / 2, grp = warp % 2;\n";
   appendf(f, "  uint32_t *xs = reinterpret_cast<uint32_t *>(bs_smem + kBsSlots * kBsSlotStep) + pair * %d;\n",
           alpha * 8 * 32);
-  f += "  const uint32_t pairs = gridDim.x * (kBsThreads / 64);\n";
-  f += "  for (uint32_t u = blockIdx.x * (kBsThreads / 64) + pair; u < a.ntiles; u += pairs) {\n";
+  // tile u goes to CTA u % gridDim.x: consecutive tiles spread over every
+  // SM, whatever the tile count
+  f += "  for (uint32_t u = pair * gridDim.x + blockIdx.x; u < a.ntiles; u += gridDim.x * (kBsThreads / 64)) {\n";
   f += "    BsCtx x;\n    const bool live = bs_ctx(a, x, u);\n";
   f += "    if (!live) x.off = 0;  // lanes past the end read in-range bytes and store nothing\n";
   appendf(f, "    uint32_t acc[%d][8];\n#pragma unroll\n    for (int r = 0; r < %d; r++)\n#pragma unroll\n"

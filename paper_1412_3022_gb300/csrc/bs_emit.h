@@ -51,9 +51,14 @@ struct BsEmitted {
 // Source of the block functions and of the kernel `name` for the matrix M
 // (rows x cols, row-major): output row r goes to pointer slot cols + r.  With
 // extern_c the kernel gets C linkage (for lookup by name after run-time
-// compilation).
+// compilation).  With pair_split the two warps of a pair take each (block,
+// tile) item together, each over half of the block's inputs, and combine
+// their partial sums through shared memory (kBsPairExchangeBytes beyond the
+// staging ring): twice the warp tasks at half the latency, for launches
+// with few tiles per warp.
 BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
-                         const std::string &name, bool extern_c);
+                         const std::string &name, bool extern_c, bool pair_split = false);
+constexpr int kBsPairExchangeBytes = 8 * 8 * 8 * 32 * 4;  // 8 pairs x 8 rows x 8 planes x 32 lanes
 
 // Repair schedules, emitted at run time for one failed node's helper
 // coefficients phi (alpha entries, the projection each helper applies to its

@@ -8,6 +8,7 @@
 
 #include <dlfcn.h>
 #include <nvrtc.h>
+#include <sys/stat.h>
 #include <unistd.h>
 
 #include <condition_variable>
@@ -60,10 +61,31 @@ const Nvrtc &nvrtc() {
 constexpr int kNumOpts = 3;
 const char *const kOpts[kNumOpts] = {"--gpu-architecture=sm_103a", "-std=c++17", "-w"};
 
+// Directory of the on-disk cubin cache, read at each compilation (they are
+// rare): $PMRC_KERNEL_CACHE when set (empty, "0" or "off" turns the cache
+// off), else $XDG_CACHE_HOME/pmrc, else $HOME/.cache/pmrc, created (mode
+// 0700) when missing; "" when no writable directory results.
+std::string cache_dir() {
+  const char *env = getenv("PMRC_KERNEL_CACHE");
+  if (env) return (*env && strcmp(env, "0") != 0 && strcmp(env, "off") != 0) ? env : "";
+  const char *xdg = getenv("XDG_CACHE_HOME"), *home = getenv("HOME");
+  std::string base;
+  if (xdg && *xdg)
+    base = xdg;
+  else if (home && *home)
+    base = std::string(home) + "/.cache";
+  if (base.empty()) return "";
+  mkdir(base.c_str(), 0700);  // EEXIST is fine
+  const std::string d = base + "/pmrc";
+  mkdir(d.c_str(), 0700);
+  return access(d.c_str(), W_OK | X_OK) == 0 ? d : "";
+}
+
 // Path of the cached cubin for this source, or "" without a cache directory.
 std::string cache_path(const std::string &src, const Nvrtc &n) {
-  const char *dir = getenv("PMRC_KERNEL_CACHE");
-  if (!dir || !*dir) return "";
+  const std::string d = cache_dir();
+  if (d.empty()) return "";
+  const char *dir = d.c_str();
   uint64_t h = 1469598103934665603ull;  // FNV-1a over source, options, version
   auto mix = [&](const char *p, size_t len) {
     for (size_t i = 0; i < len; i++) {

@@ -15,11 +15,12 @@ bool jit_available();
 
 // Compiles CUDA source for sm_103a into a cubin (kEUnsupported with the
 // compiler log in err when NVRTC is missing or the source does not build).
-// When the environment variable PMRC_KERNEL_CACHE names a directory, cubins
-// are kept there under a hash of the source, the options and the NVRTC
-// version, and a later compilation of the same source (in this or another
-// process) reads the file instead; cache files that cannot be read or
-// written are ignored.
+// Cubins are kept on disk under a hash of the source, the options and the
+// NVRTC version, and a later compilation of the same source (in this or
+// another process) reads the file instead.  The directory is
+// $PMRC_KERNEL_CACHE when set (empty, "0" or "off" turns the cache off),
+// else $XDG_CACHE_HOME/pmrc or $HOME/.cache/pmrc; cache files that cannot be
+// read or written are ignored.
 int jit_compile(const std::string &src, const char *kernel_name, std::vector<char> &cubin,
                 std::string &err);
 

@@ -206,30 +206,15 @@ int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *cons
   rc = repair_pointers(h, helper_blocks, out, a, err);
   if (rc) return rc;
   if (nbytes == 0) return kOk;
-  // device address of the fixed scratch, looked up once per device with
-  // that device current (the host-side name is not a device address)
-  static std::mutex mu;
-  static std::map<int, uint8_t *> base_of;
-  int devid = -1;
-  cudaError_t e = cudaGetDevice(&devid);
-  if (e != cudaSuccess) {
-    err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
-    return kECuda;
-  }
+  // device address of the fixed scratch on the calling thread's current
+  // device, looked up on every call (a host-side query): the host-side name
+  // is not a device address, and a cached address would go stale if the
+  // device's context were torn down and the module loaded again
   uint8_t *base = nullptr;
-  {
-    std::lock_guard<std::mutex> g(mu);
-    auto it = base_of.find(devid);
-    if (it == base_of.end()) {
-      e = cudaGetSymbolAddress((void **)&base, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        err = std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e);
-        return kECuda;
-      }
-      base_of[devid] = base;
-    } else {
-      base = it->second;
-    }
+  cudaError_t e = cudaGetSymbolAddress((void **)&base, g_noalloc_scratch);
+  if (e != cudaSuccess) {
+    err = std::string("cudaGetSymbolAddress(fixed scratch): ") + cudaGetErrorString(e);
+    return kECuda;
   }
   e = cudaMemcpyAsync(base, plan.image.data(), plan.image.size(), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = repair_launch(h, a, base, nbytes, stream);

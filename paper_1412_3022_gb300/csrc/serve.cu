@@ -21,6 +21,8 @@
 // queries polled by the host: no device-side wait exists.
 #include <cuda_runtime.h>
 
+#include "trace.h"
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -429,6 +431,7 @@ void pmrc_server_destroy(pmrc_server *s) {
 }
 
 int pmrc_server_submit(pmrc_server *s, const pmrc_request *q, uint64_t *id_out) {
+  PMRC_TRACE("pmrc_server_submit");
   const Clock::time_point t_submit = Clock::now();
   if (!s || !q || !q->code || !q->in || !q->out || q->block_bytes == 0)
     return sfail(PMRC_EINVAL, "NULL argument or empty block");

@@ -1,5 +1,6 @@
 // Prints a random matrix and the bitsliced schedule the emitter writes for
-// it (both block rules), for tests/test_host_units.py to evaluate.
+// it (both block rules, optionally split over warp pairs), for
+// tests/test_host_units.py to evaluate.
 #include <cstdio>
 #include <cstdlib>
 #include <random>
@@ -16,7 +17,8 @@ int main(int argc, char **argv) {
   for (auto &v : M) v = (rng() % 4 == 0) ? 0 : (uint8_t)(rng() & 0xFF);
   const auto blks = by_support ? pmrc::bs_blocks_by_support(M.data(), rows, cols)
                                : pmrc::bs_blocks_chunked(M.data(), rows, cols);
-  const pmrc::BsEmitted e = pmrc::bs_emit_kernel(M.data(), rows, cols, blks, "k", true);
+  const bool pairs = argc > 5 && atoi(argv[5]) != 0;
+  const pmrc::BsEmitted e = pmrc::bs_emit_kernel(M.data(), rows, cols, blks, "k", true, pairs);
   printf("MATRIX %d %d\n", rows, cols);
   for (int r = 0; r < rows; r++) {
     for (int c = 0; c < cols; c++) printf("%d ", M[(size_t)r * cols + c]);

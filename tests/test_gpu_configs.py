@@ -19,13 +19,13 @@ the repairs in the batch are seeded random helper blocks: the repair is a
 linear map of the blocks it reads, and the oracle applies the same map
 (helper projections, then the newcomer matrix) to the same bytes."""
 import concurrent.futures as cf
-import os
 
 import numpy as np
 import pytest
 
 import oracle as O
 import paper_1412_3022_gb300 as P
+from oracle_columns import THREADS, oracle_columns
 from paper_1412_3022_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -33,26 +33,6 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
-
-THREADS = max(1, min(32, len(os.sched_getaffinity(0))))
-
-
-def oracle_columns(fn, arrays, slices=None):
-    """fn(*[a[:, s] for a in arrays]) for column slices s, stitched along
-    the columns.  The first slice runs on this thread (it initializes the
-    oracle's field tables), the rest on a thread pool."""
-    nbytes = arrays[0].shape[1]
-    parts = slices or max(1, min(4 * THREADS, nbytes // 4096))
-    edges = [nbytes * i // parts for i in range(parts + 1)]
-    cols = [slice(edges[i], edges[i + 1]) for i in range(parts) if edges[i + 1] > edges[i]]
-
-    def run(s):
-        return fn(*[np.ascontiguousarray(a[:, s]) for a in arrays])
-
-    first = run(cols[0])
-    with cf.ThreadPoolExecutor(THREADS) as ex:
-        rest = list(ex.map(run, cols[1:]))
-    return np.concatenate([first] + rest, axis=1)
 
 
 def oracle_encode_rows(n, k, cons, form, X):

@@ -45,20 +45,22 @@ def _gf_mul(a, b):
 
 def _evaluate_schedule(text, cols, X):
     """Runs the emitted XOR schedule on byte columns X (cols x T) the way
-    the kernel does: per block, per input, bit planes -> subset tables Q, R
-    -> the case's accumulate statements; then planes back to bytes."""
+    the kernel does: per block (per half of its inputs when the block is
+    split over a warp pair), per input, bit planes -> subset tables Q, R ->
+    the case's accumulate statements; the halves' sums XORed; then planes
+    back to bytes."""
     import re
     import numpy as np
     T = X.shape[1]
     planes = [((X >> j) & 1).astype(np.uint8) for j in range(8)]     # [j][col][t]
-    inputs = {int(b): [int(v) for v in lst.split(",")] for b, lst in
-              re.findall(r"k_b(\d+)_in\[\d+\] = \{([^}]*)\};", text)}
-    out = {}
-    for b, body in re.findall(r"void k_b(\d+)\(.*?\{(.*?)\n\}\n", text, re.S):
-        b = int(b)
-        acc = np.zeros((8, 8, T), np.uint8)
+    inputs = {name: [int(v) for v in lst.split(",")] for name, lst in
+              re.findall(r"(k_b\d+(?:_h[01])?)_in\[\d+\] = \{([^}]*)\};", text)}
+    acc_of = {}
+    for name, body in re.findall(r"void (k_b\d+(?:_h[01])?)\(.*?\{(.*?)\n\}\n", text, re.S):
+        b = int(re.match(r"k_b(\d+)", name).group(1))
+        acc = acc_of.setdefault(b, np.zeros((8, 8, T), np.uint8))
         for i, case in re.findall(r"case (\d+):(.*?)break;", body, re.S):
-            col = inputs[b][int(i)]
+            col = inputs[name][int(i)]
             p = [planes[j][col] for j in range(8)]
             Q = [np.bitwise_xor.reduce([p[j] for j in range(4) if s >> j & 1] or [np.zeros(T, np.uint8)])
                  for s in range(16)]
@@ -66,18 +68,23 @@ def _evaluate_schedule(text, cols, X):
                  for s in range(16)]
             for q, bit, terms in re.findall(
                     r"acc\[(\d+)\]\[(\d+)\] = bs_x[23]\(acc\[\1\]\[\2\], ([^;]*)\);", case):
-                for name, idx in re.findall(r"([QR])\[(\d+)\]", terms):
-                    acc[int(q), int(bit)] ^= (Q if name == "Q" else R)[int(idx)]
-        kernel_case = re.search(r"case %d: \{\s*k_b%d\(x, acc\);(.*?)\} break;" % (b, b), text, re.S)
+                for nm, idx in re.findall(r"([QR])\[(\d+)\]", terms):
+                    acc[int(q), int(bit)] ^= (Q if nm == "Q" else R)[int(idx)]
+    out = {}
+    for b, acc in acc_of.items():
+        kernel_case = re.search(r"case %d: \{\s*(?:if \(half == 0\) )?k_b%d(?:_h0)?\(x, acc\);(.*?)\} break;"
+                                % (b, b), text, re.S)
         for slot, q in re.findall(r"bs_store\(x, (\d+), acc\[(\d+)\]\)", kernel_case.group(1)):
             row = int(slot) - cols
             out[row] = sum((acc[int(q), bit].astype(np.uint16) << bit) for bit in range(8)).astype(np.uint8)
     return out
 
 
-@pytest.mark.parametrize("rows,cols,by_support,seed", [(13, 9, 0, 1), (21, 56, 0, 2), (8, 3, 1, 3),
-                                                       (30, 17, 1, 4), (1, 1, 0, 5), (7, 64, 0, 6)])
-def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed):
+@pytest.mark.parametrize("rows,cols,by_support,seed,pairs",
+                         [(13, 9, 0, 1, 0), (21, 56, 0, 2, 0), (8, 3, 1, 3, 0), (30, 17, 1, 4, 0),
+                          (1, 1, 0, 5, 0), (7, 64, 0, 6, 0), (21, 56, 0, 7, 1), (7, 14, 0, 8, 1),
+                          (13, 9, 0, 9, 1), (1, 1, 0, 10, 1), (3, 2, 0, 11, 1)])
+def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed, pairs):
     """The emitter's XOR schedule (blocks, input lists, subset-table terms,
     output slots), evaluated on the CPU, equals the GF(2^8) matrix product
     computed with an independent multiply."""
@@ -91,8 +98,8 @@ def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed):
                         os.path.join(ROOT, "tests", "host", "emit_dump.cpp"),
                         os.path.join(CSRC, "bs_emit.cpp")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
-    r = subprocess.run([exe, str(rows), str(cols), str(by_support), str(seed)], capture_output=True,
-                       text=True, timeout=120)
+    r = subprocess.run([exe, str(rows), str(cols), str(by_support), str(seed), str(pairs)],
+                       capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     head, code = r.stdout.split("CODE\n", 1)
     lines = head.strip().splitlines()
@@ -287,3 +294,40 @@ def test_kernel_cache_on_disk():
     with open(path, "rb") as f:
         assert f.read() == image                     # replaced by a fresh compilation
     shutil.rmtree(cache)
+
+
+def test_kernel_cache_default_directory_and_off():
+    """Without PMRC_KERNEL_CACHE the cubins go to $XDG_CACHE_HOME/pmrc
+    (created); PMRC_KERNEL_CACHE=off writes nothing."""
+    cxx = shutil.which("g++")
+    cuda = "/usr/local/cuda"
+    if not cxx or not os.path.exists(os.path.join(cuda, "include", "nvrtc.h")):
+        pytest.skip("g++ or the CUDA headers not found")
+    build = os.path.join(ROOT, "_build")
+    exe = os.path.join(build, "test_jit_cache")
+    r = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-I" + os.path.join(cuda, "include"),
+                        "-o", exe, os.path.join(ROOT, "tests", "host", "jit_cache.cpp"),
+                        os.path.join(CSRC, "jit.cpp"), "-L" + os.path.join(cuda, "lib64"),
+                        "-lcudart", "-ldl", "-lpthread"], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("cannot build against the CUDA runtime here: " + r.stderr[-200:])
+    base = os.path.join(build, "test_kernel_cache_xdg")
+    shutil.rmtree(base, ignore_errors=True)
+    os.makedirs(base)
+    env = {k: v for k, v in os.environ.items() if k != "PMRC_KERNEL_CACHE"}
+    env.update(XDG_CACHE_HOME=base,
+               LD_LIBRARY_PATH=os.path.join(cuda, "lib64") + ":" + os.environ.get("LD_LIBRARY_PATH", ""))
+    p = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=300)
+    assert p.returncode == 0, p.stdout + p.stderr
+    if p.stdout.strip() == "nonvrtc":
+        pytest.skip("NVRTC is not available")
+    files = os.listdir(os.path.join(base, "pmrc"))
+    assert len(files) == 1 and files[0].endswith(".cubin")
+    assert oct(os.stat(os.path.join(base, "pmrc")).st_mode & 0o777) == oct(0o700)
+    shutil.rmtree(base)
+    os.makedirs(base)
+    env["PMRC_KERNEL_CACHE"] = "off"
+    p = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=300)
+    assert p.returncode == 0 and p.stdout.startswith("ok"), p.stdout + p.stderr
+    assert os.listdir(base) == []
+    shutil.rmtree(base)
