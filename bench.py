@@ -408,25 +408,42 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(ach / hbm, 4), "peak_source": peak_src + " hbm_gbs (burst copy)",
                 "traffic": None}
     # the same kernel against its integer-ALU ceiling (64 ALU lanes/clk/SM
-    # on 152 SMs at the sampled clock); lane-ops per launch from the
-    # kernel's instruction model (alu_model)
+    # on 152 SMs at the sampled clock); ALU lane-ops per launch measured by
+    # ncu (sm__inst_executed_pipe_alu.sum x 32 on one launch of this
+    # workload, profiles/kernel_counters.json), the instruction model beside
+    # it; DRAM bytes per launch from the same captures
     mhz = (ck or {}).get("sm_mhz") or 2070.0
     peak_ops = 64.0 * SMS * mhz * 1e6 / 1e12
-    ach_ops = W.alu_ops[dom] / (op_ms[dom] * 1e-3) / 1e12
-    roofline["alu"] = {"unit": "T lane-ops/s", "achieved": round(ach_ops, 2),
-                       "peak": round(peak_ops, 2), "frac": round(ach_ops / peak_ops, 4),
-                       "lane_ops_per_launch": W.alu_ops[dom], "sm_mhz": mhz,
-                       "model": W.alu_model[dom]}
-    for n in names:
-        per_op[n]["kernel"] = W.kernel[n]
-        per_op[n]["alu_frac"] = round(W.alu_ops[n] / (op_ms[n] * 1e-3) / 1e12 / peak_ops, 4)
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    counters = {}
+    prof = os.path.join(ROOT, "profiles", "kernel_counters.json")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
-                roofline["traffic"] = json.load(f).get(dom)
+                counters = json.load(f).get("ops", {})
         except (OSError, ValueError):
-            pass
+            counters = {}
+
+    def alu_lane_ops(n):
+        c = counters.get(n, {})
+        return (int(c["alu_warp_inst"]) * 32, "measured") if "alu_warp_inst" in c else (
+            W.alu_ops[n], "model")
+
+    lane_ops, src = alu_lane_ops(dom)
+    ach_ops = lane_ops / (op_ms[dom] * 1e-3) / 1e12
+    roofline["alu"] = {"unit": "T lane-ops/s", "achieved": round(ach_ops, 2),
+                       "peak": round(peak_ops, 2), "frac": round(ach_ops / peak_ops, 4),
+                       "lane_ops_per_launch": lane_ops, "lane_ops_source": src,
+                       "model_lane_ops_per_launch": W.alu_ops[dom], "sm_mhz": mhz,
+                       "model": W.alu_model[dom]}
+    for n in names:
+        per_op[n]["kernel"] = W.kernel[n]
+        lo, src = alu_lane_ops(n)
+        per_op[n]["alu_frac"] = round(lo / (op_ms[n] * 1e-3) / 1e12 / peak_ops, 4)
+        per_op[n]["alu_source"] = src
+        if "dram_bytes" in counters.get(n, {}):
+            per_op[n]["traffic"] = int(counters[n]["dram_bytes"])
+    if "dram_bytes" in counters.get(dom, {}):
+        roofline["traffic"] = int(counters[dom]["dram_bytes"])
 
     # the end-to-end run comes before the extra rows: their handles, run-time
     # compilations and allocations stay out of its pipelined copy timing
@@ -1069,9 +1086,10 @@ def run_batched(torch, P, inputs, args, dev, stream):
         "plain_ms": round(res["plain"][0], 3),
         "plain_wall_ms": round(res["plain"][1], 3),
         "speedup": round(res["plain"][0] / res["batched"][0], 3),
-        "launches": {"batched": 1, "plain": len(ops)},
+        "launches": {"batched": 1 + info["bitsliced_launches"], "plain": len(ops)},
         "tuned": {"work_bytes": best[0], "ctas_per_sm": best[1], "tune_s": round(tune_s, 2),
-                  "items": info["items"], "ctas": info["ctas"]},
+                  "items": info["items"], "ctas": info["ctas"],
+                  "bitsliced_launches": info["bitsliced_launches"]},
         "l2": "not flushed (working set far larger than L2)",
     }
     if scale_note:

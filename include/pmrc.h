@@ -383,7 +383,11 @@ int pmrc_batch_launch(pmrc_batch *batch, pmrc_stream_t stream);
 int pmrc_batch_tune(pmrc_batch *batch, pmrc_stream_t stream, int *best_out);
 
 /* info_out[8] = {stripes, work items, CTAs, work_bytes, ctas_per_sm,
- * user bytes per launch, 0 (unused), shared memory bytes per CTA}. */
+ * user bytes per launch, bitsliced encode launches, shared memory bytes per
+ * CTA}.  Encodes of at least 4 MiB of data on codes with a built-in
+ * bitsliced kernel (16-byte aligned blocks) run as their own launches of that
+ * kernel in the batch's graph, after the persistent kernel (which takes
+ * their ragged tails and every other stripe). */
 int pmrc_batch_info(const pmrc_batch *batch, int64_t *info_out);
 
 /* ---- serving -------------------------------------------------------------

@@ -432,7 +432,7 @@ def pmrc_batch_info(batch) -> dict:
     out = (ctypes.c_int64 * 8)()
     _check(lib().pmrc_batch_info(batch, out), "pmrc_batch_info")
     return dict(zip(("stripes", "items", "ctas", "work_bytes", "ctas_per_sm", "user_bytes",
-                     "unused", "smem_bytes"), list(out)))
+                     "bitsliced_launches", "smem_bytes"), list(out)))
 
 
 class Batch:

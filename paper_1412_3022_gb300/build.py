@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpmrc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["region.cu", "bitslice.cu", "repair.cu", "batch.cu", "serve.cu", "plan.cpp",
+SOURCES = ["bitslice_k16.cu", "bitslice_k12.cu", "region.cu", "bitslice.cu", "repair.cu", "batch.cu", "serve.cu", "plan.cpp",
            "code.cpp", "code16.cpp", "specific.cpp", "bs_emit.cpp", "jit.cpp", "api.cpp"]
 
 
@@ -56,7 +56,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"g++ failed on gen_bitslice:\n{r.stdout}\n{r.stderr}")
-    r = subprocess.run([gen, os.path.join(BUILD, "bitslice_gen.cuh")], capture_output=True, text=True)
+    r = subprocess.run([gen, os.path.join(BUILD, "bitslice_gen.cuh"),
+                        os.path.join(BUILD, "bitslice_gen_k12.cuh"),
+                        os.path.join(BUILD, "bitslice_gen_k16.cuh")], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"gen_bitslice failed:\n{r.stdout}\n{r.stderr}")
     # 2. the bitsliced device code as a string, for run-time compilation

@@ -25,6 +25,7 @@
 #include "../../include/pmrc.h"
 #include "api_internal.h"
 #include "batch_internal.h"
+#include "bitslice.h"
 #include "device_info.h"
 #include "trace.h"
 #include "gf256.h"
@@ -151,6 +152,23 @@ int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const
   s.work = s.plan->nnz;
   finish_stripe(s);
   return kOk;
+}
+
+bool bitsliced_encode_split(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                            size_t nbytes, BitslicedEncode &e) {
+  if (c->m.w != 8 || c->bs_id < 0 || c->encode_kernel == PMRC_KERNEL_GENERIC || nbytes < 32 ||
+      (size_t)c->m.K * nbytes < kBatchBitslicedMinBytes || !c->encode->parts.empty())
+    return false;
+  const Plan &P = *c->encode;
+  for (int i = 0; i < P.nin; i++)
+    if (!data[i] || (uintptr_t)data[i] % 16) return false;
+  for (int j = 0; j < P.nout; j++)
+    if (!out[j] || (uintptr_t)out[j] % 16) return false;
+  e.id = c->bs_id;
+  e.in.assign(data, data + P.nin);
+  e.out.assign(out, out + P.nout);
+  e.nbytes = nbytes & ~(size_t)31;
+  return true;
 }
 
 int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
@@ -317,7 +335,9 @@ cudaError_t worklist_launch(const WorkItem *d_items, int nitems, uint8_t *const 
 using namespace pmrc;
 
 struct pmrc_batch {
-  std::vector<WorkStripe> stripes;
+  std::vector<WorkStripe> stripes;        // items of the batched kernel
+  std::vector<BitslicedEncode> bitsliced;  // large encodes: own launches in the graph
+  int count = 0;                           // stripes added
   bool built = false;
   // device state
   uint8_t **d_ptrs = nullptr;
@@ -389,8 +409,18 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   std::vector<const WorkStripe *> sp;
   for (auto &s : b->stripes) sp.push_back(&s);
   WorkList wl;
-  int rc = worklist_build(sp, work_bytes, wl, err);
-  if (rc) return rc;
+  if (!sp.empty()) {
+    int rc = worklist_build(sp, work_bytes, wl, err);
+    if (rc) return rc;
+  }
+  // the bitsliced kernels' shared-memory setting is made before the capture
+  for (const auto &be : b->bitsliced) {
+    const cudaError_t pe = bitslice_prepare(be.id);
+    if (pe != cudaSuccess) {
+      err = std::string("bitsliced encode setup: ") + cudaGetErrorString(pe);
+      return kECuda;
+    }
+  }
   e = cudaMalloc(&b->d_ptrs, std::max<size_t>(1, wl.ptrs.size()) * sizeof(uint8_t *));
   if (e == cudaSuccess && !wl.ptrs.empty())
     e = cudaMemcpy(b->d_ptrs, wl.ptrs.data(), wl.ptrs.size() * sizeof(uint8_t *),
@@ -410,12 +440,18 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   const int per_sm = std::max(1, std::min(ctas_per_sm, worklist_ctas_per_sm(wl.smem)));
   b->grid = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((int64_t)sms * per_sm, std::max(1, b->nitems)));
-  // graph: counter reset + persistent kernel
+  // graph: counter reset + persistent kernel, then one launch of the
+  // built-in bitsliced kernel per large encode
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t le = worklist_launch(b->d_items, b->nitems, b->d_ptrs, b->d_counter, b->grid,
-                                     b->smem, b->cap);
+    cudaError_t le = cudaSuccess;
+    if (b->nitems > 0)
+      le = worklist_launch(b->d_items, b->nitems, b->d_ptrs, b->d_counter, b->grid, b->smem,
+                           b->cap);
+    for (const auto &be : b->bitsliced)
+      if (le == cudaSuccess)
+        le = bitslice_launch(be.id, be.in.data(), be.out.data(), be.nbytes, b->cap);
     e = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) e = le;
   }
@@ -434,7 +470,7 @@ int add(pmrc_batch *b, int rc, WorkStripe &&s, const std::string &err) {
   if (rc) return bfail(rc, err);
   b->user_bytes += s.user_bytes;
   b->stripes.push_back(std::move(s));
-  return (int)b->stripes.size() - 1;
+  return b->count++;
 }
 
 const char *kErrBuilt = "batch already built: create a new batch to add stripes";
@@ -457,6 +493,22 @@ int pmrc_batch_add_encode(pmrc_batch *b, const pmrc_code *c, const uint8_t *cons
   if (b->built) return bfail(PMRC_EBUSY, kErrBuilt);
   WorkStripe s;
   std::string err;
+  BitslicedEncode be;
+  if (bitsliced_encode_split(c, data, out, nbytes, be)) {
+    if (be.nbytes < nbytes) {  // the ragged tail joins the batched kernel's items
+      std::vector<const uint8_t *> in2(be.in.size());
+      std::vector<uint8_t *> out2(be.out.size());
+      for (size_t i = 0; i < in2.size(); i++) in2[i] = be.in[i] + be.nbytes;
+      for (size_t j = 0; j < out2.size(); j++) out2[j] = be.out[j] + be.nbytes;
+      int rc = stripe_encode(c, in2.data(), out2.data(), nbytes - be.nbytes, s, err);
+      if (rc) return bfail(rc, err);
+      s.user_bytes = 0;  // counted with the stripe below
+      b->stripes.push_back(std::move(s));
+    }
+    b->user_bytes += (int64_t)c->m.K * nbytes;
+    b->bitsliced.push_back(std::move(be));
+    return b->count++;
+  }
   int rc = stripe_encode(c, data, out, nbytes, s, err);
   return add(b, rc, std::move(s), err);
 }
@@ -485,7 +537,7 @@ int pmrc_batch_add_decode(pmrc_batch *b, const pmrc_code *c, const int *nodes,
 int pmrc_batch_build(pmrc_batch *b, int work_bytes, int ctas_per_sm) {
   PMRC_TRACE("pmrc_batch_build");
   if (!b) return bfail(PMRC_EINVAL, "NULL batch");
-  if (b->stripes.empty()) return bfail(PMRC_EINVAL, "empty batch");
+  if (b->stripes.empty() && b->bitsliced.empty()) return bfail(PMRC_EINVAL, "empty batch");
   if (work_bytes <= 0 || ctas_per_sm <= 0) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(signature(b));
@@ -561,13 +613,13 @@ int pmrc_batch_tune(pmrc_batch *b, pmrc_stream_t stream, int *best_out) {
 
 int pmrc_batch_info(const pmrc_batch *b, int64_t *info) {
   if (!b || !info) return bfail(PMRC_EINVAL, "NULL argument");
-  info[0] = (int64_t)b->stripes.size();
+  info[0] = b->count;
   info[1] = b->nitems;
   info[2] = b->grid;
   info[3] = b->work_bytes;
   info[4] = b->ctas_per_sm;
   info[5] = b->user_bytes;
-  info[6] = 0;
+  info[6] = (int64_t)b->bitsliced.size();
   info[7] = (int64_t)b->smem;
   return PMRC_OK;
 }

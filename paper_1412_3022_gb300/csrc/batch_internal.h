@@ -29,6 +29,27 @@ struct WorkStripe {
 
 int stripe_encode(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
                   size_t nbytes, WorkStripe &s, std::string &err);
+
+// An encode large enough to run as its own launch of the code's built-in
+// bitsliced kernel (beside the batched kernel, in the same graph or
+// iteration): bytes [0, nbytes) of every block, nbytes a multiple of 32;
+// a ragged tail of the stripe stays with the batched kernel.
+struct BitslicedEncode {
+  int id = -1;  // built-in kernel (bitslice_find)
+  std::vector<const uint8_t *> in;
+  std::vector<uint8_t *> out;
+  size_t nbytes = 0;
+};
+
+// Stripes of at least this many data bytes (k alpha x B) take the bitsliced
+// launch: below it the batched kernel's fine-grained items beat a launch.
+constexpr size_t kBatchBitslicedMinBytes = 4u << 20;
+
+// Whether an encode of c over nbytes-byte blocks takes its bitsliced kernel
+// (built-in kernel, GF(2^8), at least kBatchBitslicedMinBytes of data,
+// every pointer non-NULL and 16-byte aligned); fills e when it does.
+bool bitsliced_encode_split(const pmrc_code *c, const uint8_t *const *data, uint8_t *const *out,
+                            size_t nbytes, BitslicedEncode &e);
 int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *const *blocks,
                   uint8_t *const *out, size_t nbytes, WorkStripe &s, std::string &err);
 int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,

@@ -48,7 +48,10 @@
 #include "jit.h"
 
 namespace pmrc {
-namespace {
+// a named namespace: the built-in kernels of the large codes are defined in
+// translation units of their own (bitslice_k12.cu, bitslice_k16.cu) over the
+// same launch-argument type
+namespace bsk {
 
 #include "bitslice_dev.cuh"
 
@@ -63,7 +66,9 @@ struct BsKernel {
 
 #include "bitslice_gen.cuh"
 
-}  // namespace
+}  // namespace bsk
+
+using namespace bsk;
 
 uint64_t bitslice_checksum(const uint8_t *m, size_t len) {
   uint64_t h = 1469598103934665603ull;
@@ -130,6 +135,11 @@ std::atomic<uint64_t> g_static_smem_set[kMaxDevices];
 #include "bitslice_dev_src.inc"
 
 }  // namespace
+
+cudaError_t bitslice_prepare(int id) {
+  if (id < 0 || id >= kBsNumKernels) return cudaErrorInvalidValue;
+  return allow_max_smem(reinterpret_cast<const void *>(kBsKernels[id].fn), g_static_smem_set, id);
+}
 
 cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
                             cudaStream_t stream) {

@@ -29,6 +29,11 @@ cudaError_t bitslice_launch(int id, const uint8_t *const *in, uint8_t *const *ou
 
 int bitslice_max_pointers();
 
+// Makes the shared-memory setting of built-in kernel `id` on the current
+// device (once), so that later launches -- inside a stream capture too --
+// need no attribute call.
+cudaError_t bitslice_prepare(int id);
+
 
 // A bitsliced kernel compiled at run time (NVRTC) for a matrix known only
 // then: the rows of a reconstruction or a newcomer's apply (consecutive rows

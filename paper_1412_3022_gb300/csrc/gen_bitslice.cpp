@@ -15,7 +15,7 @@
 //
 // The output is a header of __device__ functions, one per block, plus a
 // table mapping (n, k, construction, form) to its kernel.  Usage:
-//   gen_bitslice <out.cuh>
+//   gen_bitslice <main.cuh> <k12.cuh> <k16.cuh>
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -35,11 +35,17 @@ struct Spec {
 };
 
 // the codes of the benchmarked workloads (n = 2k, d = 2k-2 for the PM codes;
-// construction 2 is PM-MBR, 3 the Reed-Solomon baseline with d = k)
+// construction 2 is PM-MBR, 3 the Reed-Solomon baseline with d = k).  Group 0
+// goes to the main header; the two large sparse systematic codes (k = 12 and
+// 16, thousands of coefficients each) get headers of their own, compiled as
+// separate translation units in parallel with the rest.
 const Spec kSpecs[] = {
     {16, 8, 1, 1, 14}, {16, 8, 0, 0, 14}, {8, 4, 1, 1, 6}, {6, 3, 1, 1, 4},
-    {6, 3, 0, 0, 4},   {16, 8, 2, 1, 14}, {16, 8, 3, 1, 8},
+    {6, 3, 0, 0, 4},   {16, 8, 2, 1, 14}, {16, 8, 3, 1, 8}, {24, 12, 1, 1, 22},
+    {32, 16, 1, 1, 30},
 };
+const int kGroup[] = {0, 0, 0, 0, 0, 0, 0, 1, 2};
+constexpr int kGroups = 3;
 
 
 uint64_t fnv(const std::vector<uint8_t> &v) {
@@ -54,16 +60,22 @@ uint64_t fnv(const std::vector<uint8_t> &v) {
 }  // namespace
 
 int main(int argc, char **argv) {
-  if (argc != 2) {
-    fprintf(stderr, "usage: gen_bitslice <out.cuh>\n");
+  if (argc != 1 + kGroups) {
+    fprintf(stderr, "usage: gen_bitslice <main.cuh> <group1.cuh> <group2.cuh>\n");
     return 2;
   }
-  FILE *f = fopen(argv[1], "w");
-  if (!f) return 1;
-  fprintf(f, "// generated by gen_bitslice.cpp -- do not edit\n#pragma once\n\n");
+  std::vector<FILE *> out(kGroups);
+  for (int g = 0; g < kGroups; g++) {
+    out[g] = fopen(argv[1 + g], "w");
+    if (!out[g]) return 1;
+    fprintf(out[g], "// generated by gen_bitslice.cpp -- do not edit\n#pragma once\n\n");
+  }
+  FILE *f = out[0];
   std::string table;
   int nspec = 0;
-  for (const Spec &s : kSpecs) {
+  for (size_t si = 0; si < sizeof kSpecs / sizeof kSpecs[0]; si++) {
+    const Spec &s = kSpecs[si];
+    FILE *fg = out[kGroup[si]];
     CodeMatrices c;
     std::string err;
     if (build_code(s.n, s.k, s.d, s.construction, s.form, c, err)) {
@@ -88,10 +100,13 @@ int main(int argc, char **argv) {
     const std::string name = "bs_n" + std::to_string(s.n) + "_k" + std::to_string(s.k) + "_c" +
                              std::to_string(s.construction) + "_f" + std::to_string(s.form);
     const BsEmitted em = bs_emit_kernel(M.data(), rows, K, blks, name, false);
-    fputs(em.code.c_str(), f);
-    fprintf(f, "static const int %s_cost[] = {", name.c_str());
-    for (size_t i = 0; i < em.cost.size(); i++) fprintf(f, "%s%d", i ? ", " : "", em.cost[i]);
-    fprintf(f, "};\n\n");
+    fputs(em.code.c_str(), fg);
+    fprintf(fg, "extern const int %s_cost[] = {", name.c_str());
+    for (size_t i = 0; i < em.cost.size(); i++) fprintf(fg, "%s%d", i ? ", " : "", em.cost[i]);
+    fprintf(fg, "};\n\n");
+    if (kGroup[si] != 0)  // defined in its own translation unit
+      fprintf(f, "__global__ void %s(const __grid_constant__ BsArgs a);\nextern const int %s_cost[];\n\n",
+              name.c_str(), name.c_str());
     const long long xors = em.xors;
     char buf[256];
     snprintf(buf, sizeof buf, "    {%d, %d, %d, %d, %zu, %d, %d, 0x%016llxull, %lldll, %s, %s_cost},\n",
@@ -102,6 +117,6 @@ int main(int argc, char **argv) {
   }
   fprintf(f, "static const BsKernel kBsKernels[] = {\n%s};\nstatic const int kBsNumKernels = %d;\n",
           table.c_str(), nspec);
-  fclose(f);
+  for (FILE *fg : out) fclose(fg);
   return 0;
 }

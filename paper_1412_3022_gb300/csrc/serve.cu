@@ -40,6 +40,7 @@
 #include "../../include/pmrc.h"
 #include "api_internal.h"
 #include "batch_internal.h"
+#include "bitslice.h"
 
 using namespace pmrc;
 
@@ -195,6 +196,7 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
   std::vector<WorkStripe> stripes(ready.size());
   std::vector<const WorkStripe *> sp;
   std::vector<Req *> ok;
+  std::vector<BitslicedEncode> bitsliced;  // large encodes: own launches after the kernel
   for (size_t i = 0; i < ready.size(); i++) {
     Req *r = ready[i];
     std::vector<const uint8_t *> in;
@@ -202,6 +204,24 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
     block_ptrs(this, r, in, out);
     std::string e2;
     int rc;
+    BitslicedEncode be;
+    if (r->op == PMRC_OP_ENCODE && bitsliced_encode_split(r->code, in.data(), out.data(), r->B, be)) {
+      rc = kOk;
+      if (be.nbytes < r->B) {  // the ragged tail goes with the batched kernel
+        for (auto &p : in) p += be.nbytes;
+        for (auto &p : out) p += be.nbytes;
+        rc = stripe_encode(r->code, in.data(), out.data(), r->B - be.nbytes, stripes[i], e2);
+        if (!rc) sp.push_back(&stripes[i]);
+      }
+      if (rc) {
+        r->status = rc;
+        r->state = kFailed;
+        continue;
+      }
+      bitsliced.push_back(std::move(be));
+      ok.push_back(r);
+      continue;
+    }
     if (r->op == PMRC_OP_ENCODE)
       rc = stripe_encode(r->code, in.data(), out.data(), r->B, stripes[i], e2);
     else if (r->op == PMRC_OP_REPAIR)
@@ -239,6 +259,18 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
   Iteration it;
   it.buf = b;
   cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming);
+  for (const auto &be : bitsliced) {  // attribute set outside the launch sequence
+    const cudaError_t pe = bitslice_prepare(be.id);
+    if (pe != cudaSuccess) {
+      err = std::string("serving bitsliced setup: ") + cudaGetErrorString(pe);
+      for (Req *r : ok) {
+        r->status = PMRC_ECUDA;
+        r->state = kFailed;
+      }
+      ok.clear();
+      bitsliced.clear();
+    }
+  }
   if (!ok.empty() && !wl.items.empty()) {
     memcpy(h_items[b], wl.items.data(), wl.items.size() * sizeof(WorkItem));
     memcpy(h_ptrs[b], wl.ptrs.data(), wl.ptrs.size() * sizeof(uint8_t *));
@@ -261,8 +293,21 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
       ok.clear();
     }
   }
+  if (!ok.empty())
+    for (const auto &be : bitsliced) {
+      const cudaError_t e = bitslice_launch(be.id, be.in.data(), be.out.data(), be.nbytes, s_comp);
+      if (e != cudaSuccess) {
+        err = std::string("serving bitsliced launch: ") + cudaGetErrorString(e);
+        for (Req *r : ok) {
+          r->status = PMRC_ECUDA;
+          r->state = kFailed;
+        }
+        ok.clear();
+        break;
+      }
+    }
   cudaEventRecord(it.done, s_comp);
-  // outputs go back as soon as the iteration's kernel is done
+  // outputs go back as soon as the iteration's kernels are done
   cudaStreamWaitEvent(s_out, it.done, 0);
   for (Req *r : ok) {
     if (!r->device)

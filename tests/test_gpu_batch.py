@@ -163,3 +163,35 @@ def test_batch_rejects_adds_after_build_and_bad_args():
     with pytest.raises(P.PMRCError) as e:
         b2.add_decode(c, [0, 1, 1, 2], [0] * 12, [0] * 12, 64)
     assert e.value.rc == P.PMRC_EINVAL
+
+
+def test_batch_large_encodes_take_bitsliced_launches_with_ragged_tails():
+    """Encodes of at least 4 MiB of data on codes with a built-in bitsliced
+    kernel run as their own launches in the batch's graph (their last
+    bytes, beyond a multiple of 32, with the persistent kernel); every
+    stripe equals the oracle and the plain call, whatever mix of launches."""
+    cases = [(8, 80000 + 16), (8, 80000 + 32), (4, 360000 + 16), (16, 20000 + 16), (12, 40000),
+             (8, 4000)]                        # the last one stays in the persistent kernel
+    stripes = []
+    b = P.Batch()
+    for s, (k, nb) in enumerate(cases):
+        n, a = 2 * k, k - 1
+        c = P.Code(n, k, 1, 1)
+        X = inputs.blocks(k * a, nb, seed=900 + s)
+        st = {"c": c, "k": k, "nb": nb, "X": X, "in": dev(X),
+              "out": torch.full(((n - k) * a, nb), 0xA5, dtype=torch.uint8, device="cuda")}
+        b.add_encode(c, [st["in"][i] for i in range(k * a)],
+                     [st["out"][i] for i in range(st["out"].shape[0])], nb)
+        stripes.append(st)
+    b.build()
+    info = b.info()
+    assert info["stripes"] == len(cases) and info["bitsliced_launches"] == 5
+    for _ in range(2):
+        for st in stripes:
+            st["out"].fill_(0xA5)
+        b.launch()
+        torch.cuda.synchronize()
+        for st in stripes:
+            k = st["k"]
+            want = O.encode(2 * k, k, 1, True, st["X"])[k * (k - 1):]
+            assert np.array_equal(st["out"].cpu().numpy(), want), (k, st["nb"])

@@ -137,6 +137,7 @@ def test_batched_mix_every_stripe_at_the_stated_distribution():
         else:
             b.add_repair(st["c"], st["f"], st["H"], ins(st), outs(st), st["nb"])
     b.build()
+    assert b.info()["bitsliced_launches"] > 0   # the large encodes run as bitsliced launches
     b.launch()
     alone = []
     for st in stripes:

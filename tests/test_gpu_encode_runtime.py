@@ -29,7 +29,7 @@ def encode(c, X, nbytes, shift=0):
 
 # PM-MSR codes of n = 2k and other n, both constructions and forms; the
 # vanilla k = 12 generator takes 33 blocks and 396 block pointers
-MSR = [(24, 12, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC), (20, 10, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC),
+MSR = [(14, 7, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC), (20, 10, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC),
        (12, 6, P.PMRC_VANILLA, P.PMRC_SYSTEMATIC), (24, 12, P.PMRC_VANILLA, P.PMRC_NONSYSTEMATIC),
        (11, 5, P.PMRC_SPARSE, P.PMRC_NONSYSTEMATIC)]
 

@@ -358,7 +358,8 @@ def test_gpu_calls_reject_bad_arguments_without_launching():
     assert e.value.rc == P.PMRC_EINVAL
 
 
-BITSLICED_CODES = [(16, 8, 1, 1), (16, 8, 0, 0), (8, 4, 1, 1), (6, 3, 1, 1), (6, 3, 0, 0)]
+BITSLICED_CODES = [(16, 8, 1, 1), (16, 8, 0, 0), (8, 4, 1, 1), (6, 3, 1, 1), (6, 3, 0, 0),
+                   (24, 12, 1, 1), (32, 16, 1, 1)]
 
 
 @pytest.mark.parametrize("nbytes", [32, 33, 8192, 8192 + 32 + 7, 3 * 8192 + 16, 100000])
