@@ -395,12 +395,17 @@ int pmrc_batch_info(const pmrc_batch *batch, int64_t *info_out);
  * requests in arrival order while a slot is free and the device budget has
  * room for the request's inputs and outputs, copies their inputs in while
  * the previous iteration computes, runs every request whose inputs have
- * landed in one persistent launch (the batched kernel), and copies results
- * back, recording submit-to-completion latency.  Each request gives the same
- * bytes as the corresponding single call.  Requests use HOST buffers (make
- * them pinned, cudaMallocHost / cudaHostRegister, so the copies run
- * asynchronously, and keep them alive until the request is finished), or
- * device blocks with PMRC_REQ_DEVICE. */
+ * landed in one persistent launch (the batched kernel, plus the built-in
+ * bitsliced kernel for encodes of at least 4 MiB of data), and copies
+ * results back, recording submit-to-completion latency.  Copies run on four
+ * streams per direction, each copy on the one with the fewest bytes queued;
+ * the persistent kernel reads its work list from pinned host memory in
+ * place.  Each request gives the same bytes as the corresponding single
+ * call.  Requests use HOST buffers (make them pinned, cudaMallocHost /
+ * cudaHostRegister, so the copies run asynchronously, and keep them alive
+ * until the request is finished), or device blocks with PMRC_REQ_DEVICE.
+ * The coefficient plan of a request is built (or found) and uploaded at
+ * submission, on the caller's thread. */
 typedef struct pmrc_server pmrc_server;
 
 enum { PMRC_OP_ENCODE = 0, PMRC_OP_REPAIR = 1, PMRC_OP_DECODE = 2 };

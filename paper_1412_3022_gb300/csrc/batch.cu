@@ -3,7 +3,9 @@
 //
 // Every stripe operation is cut into work items: (dense block of its plan x
 // range of 4 KiB byte tiles) for encode and decode, (fused repair x range of
-// tiles) for repair.  A persistent grid pulls items from an atomic counter
+// 1 KiB tiles) for repair; no item costs more than a fixed share of the
+// list, so a stripe with short blocks and many products still spreads over
+// the grid.  A persistent grid pulls items from an atomic counter
 // (reset by a memset node in the same graph), stages the item's split tables
 // in shared memory and runs the same inner loops as the single-stripe
 // kernels (region_dev.cuh, repair_dev.cuh).  Items are listed biggest stripe
@@ -14,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -43,21 +46,30 @@ struct BatchArgs {
   int nitems;
   uint8_t *const *ptrs;  // pointer table of the launch
   unsigned *counter;
+  uint32_t ptr_area;     // leading shared-memory bytes: the item's stripe pointers
   MulConsts k;
 };
 
 template <int R>
 __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchArgs a) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  extern __shared__ __align__(16) uint8_t dsm[];
   __shared__ int s_item;
+  __shared__ uint4 s_w[sizeof(WorkItem) / 16];
   const MulConsts k = a.k;
+  // the item's stripe pointers stay in shared memory for the whole item:
+  // the list and the pointer table are read once per item, wherever they sit
+  uint8_t **ptrs = reinterpret_cast<uint8_t **>(dsm);
+  uint8_t *const smem = dsm + a.ptr_area;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
     __syncthreads();
     const int it = s_item;
     if (it >= a.nitems) break;
-    const WorkItem w = a.items[it];
-    uint8_t *const *ptrs = a.ptrs + w.ptr_off;
+    if (threadIdx.x < sizeof(WorkItem) / 16)
+      s_w[threadIdx.x] = reinterpret_cast<const uint4 *>(a.items + it)[threadIdx.x];
+    __syncthreads();
+    const WorkItem w = *reinterpret_cast<const WorkItem *>(s_w);
+    for (uint32_t i = threadIdx.x; i < w.nptrs; i += kThreads) ptrs[i] = a.ptrs[w.ptr_off + i];
     const bool vec = w.aligned != 0;
     if (w.type == 0) {
       const BlockDesc d = reinterpret_cast<const BlockDesc *>(w.image)[w.block];
@@ -107,9 +119,9 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
       }
       if (threadIdx.x < 16) s_nz[threadIdx.x] = hp->nzidx[threadIdx.x];
       __syncthreads();
-      const uint64_t span_end = (uint64_t)(w.tile0 + w.ntiles) * kThreads * kVec;
+      const uint64_t span_end = (uint64_t)(w.tile0 + w.ntiles) * kRepTile;
       const uint64_t end = span_end < w.nbytes ? span_end : w.nbytes;
-      for (uint64_t t = (uint64_t)w.tile0 * kThreads * kVec; t < end; t += kRepTile)
+      for (uint64_t t = (uint64_t)w.tile0 * kRepTile; t < end; t += kRepTile)
         fused_repair_tile<0>(ptrs, t, w.nbytes, vec, d, alpha, nz, direct, s_nz, t1a, t1b, t2a,
                              t2b, rl, proj, k);
     }
@@ -253,30 +265,51 @@ int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *no
   return kOk;
 }
 
-int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_bytes, WorkList &wl,
-                   std::string &err) {
-  const uint64_t tile = (uint64_t)kThreads * kVec;
-  const uint32_t tiles_per_item = (uint32_t)std::max<uint64_t>(1, (uint64_t)work_bytes / tile);
+int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_bytes,
+                   int target_items, WorkList &wl, std::string &err) {
+  const uint64_t tile = (uint64_t)kThreads * kVec;  // region items: 4 KiB tiles
+  const uint64_t rtile = (uint64_t)kRepTile;        // fused repair items: 1 KiB tiles
   std::vector<const WorkStripe *> order(stripes);
   std::stable_sort(order.begin(), order.end(), [](const WorkStripe *x, const WorkStripe *y) {
     return (double)x->work * x->nbytes > (double)y->work * y->nbytes;
   });
+  // No item may cost more than 1/target_items of the whole list (products
+  // per item = bytes of its range x products per byte column): a stripe
+  // with few byte columns but many products (a large-k repair or
+  // reconstruction over short blocks) is cut into finer ranges, down to one
+  // tile, so that it spreads over the grid instead of a few CTAs.
+  double total = 0;
+  for (const WorkStripe *S : order) total += (double)S->work * (double)S->nbytes;
+  const double cap = target_items > 0 ? total / target_items : 0;
   for (const WorkStripe *S : order) {
     if (S->nbytes == 0) continue;
     const uint32_t base = (uint32_t)wl.ptrs.size();
     wl.ptrs.insert(wl.ptrs.end(), S->ptrs.begin(), S->ptrs.end());
     wl.user_bytes += S->user_bytes;
-    const uint32_t ntiles = (uint32_t)((S->nbytes + tile - 1) / tile);
+    const uint64_t unit = S->type == 0 ? tile : rtile;
+    const uint32_t nunits = (uint32_t)((S->nbytes + unit - 1) / unit);
+    uint32_t span = (uint32_t)std::max<uint64_t>(1, (uint64_t)work_bytes / unit);
+    double per_unit = (double)unit * (double)S->work;  // products of one unit of the stripe
+    if (S->type == 0) {
+      size_t widest = 1;
+      for (const PlanBlock &b : S->plan->blocks)
+        widest = std::max(widest, b.inputs.size() * b.rows.size());
+      per_unit = (double)unit * (double)widest;
+    }
+    if (cap > 0 && per_unit * span > cap)
+      span = (uint32_t)std::max(1.0, std::floor(cap / per_unit));
     const void *image = nullptr;
     int rc = S->type == 0 ? S->plan->device_image(&image, err) : S->fplan->device_image(&image, err);
     if (rc) return rc;
-    for (uint32_t t0 = 0; t0 < ntiles; t0 += tiles_per_item) {
+    wl.ptr_area = std::max(wl.ptr_area, (S->ptrs.size() * sizeof(uint8_t *) + 15) & ~(size_t)15);
+    for (uint32_t t0 = 0; t0 < nunits; t0 += span) {
       WorkItem w{};
       w.image = static_cast<const uint8_t *>(image);
       w.nbytes = S->nbytes;
       w.ptr_off = base;
+      w.nptrs = (uint32_t)S->ptrs.size();
       w.tile0 = t0;
-      w.ntiles = std::min(tiles_per_item, ntiles - t0);
+      w.ntiles = std::min(span, nunits - t0);
       w.aligned = S->aligned ? 1 : 0;
       if (S->type == 0) {
         const Plan &P = *S->plan;
@@ -298,6 +331,7 @@ int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_byte
       }
     }
   }
+  wl.smem += wl.ptr_area;
   return kOk;
 }
 
@@ -311,18 +345,20 @@ int worklist_ctas_per_sm(size_t smem) {
   return fit < 1 ? 1 : fit;
 }
 
-cudaError_t worklist_launch(const WorkItem *d_items, int nitems, uint8_t *const *d_ptrs,
-                            unsigned *d_counter, unsigned grid, size_t smem, cudaStream_t stream) {
+cudaError_t worklist_launch(const WorkItem *items, int nitems, uint8_t *const *ptrs,
+                            unsigned *d_counter, unsigned grid, size_t smem, size_t ptr_area,
+                            cudaStream_t stream) {
   if (smem > 48 * 1024) {
     const cudaError_t e =
         allow_max_smem(reinterpret_cast<const void *>(batch_kernel<kBatchR>), g_batch_smem_set, 0);
     if (e != cudaSuccess) return e;
   }
   BatchArgs args;
-  args.items = d_items;
+  args.items = items;
   args.nitems = nitems;
-  args.ptrs = d_ptrs;
+  args.ptrs = ptrs;
   args.counter = d_counter;
+  args.ptr_area = (uint32_t)ptr_area;
   args.k = MulConsts{2u, 16u, 1u << 16, 1u << 26, 1u << 29, 1u << 30};
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
@@ -345,7 +381,7 @@ struct pmrc_batch {
   unsigned *d_counter = nullptr;
   int nitems = 0;
   unsigned grid = 0;
-  size_t smem = 0;
+  size_t smem = 0, ptr_area = 0;
   int work_bytes = 0, ctas_per_sm = 0;
   int64_t user_bytes = 0;
   cudaStream_t cap = nullptr;
@@ -410,7 +446,7 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   for (auto &s : b->stripes) sp.push_back(&s);
   WorkList wl;
   if (!sp.empty()) {
-    int rc = worklist_build(sp, work_bytes, wl, err);
+    int rc = worklist_build(sp, work_bytes, kItemsPerCta * sms * std::max(1, ctas_per_sm), wl, err);
     if (rc) return rc;
   }
   // the bitsliced kernels' shared-memory setting is made before the capture
@@ -437,6 +473,7 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   }
   b->nitems = (int)wl.items.size();
   b->smem = wl.smem;
+  b->ptr_area = wl.ptr_area;
   const int per_sm = std::max(1, std::min(ctas_per_sm, worklist_ctas_per_sm(wl.smem)));
   b->grid = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((int64_t)sms * per_sm, std::max(1, b->nitems)));
@@ -447,7 +484,7 @@ int build_device(pmrc_batch *b, int work_bytes, int ctas_per_sm, std::string &er
   if (e == cudaSuccess) {
     cudaError_t le = cudaSuccess;
     if (b->nitems > 0)
-      le = worklist_launch(b->d_items, b->nitems, b->d_ptrs, b->d_counter, b->grid, b->smem,
+      le = worklist_launch(b->d_items, b->nitems, b->d_ptrs, b->d_counter, b->grid, b->smem, b->ptr_area,
                            b->cap);
     for (const auto &be : b->bitsliced)
       if (le == cudaSuccess)

@@ -55,37 +55,54 @@ int stripe_repair(const pmrc_code *c, int f, const int *helpers, const uint8_t *
 int stripe_decode(const pmrc_code *c, const int *nodes, const uint8_t *const *node_blocks,
                   uint8_t *const *data_out, size_t nbytes, WorkStripe &s, std::string &err);
 
-// Device work item (16-byte aligned, position independent: pointers are
-// offsets into the launch's pointer table).
-struct WorkItem {
+// Device work item (position independent: pointers are offsets into the
+// launch's pointer table).  The kernel reads it as four 16-byte words, so
+// the list may sit in device memory or in mapped pinned host memory.
+struct alignas(16) WorkItem {
   const uint8_t *image;    // region plan image or fused repair image (device)
   uint64_t nbytes;         // block size of the stripe
   uint32_t ptr_off;        // first pointer of the stripe in the table
-  uint32_t tile0, ntiles;  // 4 KiB tile range
+  uint32_t nptrs;          // pointers of the stripe (inputs, then outputs)
+  uint32_t tile0, ntiles;  // tile range: 4 KiB tiles (region), 1 KiB (fused repair)
   uint32_t idx_base, tab4_base, tab1_base;  // region image offsets
   uint16_t type;           // 0 region block, 1 fused repair
   uint16_t block;          // region: block index
   uint16_t stride;         // region: table stride (the plan's R)
   uint16_t aligned;
+  uint32_t reserved;
 };
+static_assert(sizeof(WorkItem) == 64, "work items are read as four 16-byte words");
 
 struct WorkList {
   std::vector<uint8_t *> ptrs;
   std::vector<WorkItem> items;
-  size_t smem = 64;        // dynamic shared memory per CTA
+  size_t smem = 64;        // dynamic shared memory per CTA (pointer area included)
+  size_t ptr_area = 0;     // leading bytes of it holding the item's stripe pointers
   int64_t user_bytes = 0;
 };
 
+// Items per persistent CTA the work list is cut for: an item costs at most
+// 1/(kItemsPerCta x CTAs) of the list, so the last items pulled leave the
+// grid's tail short.
+constexpr int kItemsPerCta = 4;
+
 // Appends the stripes' items (biggest stripes first, blocks of one tile
 // range adjacent) and pointers; plan images are uploaded on first use.
-int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_bytes, WorkList &wl,
-                   std::string &err);
+// Items span work_bytes of each block, or fewer tiles where one item would
+// cost more than 1/target_items of all the stripes' products (target_items
+// <= 0: no limit).
+int worklist_build(const std::vector<const WorkStripe *> &stripes, int work_bytes,
+                   int target_items, WorkList &wl, std::string &err);
 
 // Persistent CTAs per SM that fit the kernel with this shared memory.
 int worklist_ctas_per_sm(size_t smem);
 
-// Counter reset + persistent kernel over nitems items already on the device.
-cudaError_t worklist_launch(const WorkItem *d_items, int nitems, uint8_t *const *d_ptrs,
-                            unsigned *d_counter, unsigned grid, size_t smem, cudaStream_t stream);
+// Counter reset + persistent kernel over nitems items.  items and ptrs are
+// device-accessible: device memory, or mapped pinned host memory that the
+// kernel reads in place (one item and its stripe's pointers per pull);
+// ptr_area is the WorkList's.
+cudaError_t worklist_launch(const WorkItem *items, int nitems, uint8_t *const *ptrs,
+                            unsigned *d_counter, unsigned grid, size_t smem, size_t ptr_area,
+                            cudaStream_t stream);
 
 }  // namespace pmrc

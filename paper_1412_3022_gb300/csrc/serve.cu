@@ -1,24 +1,27 @@
 // Serving loop: continuous batching of encode, repair and reconstruction
 // requests on one GPU.
 //
-// A scheduler thread owns three streams (host-to-device copies, compute,
-// device-to-host copies) and a device arena whose size is the HBM budget.
-// Each pass of its loop:
+// A scheduler thread owns a compute stream, kCopyLanes streams for each copy
+// direction and a device arena whose size is the HBM budget.  Each pass of
+// its loop:
 //   1. admits queued requests in arrival order while a slot is free and the
 //      arena has room for the request's inputs and outputs (first fit);
-//      their input copies start at once on the copy stream;
+//      their input copies start at once, each on the host-to-device stream
+//      with the fewest bytes queued;
 //   2. marks requests whose inputs have landed as ready;
 //   3. when fewer than two iterations are in flight, launches one iteration:
 //      the work items of every ready request (batch.cu's persistent kernel)
-//      in one launch, followed on the copy-back stream by the output copies
-//      of those requests;
+//      in one launch, plus one built-in bitsliced launch per large encode,
+//      followed by the output copies of those requests, each on the
+//      device-to-host stream with the fewest bytes queued;
 //   4. retires requests whose outputs are back: frees their arena range and
 //      records submit-to-completion latency.
 // Requests that arrive while an iteration runs are admitted and copied in
 // meanwhile and join the next iteration, so transfers overlap compute and
-// the work of many requests overlaps in one launch.  Coefficient plans stay
-// on the device in the code handles.  All waits on the device are event
-// queries polled by the host: no device-side wait exists.
+// the work of many requests overlaps in one launch.  Coefficient plans are
+// built at submission, on the caller's thread, and stay on the device in the
+// code handles.  All waits on the device are event queries polled by the
+// host: no device-side wait exists.
 #include <cuda_runtime.h>
 
 #include "trace.h"
@@ -49,6 +52,15 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAlign = 256;
+constexpr int kCopyLanes = 4;  // copy streams per direction
+
+// The copy stream with the fewest bytes queued.
+int least_queued(const size_t *queued) {
+  int best = 0;
+  for (int l = 1; l < kCopyLanes; l++)
+    if (queued[l] < queued[best]) best = l;
+  return best;
+}
 
 // First-fit allocator over [0, size) with coalescing free list.
 class Arena {
@@ -108,6 +120,7 @@ struct Req {
   size_t in_bytes = 0, out_bytes = 0, nin = 0, nout = 0;
   size_t in_span = 0;  // in_bytes rounded up: outputs start 256-byte aligned
   size_t off = 0;
+  int in_lane = -1, out_lane = -1;  // copy streams carrying the input / output copy
   int64_t user_bytes = 0;
   State state = kQueued;
   int status = PMRC_OK;
@@ -129,13 +142,19 @@ struct pmrc_server {
   int max_slots = 0;
   uint8_t *arena_base = nullptr;
   std::unique_ptr<Arena> arena;
-  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
-  // double-buffered work lists (device + pinned staging)
-  WorkItem *d_items[2] = {nullptr, nullptr};
-  uint8_t **d_ptrs[2] = {nullptr, nullptr};
+  // copies run on several streams per direction: one copy's fixed latency
+  // overlaps the others', and a small request's copy need not queue behind
+  // a large one; each copy goes to the stream with the fewest bytes queued
+  cudaStream_t s_in[kCopyLanes] = {}, s_out[kCopyLanes] = {}, s_comp = nullptr;
+  size_t in_queued[kCopyLanes] = {}, out_queued[kCopyLanes] = {};
+  // double-buffered work lists in mapped pinned host memory: the kernel
+  // reads them in place, so launching an iteration queues no copy behind
+  // the requests' input copies on the copy engines
   unsigned *d_counter[2] = {nullptr, nullptr};
   WorkItem *h_items[2] = {nullptr, nullptr};
   uint8_t **h_ptrs[2] = {nullptr, nullptr};
+  const WorkItem *m_items[2] = {nullptr, nullptr};  // device addresses of h_items, h_ptrs
+  uint8_t *const *m_ptrs[2] = {nullptr, nullptr};
   cudaEvent_t buf_free[2] = {nullptr, nullptr};
   size_t item_cap = 0, ptr_cap = 0;
   int sms = 1;
@@ -190,7 +209,7 @@ void block_ptrs(pmrc_server *s, Req *r, std::vector<const uint8_t *> &in,
 }  // namespace
 
 bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) {
-  // the staging buffer must be free of its previous upload
+  // the work-list buffer must be free of the kernel that read it last
   const int b = next_buf;
   if (cudaEventQuery(buf_free[b]) == cudaErrorNotReady) return false;
   std::vector<WorkStripe> stripes(ready.size());
@@ -239,7 +258,7 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
   }
   WorkList wl;
   if (!sp.empty()) {
-    int rc = worklist_build(sp, 64 << 10, wl, err);
+    int rc = worklist_build(sp, 64 << 10, kItemsPerCta * sms * 2, wl, err);
     if (rc) {
       for (Req *r : ok) {
         r->status = rc;
@@ -274,16 +293,12 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
   if (!ok.empty() && !wl.items.empty()) {
     memcpy(h_items[b], wl.items.data(), wl.items.size() * sizeof(WorkItem));
     memcpy(h_ptrs[b], wl.ptrs.data(), wl.ptrs.size() * sizeof(uint8_t *));
-    cudaMemcpyAsync(d_items[b], h_items[b], wl.items.size() * sizeof(WorkItem),
-                    cudaMemcpyHostToDevice, s_comp);
-    cudaMemcpyAsync(d_ptrs[b], h_ptrs[b], wl.ptrs.size() * sizeof(uint8_t *),
-                    cudaMemcpyHostToDevice, s_comp);
-    cudaEventRecord(buf_free[b], s_comp);
     const int per_sm = std::min(2, worklist_ctas_per_sm(wl.smem));
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)wl.items.size()));
-    cudaError_t e = worklist_launch(d_items[b], (int)wl.items.size(), d_ptrs[b], d_counter[b],
-                                    grid, wl.smem, s_comp);
+    cudaError_t e = worklist_launch(m_items[b], (int)wl.items.size(), m_ptrs[b], d_counter[b],
+                                    grid, wl.smem, wl.ptr_area, s_comp);
+    cudaEventRecord(buf_free[b], s_comp);
     if (e != cudaSuccess) {
       err = std::string("serving launch: ") + cudaGetErrorString(e);
       for (Req *r : ok) {
@@ -308,12 +323,18 @@ bool pmrc_server::launch_iteration(std::vector<Req *> &ready, std::string &err) 
     }
   cudaEventRecord(it.done, s_comp);
   // outputs go back as soon as the iteration's kernels are done
-  cudaStreamWaitEvent(s_out, it.done, 0);
+  bool waited[kCopyLanes] = {};
   for (Req *r : ok) {
-    if (!r->device)
+    const int l = least_queued(out_queued);
+    if (!waited[l]) cudaStreamWaitEvent(s_out[l], it.done, 0);
+    waited[l] = true;
+    if (!r->device) {
       cudaMemcpyAsync(r->out, arena_base + r->off + r->in_span, r->out_bytes,
-                      cudaMemcpyDeviceToHost, s_out);
-    cudaEventRecord(r->ev_out, s_out);
+                      cudaMemcpyDeviceToHost, s_out[l]);
+      out_queued[l] += r->out_bytes;
+      r->out_lane = l;
+    }
+    cudaEventRecord(r->ev_out, s_out[l]);
     r->state = kRunning;
   }
   it.reqs = ok;
@@ -343,8 +364,11 @@ void pmrc_server::run() {
       if (!arena->alloc(r->in_span + r->out_bytes, off)) break;
       queue.pop_front();
       r->off = off;
-      cudaMemcpyAsync(arena_base + off, r->in, r->in_bytes, cudaMemcpyHostToDevice, s_in);
-      cudaEventRecord(r->ev_in, s_in);
+      const int l = least_queued(in_queued);
+      cudaMemcpyAsync(arena_base + off, r->in, r->in_bytes, cudaMemcpyHostToDevice, s_in[l]);
+      cudaEventRecord(r->ev_in, s_in[l]);
+      in_queued[l] += r->in_bytes;
+      r->in_lane = l;
       r->state = kCopyIn;
       active.push_back(r);
       progress = true;
@@ -352,7 +376,10 @@ void pmrc_server::run() {
     // 2. inputs landed
     std::vector<Req *> ready;
     for (Req *r : active) {
-      if (r->state == kCopyIn && cudaEventQuery(r->ev_in) == cudaSuccess) r->state = kReady;
+      if (r->state == kCopyIn && cudaEventQuery(r->ev_in) == cudaSuccess) {
+        r->state = kReady;
+        in_queued[r->in_lane] -= r->in_bytes;
+      }
       if (r->state == kReady) ready.push_back(r);
     }
     // 3. launch an iteration over every ready request
@@ -376,6 +403,7 @@ void pmrc_server::run() {
                        r->state == kFailed;
       if (fin) {
         if (r->state == kRunning) r->state = kDone;
+        if (r->out_lane >= 0) out_queued[r->out_lane] -= r->out_bytes;
         if (!r->device) arena->release(r->off, r->in_span + r->out_bytes);
         r->t_done = Clock::now();
         if (r->state == kDone) {
@@ -426,16 +454,23 @@ int pmrc_server_create(size_t budget_bytes, int max_slots, pmrc_server **out) {
   s->item_cap = 1 << 20;
   s->ptr_cap = 1 << 20;
   for (int b = 0; b < 2 && e == cudaSuccess; b++) {
-    e = cudaMalloc(&s->d_items[b], s->item_cap * sizeof(WorkItem));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_ptrs[b], s->ptr_cap * sizeof(uint8_t *));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter[b], sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_items[b], s->item_cap * sizeof(WorkItem));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_ptrs[b], s->ptr_cap * sizeof(uint8_t *));
+    e = cudaMalloc(&s->d_counter[b], sizeof(unsigned));
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(&s->h_items[b], s->item_cap * sizeof(WorkItem), cudaHostAllocMapped);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(&s->h_ptrs[b], s->ptr_cap * sizeof(uint8_t *), cudaHostAllocMapped);
+    void *mi = nullptr, *mp = nullptr;
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&mi, s->h_items[b], 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&mp, s->h_ptrs[b], 0);
+    s->m_items[b] = static_cast<const WorkItem *>(mi);
+    s->m_ptrs[b] = static_cast<uint8_t *const *>(mp);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->buf_free[b], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
+  for (int l = 0; l < kCopyLanes && e == cudaSuccess; l++) {
+    e = cudaStreamCreateWithFlags(&s->s_in[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out[l], cudaStreamNonBlocking);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     pmrc_server_destroy(s.release());
     return sfail(PMRC_ECUDA, std::string("server setup: ") + cudaGetErrorString(e));
@@ -461,16 +496,16 @@ void pmrc_server_destroy(pmrc_server *s) {
     if (kv.second->ev_out) cudaEventDestroy(kv.second->ev_out);
   }
   for (int b = 0; b < 2; b++) {
-    cudaFree(s->d_items[b]);
-    cudaFree(s->d_ptrs[b]);
     cudaFree(s->d_counter[b]);
     cudaFreeHost(s->h_items[b]);
     cudaFreeHost(s->h_ptrs[b]);
     if (s->buf_free[b]) cudaEventDestroy(s->buf_free[b]);
   }
-  if (s->s_in) cudaStreamDestroy(s->s_in);
+  for (int l = 0; l < kCopyLanes; l++) {
+    if (s->s_in[l]) cudaStreamDestroy(s->s_in[l]);
+    if (s->s_out[l]) cudaStreamDestroy(s->s_out[l]);
+  }
   if (s->s_comp) cudaStreamDestroy(s->s_comp);
-  if (s->s_out) cudaStreamDestroy(s->s_out);
   cudaFree(s->arena_base);
   delete s;
 }
