@@ -50,11 +50,43 @@ SMS = 152   # GB300 streaming multiprocessors
 
 
 # ------------------------------------------------------------ ALU models
-ALU_MODEL_REGION = ("split-table region kernel: 12 PRMT + 6 LOP3 = 18 ALU lane-ops per "
-                    "16-byte product (planner products, zeros included)")
 ALU_MODEL_BITSLICED = ("bitsliced kernel, per 32-byte lane and block: 44 lane-ops per input "
                        "(24 transpose + 20 subset-table XORs), 24 per output row (transpose "
                        "back), 8 per non-zero coefficient (one 3-input XOR per output plane)")
+ALU_MODEL_PROJECTION = ("bitsliced projection kernel, per 32-byte lane: 24 lane-ops per helper "
+                        "block read (transpose), per output plane of each constant product one "
+                        "3-input XOR per two terms, 24 per helper (transpose back)")
+
+
+def gf_mul_11d(x, y):
+    """x * y in GF(2^8) modulo 0x11D (for the instruction model only)."""
+    r = 0
+    while y:
+        if y & 1:
+            r ^= x
+        y >>= 1
+        x = (x << 1) ^ (0x11D if x & 0x80 else 0)
+    return r
+
+
+def alu_ops_projection(phi, helpers):
+    """ALU lane-ops per 32-byte column of the bitsliced helper-projection
+    kernel: each block a helper's phi reads is transposed into planes once
+    and multiplied by its constant as XORs of planes (output plane i of c*x
+    takes the input planes jj with bit i of c*2^jj set); the first block's
+    product starts the accumulator, later ones fold into it, two terms per
+    3-input XOR; the projection is transposed back."""
+    per_helper = 24
+    first = True
+    for c in phi:
+        if not c:
+            continue
+        per_helper += 24
+        for i in range(8):
+            t = sum((gf_mul_11d(int(c), 1 << jj) >> i) & 1 for jj in range(8))
+            per_helper += (t // 2) if first else -(-t // 2)
+        first = False
+    return per_helper * helpers
 
 
 def alu_ops_bitsliced(M, kind):
@@ -282,20 +314,17 @@ class Workload:
         self.decode_missing = len(missing)
         self.helper_reads = reads_per_helper
         # the kernel each operation runs, and its ALU lane-ops per launch
-        # (alu_model); the reconstruction (blocks of at least 256 KiB) and
-        # the newcomer (at least 1 MiB) run run-time bitsliced kernels, the
-        # helper projections the split-table region kernel
+        # (alu_model); the reconstruction and the helper projections (blocks
+        # of at least 256 KiB) and the newcomer (at least 1 MiB) run
+        # run-time bitsliced kernels
         P = self.P
         G = self.genc.generator()
         Gs = self.sysc.generator()[K:]
         Dn = self.sysc.newcomer_matrix(self.f, self.H)
-        Mh = np.zeros((D_, D_ * a), np.uint8)
-        for h in range(D_):
-            Mh[h, h * a:h * a + a] = coef
         Rm = R[missing] if missing else np.zeros((0, K), np.uint8)
         self.kernel = {"gen_encode": "bitsliced encode bs_n16_k8_c0_f0",
                        "sys_encode": "bitsliced encode bs_n16_k8_c1_f1",
-                       "repair_helpers": "region_kernel<1>",
+                       "repair_helpers": "bitsliced helper projections bs_rt_project (compiled at run time)",
                        "repair_newcomer": "bitsliced newcomer bs_rt_newcomer (compiled at run time)",
                        "decode": "bitsliced reconstruction bs_rt_decode (compiled at run time)"}
         self.alu_ops, self.alu_model = {}, {}
@@ -303,9 +332,8 @@ class Workload:
                            ("decode", Rm, "chunked"), ("repair_newcomer", Dn, "chunked")):
             self.alu_ops[n] = alu_ops_bitsliced(M, kind) * (B // 32)
             self.alu_model[n] = ALU_MODEL_BITSLICED
-        for n, M in (("repair_helpers", Mh),):
-            self.alu_ops[n] = int(P.pmrc_plan_stats(M)["entries"]) * (B // 16) * 18
-            self.alu_model[n] = ALU_MODEL_REGION
+        self.alu_ops["repair_helpers"] = alu_ops_projection(coef, D_) * (B // 32)
+        self.alu_model["repair_helpers"] = ALU_MODEL_PROJECTION
 
     def ops(self, stream=None):
         s, B, a = self, self.B, self.c_args

@@ -195,3 +195,43 @@ def test_batch_large_encodes_take_bitsliced_launches_with_ragged_tails():
             k = st["k"]
             want = O.encode(2 * k, k, 1, True, st["X"])[k * (k - 1):]
             assert np.array_equal(st["out"].cpu().numpy(), want), (k, st["nb"])
+
+
+def test_heavy_stripes_with_short_blocks_are_cut_into_one_tile_items():
+    """A batch holding only a k=16 repair over 84 KiB + 5 byte blocks and a
+    k=16 reconstruction over 61 KiB + 3 byte blocks: no item may cost more
+    than a fixed share of the list, so both are cut into items of one or
+    two tiles (1 KiB tiles for the repair, 4 KiB for the reconstruction's
+    blocks of rows) instead of 13 items of up to 64 KiB; the results,
+    ragged tails included, equal the oracle and the plain calls."""
+    n, k = 32, 16
+    a = k - 1
+    c = P.Code(n, k, 1, 1)
+    nr, nd = (84 << 10) + 5, (61 << 10) + 3
+    Xr = inputs.blocks(k * a, nr, seed=77)
+    Yr = O.encode(n, k, 1, True, Xr)
+    f = 21
+    H = c.default_helpers(f)
+    rin = dev(np.concatenate([Yr[a * h:a * h + a] for h in H]))
+    rout = torch.full((a, nr), 0xA5, dtype=torch.uint8, device="cuda")
+    Xd = inputs.blocks(k * a, nd, seed=78)
+    Yd = O.encode(n, k, 1, True, Xd)
+    S = [1, 4, 5, 9, 11, 16, 17, 18, 20, 22, 23, 25, 27, 29, 30, 31]
+    din = dev(Yd[[a * i + j for i in S for j in range(a)]])
+    dout = torch.full((k * a, nd), 0xA5, dtype=torch.uint8, device="cuda")
+    b = P.Batch()
+    b.add_repair(c, f, H, [rin[i] for i in range(len(H) * a)], [rout[j] for j in range(a)], nr)
+    b.add_decode(c, S, [din[i] for i in range(k * a)], [dout[r] for r in range(k * a)], nd)
+    b.build(64 << 10, 2)
+    info = b.info()
+    repair_tiles = -(-nr // 1024)
+    assert info["items"] >= repair_tiles + 16   # 64 KiB items: 2 for the repair, 11 row blocks
+    b.launch()
+    alone_r = torch.full_like(rout, 0x5A)
+    alone_d = torch.full_like(dout, 0x5A)
+    c.repair(f, H, [rin[i] for i in range(len(H) * a)], [alone_r[j] for j in range(a)], nr)
+    c.decode(S, [din[i] for i in range(k * a)], [alone_d[r] for r in range(k * a)], nd)
+    torch.cuda.synchronize()
+    assert np.array_equal(rout.cpu().numpy(), Yr[a * f:a * f + a])
+    assert np.array_equal(dout.cpu().numpy(), Xd)
+    assert torch.equal(rout, alone_r) and torch.equal(dout, alone_d)
