@@ -15,6 +15,7 @@
 #include "api_internal.h"
 #include "bitslice.h"
 #include "code.h"
+#include "device_info.h"
 #include "jit.h"
 #include "plan.h"
 #include "region.h"
@@ -934,6 +935,185 @@ std::shared_ptr<BsRuntimeKernel> decode_runtime(const pmrc_code *c, const int *n
   }, err, false, background);
 }
 
+// ALU lane-ops per 32-byte column of a bitsliced schedule (the kernels'
+// instruction model: per block, 44 per input -- 24 transpose + 20 subset
+// tables -- or 20 for a plane-layout input, 24 per output row unless it is
+// stored in plane layout; 8 per non-zero coefficient).
+long long schedule_cost(const Mat &M, const std::vector<BsBlock> &blks, bool in_planes,
+                        bool out_planes) {
+  long long c = 0;
+  for (const BsBlock &B : blks)
+    c += (long long)B.inputs.size() * (in_planes ? 20 : 44) + (out_planes ? 0 : 24 * (long long)B.rows.size());
+  for (uint8_t v : M.v) c += v ? 8 : 0;
+  return c;
+}
+
+bool blocks_fit(const std::vector<BsBlock> &blks, int rows, int cols) {
+  if (rows <= 0 || cols <= 0 || rows + cols > bitslice_max_pointers()) return false;
+  for (const BsBlock &B : blks)
+    if ((int)B.inputs.size() > kRuntimeMaxInputs) return false;
+  return true;
+}
+
+// The factored reconstruction of a systematic GF(2^8) code for these nodes
+// and wanted rows: Z (all of z), W restricted to the wanted rows, their
+// blocks, and the wanted data rows in W's order.  False when the code has no
+// such form, no data row is missing, or a wanted row is a present data row
+// (a copy the factored kernels do not make).
+struct Factored {
+  Mat Z, W;
+  std::vector<int> own, rows;
+  std::vector<BsBlock> zb, wb;
+};
+
+bool factored_form(const pmrc_code *c, const int *nodes, const std::vector<char> &want, Factored &F) {
+  if (c->m.w != 8 || !c->m.systematic || c->m.construction == kConsMbr) return false;
+  Mat Wall;
+  std::vector<int> mcols;
+  std::string e;
+  if (decode_factors(c->m, nodes, F.Z, Wall, mcols, F.own, e) || mcols.empty()) return false;
+  std::vector<int> at(c->m.K, -1);
+  for (size_t i = 0; i < mcols.size(); i++) at[mcols[i]] = (int)i;
+  std::vector<int> wi;
+  for (int r = 0; r < c->m.K; r++)
+    if (want[r]) {
+      if (at[r] < 0) return false;
+      wi.push_back(at[r]);
+      F.rows.push_back(r);
+    }
+  if (wi.empty()) return false;
+  const int m = (int)mcols.size();
+  F.W = Mat((int)wi.size(), m);
+  for (size_t q = 0; q < wi.size(); q++)
+    for (int s2 = 0; s2 < m; s2++) F.W.at((int)q, s2) = Wall.at(wi[q], s2);
+  F.zb = bs_blocks_grouped(F.Z.v.data(), m, F.Z.cols, F.own, kRuntimeMaxInputs);
+  F.wb = bs_blocks_chunked(F.W.v.data(), F.W.rows, m);
+  return true;
+}
+
+std::string nodes_key(const pmrc_code *c, const char *tag, const int *nodes) {
+  std::string key = tag;
+  for (int i = 0; i < c->m.k; i++) key += std::to_string(nodes[i]) + ",";
+  return key;
+}
+
+std::string want_key(const std::vector<char> &want) {
+  std::string key = ":";
+  for (char w : want) key += w ? '1' : '0';
+  return key;
+}
+
+// Whether a reconstruction of nbytes-byte blocks takes the factored
+// two-launch kernels: their estimated work plus the second launch's cost
+// (about 2 us of the GPU's ALU issue, 1227 lane-ops per column at 1 MiB)
+// below the one-launch schedule's, or the one-launch schedule does not fit
+// a launch.  The estimates are kept per (nodes, wanted rows).
+bool prefer_factored(const pmrc_code *c, const int *nodes, const std::vector<char> &want,
+                     size_t nbytes) {
+  const std::string key = nodes_key(c, "", nodes) + want_key(want);
+  std::pair<long long, long long> cost;
+  bool known;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->decode_costs.find(key);
+    known = it != c->decode_costs.end();
+    if (known) cost = it->second;
+  }
+  if (!known) {
+    cost = {-1, -1};
+    Factored F;
+    if (factored_form(c, nodes, want, F) && blocks_fit(F.zb, F.Z.rows, F.Z.cols) &&
+        blocks_fit(F.wb, F.W.rows, F.W.cols))
+      cost.second = schedule_cost(F.Z, F.zb, false, true) + schedule_cost(F.W, F.wb, true, false);
+    Mat R;
+    std::string e;
+    if (cost.second >= 0 && !decode_matrix(c->m, nodes, R, e)) {
+      std::vector<int> rows;
+      for (int r = 0; r < c->m.K; r++)
+        if (want[r]) rows.push_back(r);
+      Mat M((int)rows.size(), R.cols);
+      for (size_t q = 0; q < rows.size(); q++)
+        for (int col = 0; col < R.cols; col++) M.at((int)q, col) = R.at(rows[q], col);
+      const auto blks = bs_blocks_chunked(M.v.data(), M.rows, M.cols);
+      if (blocks_fit(blks, M.rows, M.cols)) cost.first = schedule_cost(M, blks, false, false);
+    }
+    std::lock_guard<std::mutex> g(c->mu);
+    c->decode_costs[key] = cost;
+  }
+  if (cost.second < 0) return false;
+  if (cost.first < 0) return true;
+  const double launch = 1227.0 * (double)(1u << 20) / (double)std::max<size_t>(nbytes, 1);
+  return (double)cost.second + launch < (double)cost.first;
+}
+
+// The two run-time kernels of the factored reconstruction (stage 1 "fz":
+// z = Z y stored in plane layout; stage 2 "fw": the wanted rows of W z), or
+// false while either is compiling (background) or when one cannot be built.
+bool factored_runtime(const pmrc_code *c, const int *nodes, const std::vector<char> &want,
+                      bool background, std::shared_ptr<BsRuntimeKernel> &kz,
+                      std::shared_ptr<BsRuntimeKernel> &kw, std::vector<int> &rows, int &m,
+                      std::string &err) {
+  Factored F;
+  if (!factored_form(c, nodes, want, F)) {
+    err = "no factored form";
+    return false;
+  }
+  rows = F.rows;
+  m = F.Z.rows;
+  kz = runtime_kernel_job(c, nodes_key(c, "fz:", nodes), [&](BsCompileFn &compile, std::string &) {
+    const Mat Z = F.Z;
+    const std::vector<BsBlock> zb = F.zb;
+    compile = [Z, zb](BsCompiled &out, std::string &e2) {
+      return bitslice_compile_stage(Z.v.data(), Z.rows, Z.cols, zb, kRuntimeMaxInputs, false, true,
+                                    "dstage1", out, e2);
+    };
+    return (int)kOk;
+  }, err, background);
+  kw = runtime_kernel_job(c, nodes_key(c, "fw:", nodes) + want_key(want),
+                          [&](BsCompileFn &compile, std::string &) {
+    const Mat W = F.W;
+    const std::vector<BsBlock> wb = F.wb;
+    compile = [W, wb](BsCompiled &out, std::string &e2) {
+      return bitslice_compile_stage(W.v.data(), W.rows, W.cols, wb, kRuntimeMaxInputs, true, false,
+                                    "dstage2", out, e2);
+    };
+    return (int)kOk;
+  }, err, background);
+  return kz && kw;
+}
+
+// Stream-ordered device scratch of the library's own (one pool per device,
+// nothing released between calls): the intermediate of a two-launch
+// product, allocated and freed in the order of the call's stream.
+cudaError_t scratch_alloc(void **p, size_t n, cudaStream_t st) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pools[dev], &props);
+      if (e != cudaSuccess) {
+        pools[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, n, pool, st);
+}
+
 // Whether a call of nbytes takes a run-time bitsliced kernel under the
 // handle's policy (GF(2^8) codes only; AUTO from auto_min bytes per block).
 bool want_runtime(const pmrc_code *c, int policy, size_t nbytes, size_t auto_min) {
@@ -966,9 +1146,39 @@ int decode_body(const pmrc_code *c, const int *nodes, const uint8_t *const *node
       aligned = !node_blocks[i] || (uintptr_t)node_blocks[i] % 16 == 0;
     for (int r : rows) aligned = aligned && (uintptr_t)data_out[r] % 16 == 0;
     std::string rerr;
+    if (aligned && prefer_factored(c, nodes, want, nbytes)) {
+      // x_M = W (Z y): the received parity blocks plus their present-data
+      // terms, then B^-1, as two launches through a plane-layout
+      // intermediate in stream-ordered scratch
+      std::shared_ptr<BsRuntimeKernel> kz, kw;
+      std::vector<int> frows;
+      int m = 0;
+      if (factored_runtime(c, nodes, want, !forced, kz, kw, frows, m, rerr)) {
+        const size_t cut = nbytes & ~(size_t)31;
+        void *zbuf = nullptr;
+        cudaError_t e = scratch_alloc(&zbuf, (size_t)m * cut, st);
+        if (e != cudaSuccess)
+          return fail(PMRC_ENOMEM, std::string("reconstruction scratch: ") + cudaGetErrorString(e));
+        std::vector<uint8_t *> z(m);
+        for (int i = 0; i < m; i++) z[i] = static_cast<uint8_t *>(zbuf) + (size_t)i * cut;
+        std::vector<const uint8_t *> zin(z.begin(), z.end());
+        std::vector<uint8_t *> outs;
+        for (int r : frows) outs.push_back(data_out[r]);
+        e = bitslice_launch_runtime(*kz, node_blocks, z.data(), cut, st);
+        if (e == cudaSuccess) e = bitslice_launch_runtime(*kw, zin.data(), outs.data(), cut, st, true);
+        const cudaError_t fe = cudaFreeAsync(zbuf, st);
+        if (e == cudaSuccess) e = fe;
+        if (e != cudaSuccess)
+          return fail(PMRC_ECUDA, std::string("bitsliced reconstruction launch: ") + cudaGetErrorString(e));
+        done = cut;
+      } else if (forced) {
+        return fail(PMRC_EUNSUPPORTED, "bitsliced reconstruction: " + rerr);
+      }
+      aligned = false;  // not the one-launch schedule: done, or the split-table kernel meanwhile
+    }
     std::shared_ptr<BsRuntimeKernel> k =
         aligned ? decode_runtime(c, nodes, want, !forced, rerr) : nullptr;
-    if (!k && forced)
+    if (!k && forced && done == 0)
       return fail(PMRC_EUNSUPPORTED, aligned ? "bitsliced reconstruction: " + rerr
                                              : "bitsliced reconstruction needs 16-byte aligned blocks");
     if (k) {

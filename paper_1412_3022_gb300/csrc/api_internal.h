@@ -51,6 +51,10 @@ struct pmrc_code {
   // evicted run-time kernels stay loaded until the handle is destroyed: a
   // launch from them may still be running
   mutable std::vector<std::shared_ptr<pmrc::BsRuntimeKernel>> rt_retired;
+  // reconstructions of a systematic code: per (nodes, wanted rows), the
+  // estimated ALU work per 32-byte column of the one-launch schedule and of
+  // the two-launch factored one (-1: not possible), decided at first use
+  mutable std::map<std::string, std::pair<long long, long long>> decode_costs;
 };
 
 namespace pmrc {

@@ -96,7 +96,7 @@ namespace {
 cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs, int noutputs,
                       const uint8_t *const *in, uint8_t *const *out, size_t nbytes,
                       cudaStream_t stream, std::atomic<uint64_t> (&smem_set)[kMaxDevices],
-                      int slot, size_t extra_smem = 0) {
+                      int slot, size_t extra_smem = 0, bool dependent = false) {
   BsArgs a;
   a.nbytes = nbytes;
   a.hi28 = 1u << 28;
@@ -125,7 +125,21 @@ cudaError_t bs_launch(const void *fn, int nblocks, const int *cost, int ninputs,
   bs_cta_ranges(nblocks, cost, ntiles, ncta, a.cta_g);
   for (int c = ncta + 1; c <= kBsMaxCtas; c++) a.cta_g[c] = (uint32_t)items;
   void *args[] = {&a};
-  return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);
+  if (!dependent) return cudaLaunchKernel(fn, dim3(ncta), dim3(kBsThreads), args, smem, stream);
+  // programmatic dependent launch: the grid may be placed while the previous
+  // kernel of the stream (which signals it) still runs; its kernel waits for
+  // that kernel's completion (griddepcontrol.wait) before reading
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ncta);
+  cfg.blockDim = dim3(kBsThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr = {};
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 std::atomic<uint64_t> g_static_smem_set[kMaxDevices];
@@ -253,10 +267,11 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by
 }
 
 cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,
-                                    uint8_t *const *out, size_t nbytes, cudaStream_t stream) {
+                                    uint8_t *const *out, size_t nbytes, cudaStream_t stream,
+                                    bool dependent) {
   return bs_launch(reinterpret_cast<const void *>(k.fn), k.nblocks, k.cost.data(), k.ninputs,
                    k.noutputs, in, out, nbytes, stream, k.smem_set, 0,
-                   k.pairs ? (size_t)kBsPairExchangeBytes : 0);
+                   k.pairs ? (size_t)kBsPairExchangeBytes : 0, dependent);
 }
 
 int bitslice_max_pointers() { return kBsMaxPtr; }
@@ -293,6 +308,30 @@ void repair_args(BsArgs &a, size_t nbytes, int nin, const uint8_t *const *in, in
 }
 
 }  // namespace
+
+int bitslice_compile_stage(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
+                           int max_inputs, bool in_planes, bool out_planes, const char *role,
+                           BsCompiled &out, std::string &err) {
+  if (rows <= 0 || cols <= 0 || rows + cols > kBsMaxPtr) {
+    err = "matrix too large for one bitsliced launch";
+    return kEUnsupported;
+  }
+  int rc = check_blocks(blks, max_inputs, err);
+  if (rc) return rc;
+  out.name = std::string("bs_rt_") + role;
+  const char *kname = out.name.c_str();
+  const BsEmitted em = bs_emit_kernel(M, rows, cols, blks, kname, true, true, in_planes, out_planes);
+  rc = jit_compile(runtime_source(em.code), kname, out.cubin, err);
+  if (rc) return rc;
+  out.kind = kBsMatrix;
+  out.pairs = 1;
+  out.nblocks = (int)blks.size();
+  out.ninputs = cols;
+  out.noutputs = rows;
+  out.cost = em.cost;
+  return kOk;
+}
+
 
 int bitslice_compile_projection(const uint8_t *phi, int alpha, const char *role, BsCompiled &out,
                                 std::string &err) {

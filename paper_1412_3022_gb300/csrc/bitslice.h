@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include "bs_emit.h"
+
 namespace pmrc {
 
 // Checksum of an encode matrix (row-major bytes), as stored with each
@@ -72,6 +74,14 @@ struct BsCompiled {
 int bitslice_compile(const uint8_t *M, int rows, int cols, int max_inputs, bool by_support,
                      const char *role, BsCompiled &out, std::string &err);
 
+// One launch of a two-launch product: the matrix schedule for M with the
+// given blocks (each at most max_inputs inputs), over warp pairs, reading
+// plane-layout inputs (in_planes) and/or storing plane-layout outputs
+// (out_planes) -- see bs_emit_kernel.  Host only, like bitslice_compile.
+int bitslice_compile_stage(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
+                           int max_inputs, bool in_planes, bool out_planes, const char *role,
+                           BsCompiled &out, std::string &err);
+
 // Loads a compiled schedule as a CUDA library (the calling thread's device
 // context must be usable).
 int bitslice_load(const BsCompiled &c, std::shared_ptr<BsRuntimeKernel> &out, std::string &err);
@@ -82,9 +92,12 @@ int bitslice_build(const uint8_t *M, int rows, int cols, int max_inputs, bool by
 
 // out[r] = sum_c M[r][c] in[c] over bytes [0, nbytes); nbytes a multiple of
 // 32, every pointer 16-byte aligned; in[c] may be NULL for columns no row
-// reads, out[r] may not be NULL.
+// reads, out[r] may not be NULL.  dependent: a programmatic dependent launch
+// after the stream's previous kernel (the second launch of a two-launch
+// product, whose kernel waits for the first before reading it).
 cudaError_t bitslice_launch_runtime(BsRuntimeKernel &k, const uint8_t *const *in,
-                                    uint8_t *const *out, size_t nbytes, cudaStream_t stream);
+                                    uint8_t *const *out, size_t nbytes, cudaStream_t stream,
+                                    bool dependent = false);
 
 // Repair schedules compiled at run time (host only, like bitslice_compile).
 // Projection: phi (alpha entries, at least one non-zero), kernel

@@ -181,11 +181,30 @@ __device__ __forceinline__ void bs_planes(const BsCtx &x, uint32_t src, uint32_t
   bs_tables(w, Q, R);
 }
 
+// Plane-layout input: the 32 staged bytes at shared address `src` are
+// already the eight bit planes of the lane's 32 bytes (an intermediate a
+// plane-layout store wrote); their subset tables, no transpose.
+__device__ __forceinline__ void bs_planes_direct(uint32_t src, uint32_t (&Q)[16],
+                                                 uint32_t (&R)[16]) {
+  uint32_t w[8];
+  bs_load(src, w);
+  bs_tables(w, Q, R);
+}
+
 // Barrier of the two warps of pair `pair` (named barrier 1 + pair, 64
 // threads); the fused repair kernels exchange partial sums through shared
 // memory between them.
 __device__ __forceinline__ void bs_pair_sync(uint32_t pair) {
   asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+}
+
+// Plane-layout output: the eight planes stored as they are (an
+// intermediate for a later launch that reads it with bs_planes_direct), with
+// ordinary stores so that the next launch finds it in L2.
+__device__ __forceinline__ void bs_store_planes(const BsCtx &x, int slot, const uint32_t (&planes)[8]) {
+  uint4 *p = reinterpret_cast<uint4 *>(x.a->ptr[slot] + x.off);
+  p[0] = make_uint4(planes[0], planes[1], planes[2], planes[3]);
+  p[1] = make_uint4(planes[4], planes[5], planes[6], planes[7]);
 }
 
 __device__ __forceinline__ void bs_store(const BsCtx &x, int slot, uint32_t (&planes)[8]) {

@@ -68,6 +68,59 @@ std::vector<BsBlock> bs_blocks_chunked(const uint8_t *M, int rows, int cols) {
   return blks;
 }
 
+std::vector<BsBlock> bs_blocks_grouped(const uint8_t *M, int rows, int cols,
+                                       const std::vector<int> &own, int max_inputs) {
+  std::map<std::vector<int>, std::vector<int>> groups;
+  std::vector<std::vector<int>> order;
+  for (int r = 0; r < rows; r++) {
+    std::vector<int> key;
+    for (int q = 0; q < cols; q++)
+      if (M[(size_t)r * cols + q] && q != own[r]) key.push_back(q);
+    if (!groups.count(key)) order.push_back(key);
+    groups[key].push_back(r);
+  }
+  auto union_size = [&](const std::vector<int> &rs) {
+    std::vector<char> used(cols, 0);
+    int u = 0;
+    for (int r : rs)
+      for (int q = 0; q < cols; q++)
+        if (M[(size_t)r * cols + q] && !used[q]) used[q] = 1, u++;
+    return u;
+  };
+  std::vector<std::vector<int>> row_sets;  // rows of each block
+  std::vector<int> cur;
+  for (auto &key : order) {
+    const auto &rs = groups[key];
+    if (rs.size() > (size_t)kBsEmitRows) {  // a large group: balanced blocks of its own
+      const int nb = (int)((rs.size() + kBsEmitRows - 1) / kBsEmitRows);
+      for (int b = 0; b < nb; b++)
+        row_sets.emplace_back(rs.begin() + rs.size() * b / nb, rs.begin() + rs.size() * (b + 1) / nb);
+      continue;
+    }
+    std::vector<int> grown(cur);
+    grown.insert(grown.end(), rs.begin(), rs.end());
+    if (!cur.empty() && (grown.size() > (size_t)kBsEmitRows || union_size(grown) > max_inputs)) {
+      row_sets.push_back(cur);
+      cur.assign(rs.begin(), rs.end());
+    } else {
+      cur = grown;
+    }
+  }
+  if (!cur.empty()) row_sets.push_back(cur);
+  std::vector<BsBlock> blks;
+  for (auto &rs : row_sets) {
+    BsBlock B;
+    B.rows = rs;
+    std::vector<char> used(cols, 0);
+    for (int r : rs)
+      for (int q = 0; q < cols; q++) used[q] |= M[(size_t)r * cols + q] != 0;
+    for (int q = 0; q < cols; q++)
+      if (used[q]) B.inputs.push_back(q);
+    blks.push_back(B);
+  }
+  return blks;
+}
+
 void bs_cta_ranges(int nblocks, const int *cost, uint64_t ntiles, int ncta, uint32_t *cta_g) {
   double total = 0;
   for (int i = 0; i < nblocks; i++) total += (double)cost[i] * (double)ntiles;
@@ -90,10 +143,12 @@ void bs_cta_ranges(int nblocks, const int *cost, uint64_t ntiles, int ncta, uint
 namespace {
 
 // One block function: the loop over `ins` (a block's inputs, or half of
-// them) accumulating M's coefficients of the block's rows into acc.  Returns
-// the accumulate instructions emitted.
+// them) accumulating M's coefficients of the block's rows into acc; with
+// in_planes the inputs are plane-layout blocks (no transpose).  Returns the
+// accumulate instructions emitted.
 int emit_block_fn(std::string &f, const uint8_t *M, int K, const BsBlock &B,
-                  const std::vector<int> &ins, const std::string &fname, long long &xors) {
+                  const std::vector<int> &ins, const std::string &fname, bool in_planes,
+                  long long &xors) {
   int ops = 0;
   {  // the inputs' columns, read by the prefetch in the loop below
     std::string colsl;
@@ -120,7 +175,9 @@ int emit_block_fn(std::string &f, const uint8_t *M, int K, const BsBlock &B,
       f += "  bs_commit_empty();\n";
   appendf(f, "  uint32_t rd = base, wr = base + %d * kBsSlotStep;\n", kAhead % kSlots);
   appendf(f, "#pragma unroll 1\n  for (int i = 0; i < %d; i++) {\n", C);
-  appendf(f, "    bs_wait<%d>();\n    bs_planes(x, rd, Q, R);\n", kAhead - 1);
+  appendf(f, in_planes ? "    bs_wait<%d>();\n    bs_planes_direct(rd, Q, R);\n"
+                       : "    bs_wait<%d>();\n    bs_planes(x, rd, Q, R);\n",
+          kAhead - 1);
   appendf(f, "    if (i + %d < %d) bs_prefetch(x, in[i + %d], wr); else bs_commit_empty();\n",
           kAhead, C, kAhead);
   f += "    rd += kBsSlotStep;\n    rd = rd == end ? base : rd;\n";
@@ -169,9 +226,11 @@ int emit_block_fn(std::string &f, const uint8_t *M, int K, const BsBlock &B,
 }  // namespace
 
 BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
-                         const std::string &name, bool extern_c, bool pair_split) {
+                         const std::string &name, bool extern_c, bool pair_split, bool in_planes,
+                         bool out_planes) {
   BsEmitted e;
   std::string &f = e.code;
+  const char *store = out_planes ? "bs_store_planes" : "bs_store";
   const int K = cols;
   (void)rows;
   std::vector<int> blk_ops(blks.size(), 0);  // accumulate instructions per block
@@ -181,17 +240,23 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
             B.inputs.size());
     const std::string fn = name + "_b" + std::to_string(b);
     if (!pair_split) {
-      blk_ops[b] = emit_block_fn(f, M, K, B, B.inputs, fn, e.xors);
+      blk_ops[b] = emit_block_fn(f, M, K, B, B.inputs, fn, in_planes, e.xors);
     } else {  // the inputs cut in two halves, one per warp of a pair
       const size_t h = (B.inputs.size() + 1) / 2;
       const std::vector<int> i0(B.inputs.begin(), B.inputs.begin() + h), i1(B.inputs.begin() + h,
                                                                            B.inputs.end());
-      blk_ops[b] = emit_block_fn(f, M, K, B, i0, fn + "_h0", e.xors);
-      blk_ops[b] += emit_block_fn(f, M, K, B, i1, fn + "_h1", e.xors);
+      blk_ops[b] = emit_block_fn(f, M, K, B, i0, fn + "_h0", in_planes, e.xors);
+      blk_ops[b] += emit_block_fn(f, M, K, B, i1, fn + "_h1", in_planes, e.xors);
     }
   }
   appendf(f, "%s__global__ void __launch_bounds__(kBsThreads, 1) %s(const __grid_constant__ BsArgs a) {\n",
           extern_c ? "extern \"C\" " : "", name.c_str());
+  // a two-launch product: the first kernel lets the second be placed at
+  // once (programmatic dependent launch); the second waits for the first's
+  // completion and memory before it reads the intermediate (both are no-ops
+  // in a plain launch)
+  if (out_planes) f += "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n";
+  if (in_planes) f += "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n";
   f += "  const uint32_t g1 = a.cta_g[blockIdx.x + 1];\n";
   if (!pair_split) {
     // persistent kernel, one CTA per SM: the host splits the sequence of
@@ -207,7 +272,7 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
       const BsBlock &B = blks[b];
       appendf(f, "      case %zu: {\n        %s_b%zu(x, acc);\n", b, name.c_str(), b);
       for (size_t q = 0; q < B.rows.size(); q++)
-        appendf(f, "        bs_store(x, %d, acc[%zu]);\n", K + B.rows[q], q);
+        appendf(f, "        %s(x, %d, acc[%zu]);\n", store, K + B.rows[q], q);
       f += "      } break;\n";
     }
     f += "      default: break;\n    }\n  }\n}\n\n";
@@ -237,7 +302,7 @@ BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector
         appendf(f, "        if ((%d < %d) == (half == 0)) {\n", q, rs);
         appendf(f, "#pragma unroll\n          for (int i = 0; i < 8; i++) acc[%d][i] = bs_x2(acc[%d][i], xs[(%d * 8 + i) * 32 + lane]);\n",
                 q, q, q);
-        appendf(f, "          if (live) bs_store(x, %d, acc[%d]);\n        }\n", K + B.rows[q], q);
+        appendf(f, "          if (live) %s(x, %d, acc[%d]);\n        }\n", store, K + B.rows[q], q);
       }
       f += "        bs_pair_sync(pair);  // the exchange area is reused by the next item\n";
       f += "      } break;\n";

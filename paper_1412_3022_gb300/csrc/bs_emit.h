@@ -35,6 +35,15 @@ std::vector<BsBlock> bs_blocks_by_support(const uint8_t *M, int rows, int cols);
 // rows' non-zero columns (dense matrices such as reconstruction rows).
 std::vector<BsBlock> bs_blocks_chunked(const uint8_t *M, int rows, int cols);
 
+// Rows grouped by their non-zero columns other than own[r] (a column of
+// each row's own, such as the received parity block a row starts from), in
+// order of first appearance; groups packed whole into blocks of at most 8
+// rows whose inputs stay within max_inputs (a block holding one group may
+// exceed it), a group of more than 8 cut into balanced blocks of its own;
+// each block reads the union of its rows' columns.
+std::vector<BsBlock> bs_blocks_grouped(const uint8_t *M, int rows, int cols,
+                                       const std::vector<int> &own, int max_inputs);
+
 // The launch's work items g = b * ntiles + t (block b < nblocks, 1 KiB
 // column tile t < ntiles) cut into ncta contiguous ranges of about equal
 // cost (cost[b] per tile of block b): CTA c takes [cta_g[c], cta_g[c+1]),
@@ -55,9 +64,13 @@ struct BsEmitted {
 // tile) item together, each over half of the block's inputs, and combine
 // their partial sums through shared memory (kBsPairExchangeBytes beyond the
 // staging ring): twice the warp tasks at half the latency, for launches
-// with few tiles per warp.
+// with few tiles per warp.  in_planes / out_planes: the inputs are, the
+// outputs are stored as, plane-layout blocks (each lane's 32 bytes hold the
+// eight 32-bit bit planes of those 32 byte columns) -- the intermediate of
+// a two-launch product, which skips the transposes on both sides of it.
 BsEmitted bs_emit_kernel(const uint8_t *M, int rows, int cols, const std::vector<BsBlock> &blks,
-                         const std::string &name, bool extern_c, bool pair_split = false);
+                         const std::string &name, bool extern_c, bool pair_split = false,
+                         bool in_planes = false, bool out_planes = false);
 constexpr int kBsPairExchangeBytes = 8 * 8 * 8 * 32 * 4;  // 8 pairs x 8 rows x 8 planes x 32 lanes
 
 // Repair schedules, emitted at run time for one failed node's helper

@@ -392,6 +392,58 @@ static int decode_matrix_mbr(const CodeMatrices &c, const int *nodes, Mat &Rinv,
   return kOk;
 }
 
+namespace {
+
+// The systematic form's reconstruction, factored: a present data block is
+// its own row of G' (a unit row), so only the missing data columns M need
+// solving.  With Q the parity rows received, y_Q = A x_P + B x_M (A =
+// G'[Q][present columns], B = G'[Q][M], |Q| = |M|) and x_P = y_P, hence
+// x_M = B^-1 (y_Q + A y_P) (characteristic 2), an |M|^3 elimination instead
+// of a K^3 one.  qpos[i]: input slot of the i-th received parity block;
+// pcols / ppos: present data columns and their input slots; mcols: the
+// missing data columns, in order.
+struct SysFactors {
+  std::vector<int> qpos, pcols, ppos, mcols;
+  Mat A, Binv;
+};
+
+int systematic_factors(const CodeMatrices &c, const int *nodes, SysFactors &F,
+                       std::string &err) {
+  const int a = c.alpha, K = c.k * a;
+  std::vector<int> pos_of_col(K, -1);
+  for (int i = 0; i < c.k; i++)
+    for (int j = 0; j < a; j++) {
+      if (nodes[i] < c.k)
+        pos_of_col[a * nodes[i] + j] = a * i + j;
+      else
+        F.qpos.push_back(a * i + j);
+    }
+  for (int col = 0; col < K; col++) {
+    if (pos_of_col[col] < 0) {
+      F.mcols.push_back(col);
+    } else {
+      F.pcols.push_back(col);
+      F.ppos.push_back(pos_of_col[col]);
+    }
+  }
+  const int m = (int)F.mcols.size();
+  if (m == 0) return kOk;
+  Mat B(m, m);
+  F.A = Mat(m, (int)F.pcols.size());
+  for (int qi = 0; qi < m; qi++) {
+    const int row = a * nodes[F.qpos[qi] / a] + F.qpos[qi] % a;  // row of G'
+    for (int mi = 0; mi < m; mi++) B.at(qi, mi) = c.Gcode.at(row, F.mcols[mi]);
+    for (size_t pi = 0; pi < F.pcols.size(); pi++) F.A.at(qi, (int)pi) = c.Gcode.at(row, F.pcols[pi]);
+  }
+  if (!mat_inverse(B, F.Binv)) {
+    err = "these k nodes do not determine the data";
+    return kESingular;
+  }
+  return kOk;
+}
+
+}  // namespace
+
 int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err) {
   int rc = check_distinct(nodes, c.k, c.n, -1, err, "nodes");
   if (rc) return rc;
@@ -411,42 +463,42 @@ int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::strin
     }
     return kOk;
   }
-  // Systematic form: a present data block is its own row of G' (a unit
-  // row), so only the missing data columns M need solving.  With Q the
-  // parity rows received, y_Q = A x_P + B x_M (A = G'[Q][present columns],
-  // B = G'[Q][M], |Q| = |M|) and x_P = y_P, hence x_M = B^-1 y_Q + B^-1 A y_P
-  // (characteristic 2): the same rows as the full inverse, for an |M|^3
-  // elimination instead of a K^3 one.
-  std::vector<int> pos_of_col(K, -1), qpos, mcols, pcols;
-  for (int i = 0; i < c.k; i++)
-    for (int j = 0; j < a; j++) {
-      if (nodes[i] < c.k)
-        pos_of_col[a * nodes[i] + j] = a * i + j;
-      else
-        qpos.push_back(a * i + j);
-    }
-  for (int col = 0; col < K; col++) (pos_of_col[col] < 0 ? mcols : pcols).push_back(col);
+  SysFactors F;
+  rc = systematic_factors(c, nodes, F, err);
+  if (rc) return rc;
   Rinv = Mat(K, K);
-  for (int col : pcols) Rinv.at(col, pos_of_col[col]) = 1;
-  const int m = (int)mcols.size();
+  for (size_t pi = 0; pi < F.pcols.size(); pi++) Rinv.at(F.pcols[pi], F.ppos[pi]) = 1;
+  const int m = (int)F.mcols.size();
   if (m == 0) return kOk;
-  Mat B(m, m), A(m, (int)pcols.size()), Binv;
-  for (int qi = 0; qi < m; qi++) {
-    const int row = a * nodes[qpos[qi] / a] + qpos[qi] % a;  // row of G'
-    for (int mi = 0; mi < m; mi++) B.at(qi, mi) = c.Gcode.at(row, mcols[mi]);
-    for (size_t pi = 0; pi < pcols.size(); pi++) A.at(qi, (int)pi) = c.Gcode.at(row, pcols[pi]);
-  }
-  if (!mat_inverse(B, Binv)) {
-    err = "these k nodes do not determine the data";
-    return kESingular;
-  }
-  Mat BA = pcols.empty() ? Mat(m, 0) : mat_mul(Binv, A);
+  Mat BA = F.pcols.empty() ? Mat(m, 0) : mat_mul(F.Binv, F.A);
   for (int mi = 0; mi < m; mi++) {
-    const int col = mcols[mi];
-    for (int qi = 0; qi < m; qi++) Rinv.at(col, qpos[qi]) = Binv.at(mi, qi);
-    for (size_t pi = 0; pi < pcols.size(); pi++)
-      Rinv.at(col, pos_of_col[pcols[pi]]) = BA.at(mi, (int)pi);
+    const int col = F.mcols[mi];
+    for (int qi = 0; qi < m; qi++) Rinv.at(col, F.qpos[qi]) = F.Binv.at(mi, qi);
+    for (size_t pi = 0; pi < F.pcols.size(); pi++) Rinv.at(col, F.ppos[pi]) = BA.at(mi, (int)pi);
   }
+  return kOk;
+}
+
+int decode_factors(const CodeMatrices &c, const int *nodes, Mat &Z, Mat &W,
+                   std::vector<int> &mcols, std::vector<int> &zslot, std::string &err) {
+  int rc = check_distinct(nodes, c.k, c.n, -1, err, "nodes");
+  if (rc) return rc;
+  if (c.construction == kConsMbr || c.w != 8 || !c.systematic) {
+    err = "factored reconstruction: systematic GF(2^8) MSR and Reed-Solomon codes only";
+    return kEUnsupported;
+  }
+  SysFactors F;
+  rc = systematic_factors(c, nodes, F, err);
+  if (rc) return rc;
+  const int m = (int)F.mcols.size(), KA = c.k * c.alpha;
+  mcols = F.mcols;
+  zslot = F.qpos;
+  Z = Mat(m, KA);
+  for (int qi = 0; qi < m; qi++) {
+    Z.at(qi, F.qpos[qi]) = 1;
+    for (size_t pi = 0; pi < F.pcols.size(); pi++) Z.at(qi, F.ppos[pi]) = F.A.at(qi, (int)pi);
+  }
+  W = F.Binv;
   return kOk;
 }
 

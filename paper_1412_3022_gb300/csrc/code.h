@@ -102,6 +102,16 @@ int newcomer_matrix(const CodeMatrices &c, int f, const int *helpers, Mat &D, st
 // nodes' k alpha rows have rank K; K independent ones (rows that copy a data
 // block first) are inverted and the others get zero coefficients.
 int decode_matrix(const CodeMatrices &c, const int *nodes, Mat &Rinv, std::string &err);
+// The reconstruction of a systematic GF(2^8) MSR or Reed-Solomon code in
+// factored form: the missing data rows mcols (W's rows, in order) are
+// x_M = W z with z = Z y, y the k alpha received blocks.  Z (|M| x k alpha)
+// is the received parity blocks plus their present-data terms (sparse: a
+// parity row's non-zeros on present columns; row i starts from the parity
+// block in input slot zslot[i], coefficient 1), W = B^-1 (|M| x |M|).  The
+// product W Z equals decode_matrix's rows mcols.  |M| = 0 when every data
+// node is among the k; kEUnsupported for other codes.
+int decode_factors(const CodeMatrices &c, const int *nodes, Mat &Z, Mat &W,
+                   std::vector<int> &mcols, std::vector<int> &zslot, std::string &err);
 
 // Default helper set for node f: the d lowest-index survivors, or the first
 // set (in that order of preference) whose Psi rows are invertible.

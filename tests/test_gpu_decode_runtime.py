@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 import paper_1412_3022_gb300 as P
+from oracle_columns import oracle_columns
 from paper_1412_3022_gb300 import inputs
 from test_gpu_parity import Blocks
 
@@ -189,3 +190,65 @@ def test_forced_bitsliced_compiles_before_it_launches():
     got, _ = decode(c, [0, 2, 4, 6, 9, 11, 13, 15], Y, nbytes)
     assert np.array_equal(got, X)
     assert c.runtime_kernels() == (1, 0)
+
+
+def lazy_decode_every_column(c, n, k, S, nbytes, X, Y):
+    """Reconstruction of the missing data rows only (present data rows
+    alias their node blocks), checked byte for byte against the data."""
+    got, computed = decode(c, S, Y, nbytes, lazy=True)
+    a = k - 1
+    missing = [r for r in range(k * a) if r // a not in S]
+    assert [r for r in range(k * a) if computed[r]] == missing
+    for r in missing:
+        assert np.array_equal(got[r], X[r]), (S, r)
+
+
+@pytest.mark.parametrize("S,kernels", [([0, 1, 2, 3, 4, 5, 6, 9], None),   # one data node missing
+                                       ([0, 1, 4, 5, 7, 8, 11, 12], 2),     # three (the bench's set)
+                                       ([15, 2, 9, 4, 13, 0, 11, 6], 2),    # four, out of order
+                                       ([1, 3, 5, 8, 9, 10, 12, 14], 2)])   # five
+def test_factored_reconstruction_k8_1mib(S, kernels):
+    """Lazy reconstructions of 1 MiB blocks: where the reconstruction rows
+    are dense (three or more data nodes missing: B^-1 mixes every parity
+    block) they take the two-launch factored kernels -- z = the received
+    parity blocks plus their present-data terms, stored in plane layout in
+    stream-ordered scratch, then the missing rows B^-1 z -- two run-time
+    kernels per node set; with one data node missing the rows are about as
+    sparse as z and either schedule may be chosen.  The 48-byte ragged tail
+    goes to the split-table kernel; every missing row equals the data."""
+    n, k = 16, 8
+    nbytes = (1 << 20) + 48
+    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+    c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+    X = inputs.blocks(56, nbytes, seed=120)
+    Y = oracle_columns(lambda x: O.encode(n, k, O.SPARSE, True, x), [X])
+    lazy_decode_every_column(c, n, k, S, nbytes, X, Y)
+    first = c.runtime_kernels()
+    assert first in ((1, 0), (2, 0)) if kernels is None else first == (kernels, 0)
+    lazy_decode_every_column(c, n, k, S, nbytes, X, Y)   # the same kernels again
+    assert c.runtime_kernels() == first
+
+
+def test_factored_reconstruction_k16_where_one_launch_cannot_fit():
+    """n=32, k=16: with four data nodes missing, a row of the one-launch
+    schedule reads the 240 received blocks, beyond a bitsliced block's 64
+    inputs, so the bitsliced reconstruction exists only in factored form (z
+    rows grouped by support, B^-1 of 60 rows); with two and three missing
+    either form may be chosen.  Lazy reconstructions with a ragged 16-byte
+    tail equal the data."""
+    n, k = 32, 16
+    a = k - 1
+    nbytes = (64 << 10) + 16
+    X = inputs.blocks(k * a, nbytes, seed=121)
+    Y = oracle_columns(lambda x: O.encode(n, k, O.SPARSE, True, x), [X])
+    sets = [[0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 16, 31],
+            [31, 0, 2, 3, 17, 5, 6, 7, 8, 9, 10, 11, 12, 20, 14, 15],
+            [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 18, 19, 22, 25]]
+    for S in sets:
+        c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
+        c.set_decode_kernel(P.PMRC_KERNEL_BITSLICED)
+        lazy_decode_every_column(c, n, k, S, nbytes, X, Y)
+        if sum(1 for i in S if i >= k) == 4:   # 60 dense rows over 240 blocks: factored only
+            assert c.runtime_kernels() == (2, 0)
+        else:
+            assert c.runtime_kernels() in ((1, 0), (2, 0))

@@ -74,7 +74,7 @@ def _evaluate_schedule(text, cols, X):
     for b, acc in acc_of.items():
         kernel_case = re.search(r"case %d: \{\s*(?:if \(half == 0\) )?k_b%d(?:_h0)?\(x, acc\);(.*?)\} break;"
                                 % (b, b), text, re.S)
-        for slot, q in re.findall(r"bs_store\(x, (\d+), acc\[(\d+)\]\)", kernel_case.group(1)):
+        for slot, q in re.findall(r"bs_store(?:_planes)?\(x, (\d+), acc\[(\d+)\]\)", kernel_case.group(1)):
             row = int(slot) - cols
             out[row] = sum((acc[int(q), bit].astype(np.uint16) << bit) for bit in range(8)).astype(np.uint8)
     return out
@@ -114,6 +114,71 @@ def test_bitsliced_schedule_computes_the_matrix(rows, cols, by_support, seed, pa
             if M[row, c]:
                 want ^= np.array([_gf_mul(int(M[row, c]), int(x)) for x in X[c]], np.uint8)
         assert np.array_equal(got[row], want), row
+
+
+@pytest.mark.parametrize("m,shared,r,groups,seed,max_inputs",
+                         [(21, 35, 21, 7, 1, 64), (7, 49, 7, 7, 2, 64), (14, 42, 10, 7, 3, 64),
+                          (64, 20, 64, 8, 4, 64), (3, 5, 2, 1, 5, 64), (24, 10, 24, 3, 6, 64),
+                          (20, 30, 20, 2, 7, 64), (30, 90, 30, 15, 8, 40)])
+def test_factored_schedules_compose_to_w_times_z(m, shared, r, groups, seed, max_inputs):
+    """The two launch schedules of a factored product x = W (Z y), the
+    reconstruction of a systematic code (z: the received parity blocks plus
+    their present-data terms; W = B^-1), evaluated on the CPU one after the
+    other -- stage 1's plane-layout outputs are stage 2's plane-layout
+    inputs -- equal W (Z X) computed with an independent multiply; stage 1
+    keeps the rows of one shared support together (groups of at most 8 rows
+    whole in one block, larger groups in blocks of their own) and packs
+    several groups into a block only within the input budget."""
+    import numpy as np
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("g++ not found")
+    exe = os.path.join(ROOT, "_build", "test_emit_factored_dump")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    res = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", exe,
+                          os.path.join(ROOT, "tests", "host", "emit_factored_dump.cpp"),
+                          os.path.join(CSRC, "bs_emit.cpp")], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    res = subprocess.run([exe, str(m), str(shared), str(r), str(groups), str(seed), str(max_inputs)],
+                         capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stderr
+    head, rest = res.stdout.split("STAGE1\n", 1)
+    stage1, stage2 = rest.split("STAGE2\n", 1)
+    lines = head.strip().splitlines()
+    cols = shared + m
+    Z = np.array([[int(v) for v in ln.split()] for ln in lines[1:1 + m]], np.uint8)
+    W = np.array([[int(v) for v in ln.split()] for ln in lines[2 + m:2 + m + r]], np.uint8)
+    assert Z.shape == (m, cols) and W.shape == (r, m)
+    tokens = lines[2 + m + r].split()[1:]
+    blocks = [[int(v) for v in b.split("/")[0].split(",")] for b in tokens]
+    ninputs = [int(b.split("/")[1]) for b in tokens]
+    assert sorted(sum(blocks, [])) == list(range(m)) and max(len(b) for b in blocks) <= 8
+    size = {g: sum(1 for i in range(m) if i % groups == g) for g in range(groups)}
+    for g in range(groups):
+        holding = [b for b in blocks if any(i % groups == g for i in b)]
+        if size[g] <= 8:
+            assert len(holding) == 1, (g, blocks)
+    for b, ni in zip(blocks, ninputs):
+        if len({i % groups for i in b}) > 1:
+            assert ni <= max_inputs, (b, ni)
+    X = np.random.default_rng(seed).integers(0, 256, (cols, 64), dtype=np.uint8)
+    z = _evaluate_schedule(stage1, cols, X)
+    assert sorted(z) == list(range(m))
+    zb = np.stack([z[i] for i in range(m)])
+    got = _evaluate_schedule(stage2, m, zb)
+    assert sorted(got) == list(range(r))
+
+    def apply(M, Y):
+        out = np.zeros((M.shape[0], Y.shape[1]), np.uint8)
+        for i in range(M.shape[0]):
+            for c in range(M.shape[1]):
+                if M[i, c]:
+                    out[i] ^= np.array([_gf_mul(int(M[i, c]), int(v)) for v in Y[c]], np.uint8)
+        return out
+
+    want = apply(W, apply(Z, X))
+    for i in range(r):
+        assert np.array_equal(got[i], want[i]), i
 
 
 def _run_statements(env, lines):
