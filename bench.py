@@ -53,6 +53,10 @@ SMS = 152   # GB300 streaming multiprocessors
 ALU_MODEL_BITSLICED = ("bitsliced kernel, per 32-byte lane and block: 44 lane-ops per input "
                        "(24 transpose + 20 subset-table XORs), 24 per output row (transpose "
                        "back), 8 per non-zero coefficient (one 3-input XOR per output plane)")
+ALU_MODEL_FACTORED = ("factored reconstruction, per 32-byte lane: launch 1 (z) 44 lane-ops per "
+                      "input per block and 8 per non-zero coefficient, outputs stored as bit "
+                      "planes; launch 2 (B^-1 z, taken as dense) 20 per plane-layout input per "
+                      "block, 24 per output row, 8 per coefficient")
 ALU_MODEL_PROJECTION = ("bitsliced projection kernel, per 32-byte lane: 24 lane-ops per helper "
                         "block read (transpose), per output plane of each constant product one "
                         "3-input XOR per two terms, 24 per helper (transpose back)")
@@ -87,6 +91,53 @@ def alu_ops_projection(phi, helpers):
             per_helper += (t // 2) if first else -(-t // 2)
         first = False
     return per_helper * helpers
+
+
+def factored_blocks(Z, own, max_inputs=64):
+    """The library's first-launch blocks of a factored reconstruction: rows
+    of Z grouped by their non-zero columns other than their own parity
+    block, groups packed whole into blocks of at most 8 rows within
+    max_inputs inputs (a group of more than 8 rows cut into blocks of its
+    own); returns (rows, inputs) per block."""
+    groups, order = {}, []
+    for r in range(Z.shape[0]):
+        key = tuple(int(q) for q in np.flatnonzero(Z[r]) if q != own[r])
+        if key not in groups:
+            order.append(key)
+        groups.setdefault(key, []).append(r)
+
+    def union(rs):
+        return int((Z[rs] != 0).any(axis=0).sum())
+
+    sets, cur = [], []
+    for key in order:
+        rs = groups[key]
+        if len(rs) > 8:
+            nb = -(-len(rs) // 8)
+            sets += [rs[len(rs) * b // nb:len(rs) * (b + 1) // nb] for b in range(nb)]
+            continue
+        grown = cur + rs
+        if cur and (len(grown) > 8 or union(grown) > max_inputs):
+            sets.append(cur)
+            cur = list(rs)
+        else:
+            cur = grown
+    if cur:
+        sets.append(cur)
+    return [(len(rs), union(rs)) for rs in sets]
+
+
+def alu_ops_factored(Z, own, m_out):
+    """ALU lane-ops per 32-byte column of the factored reconstruction's two
+    launches: z = Z y (blocks of factored_blocks, 44 per input, plane-layout
+    outputs) and the m_out wanted rows of B^-1 z (taken as dense: blocks of
+    at most 8 consecutive rows over all z, 20 per plane-layout input, 24 per
+    output row), 8 per non-zero coefficient in both."""
+    m = Z.shape[0]
+    c1 = sum(44 * c for _, c in factored_blocks(Z, own)) + 8 * int((Z != 0).sum())
+    nb = -(-m_out // 8)
+    c2 = nb * 20 * m + 24 * m_out + 8 * m_out * m
+    return c1 + c2
 
 
 def alu_ops_bitsliced(M, kind):
@@ -322,16 +373,40 @@ class Workload:
         Gs = self.sysc.generator()[K:]
         Dn = self.sysc.newcomer_matrix(self.f, self.H)
         Rm = R[missing] if missing else np.zeros((0, K), np.uint8)
+        # the factored form of the reconstruction (z = received parity
+        # blocks plus their present-data terms, then B^-1 z), which the
+        # library takes when its instruction model, second launch included,
+        # beats the one-launch schedule's (the same rule and constants)
+        Gfull = self.sysc.generator()
+        slots = [(a * i + j, a * pos + j) for pos, i in enumerate(self.S) if i >= K_ for j in range(a)]
+        Z = np.zeros((len(slots), K), np.uint8)
+        own = []
+        for q, (row, slot) in enumerate(slots):
+            Z[q, slot] = 1
+            own.append(slot)
+            for pos, i in enumerate(self.S):
+                if i < K_:
+                    for j in range(a):
+                        Z[q, a * pos + j] = Gfull[row, a * i + j]
+        one_launch = alu_ops_bitsliced(Rm, "chunked")
+        factored = alu_ops_factored(Z, own, len(missing)) if missing else None
+        self.decode_factored = factored is not None and \
+            factored + 1227 * (1 << 20) / B < one_launch
         self.kernel = {"gen_encode": "bitsliced encode bs_n16_k8_c0_f0",
                        "sys_encode": "bitsliced encode bs_n16_k8_c1_f1",
                        "repair_helpers": "bitsliced helper projections bs_rt_project (compiled at run time)",
                        "repair_newcomer": "bitsliced newcomer bs_rt_newcomer (compiled at run time)",
-                       "decode": "bitsliced reconstruction bs_rt_decode (compiled at run time)"}
+                       "decode": ("factored bitsliced reconstruction bs_rt_dstage1 + bs_rt_dstage2 "
+                                  "(compiled at run time, two launches)") if self.decode_factored else
+                                 "bitsliced reconstruction bs_rt_decode (compiled at run time)"}
         self.alu_ops, self.alu_model = {}, {}
         for n, M, kind in (("gen_encode", G, "support"), ("sys_encode", Gs, "support"),
                            ("decode", Rm, "chunked"), ("repair_newcomer", Dn, "chunked")):
             self.alu_ops[n] = alu_ops_bitsliced(M, kind) * (B // 32)
             self.alu_model[n] = ALU_MODEL_BITSLICED
+        if self.decode_factored:
+            self.alu_ops["decode"] = factored * (B // 32)
+            self.alu_model["decode"] = ALU_MODEL_FACTORED
         self.alu_ops["repair_helpers"] = alu_ops_projection(coef, D_) * (B // 32)
         self.alu_model["repair_helpers"] = ALU_MODEL_PROJECTION
 
