@@ -306,7 +306,14 @@ int pmrc_set_encode_kernel(pmrc_code *code, int which);
  * in the handle; the split-table kernel until then, otherwise, and whenever
  * the run-time kernel cannot be
  * built (NVRTC missing, blocks not 16-byte aligned, or more than 64 inputs
- * per 8-row block).  PMRC_KERNEL_GENERIC: always the split-table kernel.
+ * per 8-row block).  For a systematic MSR or Reed-Solomon code whose wanted
+ * rows are all missing data rows, the reconstruction may instead run
+ * factored, as two launches of run-time kernels: z = the received parity
+ * blocks plus their present-data terms, then B^-1 z (B: the parity rows on
+ * the missing columns), z held as bit planes in stream-ordered scratch of a
+ * memory pool the library keeps per device.  The library picks the form per
+ * (node set, wanted rows) from the kernels' instruction counts.
+ * PMRC_KERNEL_GENERIC: always the split-table kernel.
  * PMRC_KERNEL_BITSLICED: the run-time kernel at any size, PMRC_EUNSUPPORTED
  * from pmrc_decode when it cannot be built.  Results are identical.  The
  * same choice applies to pmrc_repair_newcomer (its D, per failed node and
