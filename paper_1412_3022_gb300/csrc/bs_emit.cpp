@@ -142,6 +142,44 @@ void bs_cta_ranges(int nblocks, const int *cost, uint64_t ntiles, int ncta, uint
 
 namespace {
 
+// The accumulate statements of input column `col` into the block's rows:
+// one logic instruction per (row, plane) with a non-zero term, acc ^ Q[lo] ^
+// R[hi] for the two nibbles of row `plane` of the coefficient's bit matrix.
+// Returns the instructions emitted.
+int emit_accumulate(std::string &f, const uint8_t *M, int K, const BsBlock &B, int col,
+                    long long &xors) {
+  int ops = 0;
+  for (size_t q = 0; q < B.rows.size(); q++) {
+    const uint8_t cf = M[(size_t)B.rows[q] * K + col];
+    for (int bit = 0; bit < 8; bit++) {
+      int lo = 0, hi = 0;  // row `bit` of M_cf, split in two nibbles
+      for (int j = 0; j < 8; j++) {
+        const uint8_t colj = gf_mul_sr(cf, (uint8_t)(1u << j));
+        if ((colj >> bit) & 1) {
+          if (j < 4)
+            lo |= 1 << j;
+          else
+            hi |= 1 << (j - 4);
+        }
+      }
+      if (lo && hi) {
+        appendf(f, "      acc[%zu][%d] = bs_x3(acc[%zu][%d], Q[%d], R[%d]);\n", q, bit, q, bit, lo, hi);
+        xors += 2;
+        ops++;
+      } else if (lo) {
+        appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], Q[%d]);\n", q, bit, q, bit, lo);
+        xors += 1;
+        ops++;
+      } else if (hi) {
+        appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], R[%d]);\n", q, bit, q, bit, hi);
+        xors += 1;
+        ops++;
+      }
+    }
+  }
+  return ops;
+}
+
 // One block function: the loop over `ins` (a block's inputs, or half of
 // them) accumulating M's coefficients of the block's rows into acc; with
 // in_planes the inputs are plane-layout blocks (no transpose).  Returns the
@@ -185,37 +223,7 @@ int emit_block_fn(std::string &f, const uint8_t *M, int K, const BsBlock &B,
   f += "    switch (i) {\n";
   for (int i = 0; i < C; i++) {
     appendf(f, "    case %d:\n", i);
-    const int col = ins[i];
-    for (size_t q = 0; q < B.rows.size(); q++) {
-      const uint8_t cf = M[(size_t)B.rows[q] * K + col];
-      for (int bit = 0; bit < 8; bit++) {
-        int lo = 0, hi = 0;  // row `bit` of M_cf, split in two nibbles
-        for (int j = 0; j < 8; j++) {
-          const uint8_t colj = gf_mul_sr(cf, (uint8_t)(1u << j));
-          if ((colj >> bit) & 1) {
-            if (j < 4)
-              lo |= 1 << j;
-            else
-              hi |= 1 << (j - 4);
-          }
-        }
-        // one logic instruction per (row, plane, input): acc ^ Q[lo] ^ R[hi]
-        if (lo && hi) {
-          appendf(f, "      acc[%zu][%d] = bs_x3(acc[%zu][%d], Q[%d], R[%d]);\n", q, bit, q, bit,
-                  lo, hi);
-          xors += 2;
-          ops++;
-        } else if (lo) {
-          appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], Q[%d]);\n", q, bit, q, bit, lo);
-          xors += 1;
-          ops++;
-        } else if (hi) {
-          appendf(f, "      acc[%zu][%d] = bs_x2(acc[%zu][%d], R[%d]);\n", q, bit, q, bit, hi);
-          xors += 1;
-          ops++;
-        }
-      }
-    }
+    ops += emit_accumulate(f, M, K, B, ins[i], xors);
     f += "      break;\n";
   }
   f += "    default: break;\n    }\n  }\n";
