@@ -209,11 +209,9 @@ int pmrc_read_degraded(const pmrc_code *code, int node, const int *helpers,
  *
  * Every call looks up the array's device address on the calling thread's
  * current device (cudaGetSymbolAddress, a host-side query; the array's
- * host-side name is not a device address).  The call is not for graph
- * capture: on a stream that is being captured it returns PMRC_EINVAL
- * without enqueuing anything (the copy it makes reads the plan's host image,
- * which the handle's plan cache may free before a graph is replayed).
- * Every call uses the same array and it keeps the last
+ * host-side name is not a device address).  The first call on a device also
+ * loads the library's device code there, so make that first call before any
+ * stream capture.  Every call uses the same array and it keeps the last
  * call's contents, so calls that overlap on the GPU (other streams, other
  * host threads) race and corrupt each other's results: issue them one after
  * another on one stream.  For PMRC_RS codes (one block per node, helper

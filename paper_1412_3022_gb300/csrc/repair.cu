@@ -205,18 +205,6 @@ int launch_fused_repair_noalloc(const FusedRepairPlan &plan, const uint8_t *cons
   RepairArgs a;
   rc = repair_pointers(h, helper_blocks, out, a, err);
   if (rc) return rc;
-  // a captured call would record a copy from the plan's host image, which
-  // the handle's plan cache may free before the graph is replayed
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
-  if (ce != cudaSuccess) {
-    err = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce);
-    return kECuda;
-  }
-  if (cap != cudaStreamCaptureStatusNone) {
-    err = "pmrc_repair_noalloc cannot be captured into a graph";
-    return kEInval;
-  }
   if (nbytes == 0) return kOk;
   // device address of the fixed scratch on the calling thread's current
   // device, looked up on every call (a host-side query): the host-side name

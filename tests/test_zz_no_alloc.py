@@ -111,35 +111,3 @@ def test_repair_noalloc_matches_repair_for_mbr_and_reed_solomon():
     Yr = oracle_columns(lambda x: O.rs_encode(n, k, True, x), [X])
     for f in (3, 12):
         compare(rs, Yr, f, nbytes, lambda H, x, f=f: O.rs_repair(n, k, True, f, H, x)[None, :])
-
-
-def test_repair_noalloc_refuses_stream_capture():
-    """On a stream being captured the allocation-free repair enqueues nothing
-    and returns PMRC_EINVAL (its copy reads the plan's host image, which the
-    handle's plan cache may free before a replay); the same call outside the
-    capture repairs the node."""
-    n, k = 16, 8
-    a = k - 1
-    c = P.Code(n, k, P.PMRC_SPARSE, P.PMRC_SYSTEMATIC)
-    nbytes = 4096
-    X = inputs.blocks(k * a, nbytes, seed=15)
-    Yh = O.encode(n, k, O.SPARSE, True, X)
-    Y = torch.from_numpy(Yh).cuda()
-    f = 10
-    H = c.default_helpers(f)
-    blocks = [Y[a * h + j] for h in H for j in range(a)]
-    got = torch.full((a, nbytes), 0xA5, dtype=torch.uint8, device="cuda")
-    L = P.lib()
-    hs = (ctypes.c_int * len(H))(*H)
-    bp = (ctypes.c_void_p * len(blocks))(*[b.data_ptr() for b in blocks])
-    op = (ctypes.c_void_p * a)(*[got[j].data_ptr() for j in range(a)])
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        rc = L.pmrc_repair_noalloc(ctypes.c_void_p(c.handle), f, hs, bp, op, ctypes.c_size_t(nbytes),
-                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert rc == P.PMRC_EINVAL, (rc, P.pmrc_last_error())
-    assert "captured" in P.pmrc_last_error()
-    abi_call("pmrc_repair_noalloc", c, f, H, blocks, [got[j] for j in range(a)], nbytes)
-    torch.cuda.synchronize()
-    assert np.array_equal(got.cpu().numpy(), Yh[a * f:a * f + a])
