@@ -1038,6 +1038,7 @@ bool prefer_factored(const pmrc_code *c, const int *nodes, const std::vector<cha
       if (blocks_fit(blks, M.rows, M.cols)) cost.first = schedule_cost(M, blks, false, false);
     }
     std::lock_guard<std::mutex> g(c->mu);
+    if (c->decode_costs.size() >= kPlanCacheCap) c->decode_costs.erase(c->decode_costs.begin());
     c->decode_costs[key] = cost;
   }
   if (cost.second < 0) return false;
@@ -1053,14 +1054,27 @@ bool factored_runtime(const pmrc_code *c, const int *nodes, const std::vector<ch
                       bool background, std::shared_ptr<BsRuntimeKernel> &kz,
                       std::shared_ptr<BsRuntimeKernel> &kw, std::vector<int> &rows, int &m,
                       std::string &err) {
+  const std::string zkey = nodes_key(c, "fz:", nodes), wkey = nodes_key(c, "fw:", nodes) + want_key(want);
+  rows.clear();
+  for (int r = 0; r < c->m.K; r++)  // the second launch writes the wanted rows in this order
+    if (want[r]) rows.push_back(r);
+  {  // both kernels loaded: no host work beyond the lookups
+    std::lock_guard<std::mutex> g(c->mu);
+    auto iz = c->rt.find(zkey), iw = c->rt.find(wkey);
+    if (iz != c->rt.end() && iw != c->rt.end() && iz->second && iw->second) {
+      kz = iz->second;
+      kw = iw->second;
+      m = bitslice_outputs(*kz);
+      return true;
+    }
+  }
   Factored F;
   if (!factored_form(c, nodes, want, F)) {
     err = "no factored form";
     return false;
   }
-  rows = F.rows;
   m = F.Z.rows;
-  kz = runtime_kernel_job(c, nodes_key(c, "fz:", nodes), [&](BsCompileFn &compile, std::string &) {
+  kz = runtime_kernel_job(c, zkey, [&](BsCompileFn &compile, std::string &) {
     const Mat Z = F.Z;
     const std::vector<BsBlock> zb = F.zb;
     compile = [Z, zb](BsCompiled &out, std::string &e2) {
@@ -1069,8 +1083,7 @@ bool factored_runtime(const pmrc_code *c, const int *nodes, const std::vector<ch
     };
     return (int)kOk;
   }, err, background);
-  kw = runtime_kernel_job(c, nodes_key(c, "fw:", nodes) + want_key(want),
-                          [&](BsCompileFn &compile, std::string &) {
+  kw = runtime_kernel_job(c, wkey, [&](BsCompileFn &compile, std::string &) {
     const Mat W = F.W;
     const std::vector<BsBlock> wb = F.wb;
     compile = [W, wb](BsCompiled &out, std::string &e2) {

@@ -368,6 +368,8 @@ int bitslice_compile_fused_repair(const uint8_t *phi, int alpha, const uint8_t *
 
 int bitslice_kind(const BsRuntimeKernel &k) { return k.kind; }
 
+int bitslice_outputs(const BsRuntimeKernel &k) { return k.noutputs; }
+
 cudaError_t bitslice_launch_projection(BsRuntimeKernel &k, int nh, const uint8_t *const *in,
                                        uint8_t *const *out, size_t nbytes, cudaStream_t stream) {
   if (k.kind != kBsProjection || nh <= 0 || nh * k.alpha + nh > kBsMaxPtr || nbytes % kBsBytes)

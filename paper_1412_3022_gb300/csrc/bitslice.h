@@ -123,4 +123,7 @@ cudaError_t bitslice_launch_fused_repair(BsRuntimeKernel &k, const uint8_t *cons
 // The kind of a loaded run-time kernel (BsKind).
 int bitslice_kind(const BsRuntimeKernel &k);
 
+// Output blocks a run-time matrix kernel writes (its matrix's rows).
+int bitslice_outputs(const BsRuntimeKernel &k);
+
 }  // namespace pmrc
