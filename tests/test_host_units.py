@@ -181,6 +181,38 @@ def test_factored_schedules_compose_to_w_times_z(m, shared, r, groups, seed, max
         assert np.array_equal(got[i], want[i]), i
 
 
+@pytest.mark.parametrize("m,shared,groups,seed,max_inputs", [(21, 35, 7, 1, 64), (30, 90, 15, 8, 40),
+                                                            (24, 10, 3, 6, 64), (64, 20, 8, 4, 64)])
+def test_bench_models_the_library_blocks_of_the_factored_reconstruction(m, shared, groups, seed,
+                                                                         max_inputs):
+    """The benchmark's instruction model of the factored reconstruction
+    (bench.factored_blocks) cuts the first launch's rows into the same
+    blocks, with the same input counts, as the library's rule
+    (bs_blocks_grouped), on the emitter's own dump."""
+    import sys
+    import numpy as np
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("g++ not found")
+    sys.path.insert(0, ROOT)
+    import bench
+    exe = os.path.join(ROOT, "_build", "test_emit_factored_dump")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    res = subprocess.run([cxx, "-std=c++17", "-O2", "-I" + CSRC, "-o", exe,
+                          os.path.join(ROOT, "tests", "host", "emit_factored_dump.cpp"),
+                          os.path.join(CSRC, "bs_emit.cpp")], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    res = subprocess.run([exe, str(m), str(shared), str(m), str(groups), str(seed), str(max_inputs)],
+                         capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stderr
+    lines = res.stdout.split("STAGE1\n", 1)[0].strip().splitlines()
+    Z = np.array([[int(v) for v in ln.split()] for ln in lines[1:1 + m]], np.uint8)
+    tokens = lines[2 + 2 * m].split()[1:]
+    lib = [(len(b.split("/")[0].split(",")), int(b.split("/")[1])) for b in tokens]
+    own = [shared + i for i in range(m)]
+    assert bench.factored_blocks(Z, own, max_inputs) == lib
+
+
 def _run_statements(env, lines):
     """Executes emitted assignments (x = y; x = 0u; x = bs_x2(a, b);
     x = bs_x3(a, b, c);) on integer bit vectors."""
